@@ -1,0 +1,174 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module only draws inputs.  It holds none of the sorting arithmetic and
+serves the CUDA path and the CPU oracle alike; both receive the same host
+arrays.
+
+Random numbers come from SplitMix64 (Steele, Lea and Flood, "Fast Splittable
+Pseudorandom Number Generators", OOPSLA 2014) used as a counter-based
+generator: the i-th 64-bit output of stream ``seed`` is
+``mix(seed + (i + 1) * 0x9E3779B97F4A7C15)`` with the published finaliser
+``mix``.  Every draw is therefore a pure function of (seed, index), which keeps
+chunked generation of very large arrays deterministic.
+
+Distributions (the paper's workloads are random, sorted and nearly sorted
+arrays; it gives no generator parameters):
+
+* ``random``: uniform over the full int32 range.
+* ``sorted``: ascending, spread over the full int32 range; built as a running
+  sum of random gaps (no sort involved), so it has the density of a sorted
+  uniform draw and may contain equal neighbours.
+* ``nearly``: ``sorted``, then for ``floor(0.01 n)`` draws (i, j), each uniform
+  in [0, n), a[i] and a[j] are swapped, in draw order.
+* pair keys: 2^16 distinct values; u uniform in [0, 65535] mapped through the
+  injection ``u -> (u * M) xor C (mod 2^32)`` with M odd and C drawn from the
+  generator, viewed as int32; values are the original indices.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+_CHUNK = 1 << 22
+
+SEED_BASE = 0x5EED0000
+
+
+def config_seed(config_id: int, salt: int = 0) -> int:
+    """Seed of a workload: SEED_BASE + config id, plus an optional salt."""
+    return (SEED_BASE + int(config_id) + (int(salt) << 32)) & 0xFFFFFFFFFFFFFFFF
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def splitmix64(seed: int, start: int, count: int) -> np.ndarray:
+    """Outputs start .. start+count-1 of stream ``seed`` as uint64."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + idx * GAMMA
+        return _mix(z)
+
+
+def _stream_u32(seed: int, n: int, out: np.ndarray | None = None) -> np.ndarray:
+    """Low 32 bits of the first n outputs, generated in chunks."""
+    out = np.empty(n, np.uint32) if out is None else out
+    for s in range(0, n, _CHUNK):
+        c = min(_CHUNK, n - s)
+        out[s:s + c] = (splitmix64(seed, s, c) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    return out
+
+
+def uniform01(seed: int, n: int) -> np.ndarray:
+    """n doubles in [0, 1) from the top 53 bits of each output."""
+    return (splitmix64(seed, 0, n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+def uniform_int(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
+    """n integers uniform in [lo, hi] (inclusive), as int64 (floor of a scaled double)."""
+    span = hi - lo + 1
+    return lo + np.minimum((uniform01(seed, n) * span).astype(np.int64), span - 1)
+
+
+def random_i32(n: int, seed: int) -> np.ndarray:
+    return _stream_u32(seed, n).view(np.int32)
+
+
+def sorted_i32(n: int, seed: int) -> np.ndarray:
+    """Ascending keys spanning [INT32_MIN, INT32_MAX] with random gaps."""
+    if n == 0:
+        return np.empty(0, np.int32)
+    max_gap = max(1, (1 << 33) // n)  # mean gap ~ 2^32 / n
+    out = np.empty(n, np.int32)
+    acc = 0
+    for s in range(0, n, _CHUNK):
+        c = min(_CHUNK, n - s)
+        gaps = (splitmix64(seed, s, c) % np.uint64(max_gap)).astype(np.int64)
+        run = np.cumsum(gaps) + acc
+        acc = int(run[-1])
+        out[s:s + c] = np.clip(run - (1 << 31), -(1 << 31), (1 << 31) - 1).astype(np.int32)
+    return out
+
+
+def nearly_sorted_i32(n: int, seed: int) -> np.ndarray:
+    a = sorted_i32(n, seed)
+    k = n // 100
+    if k == 0:
+        return a
+    draws = splitmix64(seed ^ 0x6E6561726C79, 0, 2 * k) % np.uint64(n)
+    ii = draws[0::2].astype(np.int64).tolist()
+    jj = draws[1::2].astype(np.int64).tolist()
+    for i, j in zip(ii, jj):
+        a[i], a[j] = a[j], a[i]
+    return a
+
+
+def keys(n: int, dist: str, seed: int) -> np.ndarray:
+    """int32 keys of one distribution: 'random', 'sorted' or 'nearly'."""
+    if dist == "random":
+        return random_i32(n, seed)
+    if dist == "sorted":
+        return sorted_i32(n, seed)
+    if dist == "nearly":
+        return nearly_sorted_i32(n, seed)
+    raise ValueError(dist)
+
+
+def pair_keys_16bit(n: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """Keys from 2^16 distinct int32 values and values = original index."""
+    u = (_stream_u32(seed, n) & np.uint32(0xFFFF)).astype(np.uint32)
+    h = splitmix64(seed ^ 0x7061697273, 0, 2)
+    mult = np.uint32((int(h[0]) & 0xFFFFFFFF) | 1)
+    xor = np.uint32(int(h[1]) & 0xFFFFFFFF)
+    with np.errstate(over="ignore"):
+        k = ((u * mult) ^ xor).astype(np.uint32).view(np.int32)
+    v = np.arange(n, dtype=np.int32)
+    return k, v
+
+
+def segment_sizes(num_segs: int, seed: int, lo: int = 3, hi: int = 65536) -> np.ndarray:
+    """floor(exp(U(ln lo, ln(hi+1)))) clamped to [lo, hi] (log-uniform sizes)."""
+    u = uniform01(seed, num_segs)
+    s = np.floor(np.exp(math.log(lo) + u * (math.log(hi + 1) - math.log(lo)))).astype(np.int64)
+    return np.clip(s, lo, hi)
+
+
+DISTS = ("random", "sorted", "nearly")
+
+
+def segmented(num_segs: int, seed: int, lo: int = 3, hi: int = 65536,
+              sizes: np.ndarray | None = None):
+    """Concatenated segments with a per-segment distribution drawn uniformly
+    from (random, sorted, nearly).  Returns (keys, offsets[num_segs+1], dist_ids)."""
+    sizes = segment_sizes(num_segs, seed, lo, hi) if sizes is None else np.asarray(sizes, np.int64)
+    num_segs = sizes.size
+    off = np.zeros(num_segs + 1, np.int64)
+    np.cumsum(sizes, out=off[1:])
+    dist_ids = uniform_int(seed ^ 0x64697374, num_segs, 0, 2)
+    out = np.empty(int(off[-1]), np.int32)
+    # One contiguous random draw for the whole buffer, then per-segment rewrites
+    # for sorted and nearly sorted segments (each seeded by its index).
+    _stream_u32(seed ^ 0x6B657973, out.size, out.view(np.uint32))
+    for s in np.nonzero(dist_ids != 0)[0].tolist():
+        b, e = int(off[s]), int(off[s + 1])
+        sub_seed = (seed * 1000003 + s) & 0xFFFFFFFFFFFFFFFF
+        out[b:e] = keys(e - b, DISTS[int(dist_ids[s])], sub_seed)
+    return out, off, dist_ids
+
+
+def log_uniform_sizes(n: int, seed: int, lo: int, hi: int) -> np.ndarray:
+    """Sizes floor(exp(U(ln lo, ln(hi+1)))) clamped to [lo, hi]."""
+    return segment_sizes(n, seed, lo, hi)
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson process: cumulative exponential gaps."""
+    u = uniform01(seed, n)
+    return np.cumsum(-np.log1p(-u) / rate_per_s)

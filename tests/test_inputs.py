@@ -1,0 +1,57 @@
+"""The seeded input generators: determinism and the stated distributions."""
+import math
+
+import numpy as np
+
+import hs_inputs as g
+
+
+def test_splitmix64_reference_values():
+    # SplitMix64 with seed 0: published first outputs of the generator
+    # (Steele, Lea, Flood 2014; the java.util.SplittableRandom sequence).
+    out = g.splitmix64(0, 0, 3)
+    assert [int(x) for x in out] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_counter_based_chunks_agree():
+    a = g.splitmix64(123, 0, 1000)
+    b = np.concatenate([g.splitmix64(123, 0, 400), g.splitmix64(123, 400, 600)])
+    assert np.array_equal(a, b)
+
+
+def test_distributions():
+    n = 100_000
+    r = g.keys(n, "random", 1)
+    assert r.dtype == np.int32 and r.size == n
+    assert np.array_equal(r, g.keys(n, "random", 1))
+    assert r.min() < -(1 << 30) and r.max() > (1 << 30)
+    s = g.keys(n, "sorted", 2)
+    assert np.all(np.diff(s.astype(np.int64)) >= 0)
+    assert s[0] < -(1 << 30) and s[-1] > (1 << 30)
+    nearly = g.keys(n, "nearly", 2)
+    moved = np.count_nonzero(nearly != s)
+    assert 0 < moved <= 2 * (n // 100)
+    assert np.array_equal(np.sort(nearly), s)
+
+
+def test_pair_keys():
+    k, v = g.pair_keys_16bit(1 << 18, 5)
+    assert np.unique(k).size <= 1 << 16
+    assert np.array_equal(v, np.arange(1 << 18, dtype=np.int32))
+
+
+def test_segment_sizes():
+    sz = g.segment_sizes(200_000, 5)
+    assert sz.min() >= 3 and sz.max() <= 65536
+    mean = (65536 - 3) / math.log(65536 / 3)
+    assert abs(sz.mean() / mean - 1) < 0.02
+    keys, off, d = g.segmented(500, 6)
+    assert off[0] == 0 and off[-1] == keys.size and np.all(np.diff(off) >= 3)
+    assert set(np.unique(d)) <= {0, 1, 2}
+
+
+def test_poisson():
+    t = g.poisson_arrivals(20000, 100.0, 3)
+    gaps = np.diff(t)
+    assert np.all(gaps >= 0)
+    assert abs(gaps.mean() * 100.0 - 1) < 0.05
