@@ -1,0 +1,422 @@
+"""Benchmark: hybrid network-leaf merge sort of 2^28 uniform int32 keys on GB300.
+
+One step = one full sort (block sort with {6,7,8} network leaves + every
+global merge level) of n = 2^28 uniform int32 keys resident in HBM.  Prints
+ONE JSON line (rank 0).  Multi-GPU runs are independent replicas: each rank
+sorts its own array, no collective touches the data path.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The reference arm (--impl reference) times the plain CPU oracle
+(Algorithm 1 with {6,7,8} leaves, single thread) on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import hs_inputs  # noqa: E402
+
+METRIC = "int32 keys/s & %HBM roofline; batched vs plain keys/s; serve p50/p99"
+UNIT = "keys/s"
+FALLBACK_HBM_GBS = 6800.0
+SPEC_HBM_GBS = 8000.0
+KERNEL_SOURCES = ["paper_2503_05934_gb300/csrc/hs_merge_kernels.cuh",
+                  "paper_2503_05934_gb300/csrc/hs_merge.cu",
+                  "paper_2503_05934_gb300/csrc/hs_common.cuh",
+                  "paper_2503_05934_gb300/csrc/hs_networks.cuh"]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "merge_keys_2p28_uniform.md")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--log2n", type=int, default=28)
+    p.add_argument("--netset", default="6To8")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    return p.parse_args()
+
+
+def workload_config(args, n):
+    return {
+        "workload": f"hybrid merge sort, n=2^{args.log2n} uniform int32 keys, "
+                    f"{args.netset} network leaves",
+        "n": n, "dist": "uniform over [INT32_MIN, INT32_MAX]", "algo": "merge",
+        "netset": args.netset, "seed": hs_inputs.config_seed(2),
+        "l2": "inputs larger than L2 (1 GiB per array vs 129 MB L2)",
+        "restore": "in-place sort; the input is restored from a pristine device copy "
+                   "before each step, outside the timed events",
+        "parallelism": "replicas (one independent array per GPU)",
+    }
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 100 ms) while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.lines: list[str] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n: int):
+    """DRAM bytes per merge_keys launch from the committed ncu summary, scaled
+    to n keys, or None when the kernel sources changed since the capture."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
+    m_bpk = re.search(r"dram_bytes_per_key_per_launch:\s*([0-9.]+)", text)
+    if not m_hash or not m_bpk or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bpk.group(1)) * n
+
+
+def sort_passes(n: int, tile: int) -> int:
+    p, w = 1, tile
+    while w < n:
+        w *= 2
+        p += 1
+    return p
+
+
+def cpu_oracle_rate(sample: np.ndarray, seconds: float, netset: str):
+    import oracle
+    done, t_total, reps = 0, 0.0, 0
+    while reps == 0 or t_total < seconds:
+        t0 = time.perf_counter()
+        oracle.merge_sort(sample, netset)
+        t_total += time.perf_counter() - t0
+        done += sample.size
+        reps += 1
+    return done / t_total, reps
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = 1 << args.log2n
+    sample_n = min(n, 1 << 22)
+    a = hs_inputs.random_i32(sample_n, hs_inputs.config_seed(2))
+    import oracle
+    oracle.lib()
+    for _ in range(args.warmup):
+        oracle.merge_sort(a, args.netset)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.merge_sort(a, args.netset)
+        times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    value = sample_n / mean
+    sample = (f"first 2^{int(np.log2(sample_n))} keys of the 2^{args.log2n} uniform workload, "
+              f"one full oracle sort per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+        "data": "synthetic", "config": workload_config(args, n),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    ws_world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws_world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    from paper_2503_05934_gb300 import build as hs_build
+    hs_build.build()
+    import paper_2503_05934_gb300 as hs
+
+    n = 1 << args.log2n
+    seed = hs_inputs.config_seed(2, salt=rank)
+    host = hs_inputs.random_i32(n, seed)
+    pristine = torch.from_numpy(host).to(dev)
+    work = torch.empty_like(pristine)
+    wsb = torch.empty(hs.hs_sort_workspace_bytes(n), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step_timed():
+        work.copy_(pristine)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hs.hs_sort_i32(work, "merge", args.netset, ws=wsb, stream=stream)
+        e1.record(stream)
+        return e0, e1
+
+    for _ in range(args.warmup):
+        step_timed()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    hs.hs_prof_reset()
+    hs.hs_prof_enable(True)
+    launches0 = hs.hs_launch_count()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.perf_counter()
+    evs = [step_timed() for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    launches = hs.hs_launch_count() - launches0
+    hs.hs_prof_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    mk_launches, mk_ms = hs.hs_prof_read("merge_keys")
+    bs_launches, bs_ms = hs.hs_prof_read("blocksort_keys")
+    mp_launches, mp_ms = hs.hs_prof_read("merge_partition")
+
+    # Correctness guard on the last result (cheap: sortedness on the device).
+    assert bool((work[1:] >= work[:-1]).all().item()), "benchmark output not sorted"
+
+    if pg:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    value = ws_world * n * args.steps / (total_ms / 1e3)
+    peak, peak_kind = measured_peak()
+    avg_mk_s = (mk_ms / mk_launches) / 1e3 if mk_launches else None
+    alg_bytes = 8.0 * n  # one read + one write of every key per merge level
+    achieved = alg_bytes / avg_mk_s / 1e9 if avg_mk_s else None
+    traffic = profiled_traffic(n)
+    roofline = {
+        "kernel": "merge_keys", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "peak_kind": peak_kind, "unit": "GB/s",
+        "frac": achieved / peak if achieved else None, "traffic": traffic,
+        "algorithmic_bytes_per_launch": alg_bytes,
+        "launch_ms": avg_mk_s * 1e3 if avg_mk_s else None,
+    }
+    tile = 1024 * 8 if args.netset in ("6To8", "3To8", "PowerOf2", "Even") else None
+    passes = sort_passes(n, tile) if tile else None
+    p_ref = sort_passes(n, 8192)
+    ms_step = total_ms / args.steps
+    whole = None
+    if passes:
+        b = min(passes, p_ref) * 2 * 4 * n
+        whole = {"passes": passes, "passes_ref": p_ref, "bytes": b,
+                 "frac_of_measured": b / (ms_step / 1e3) / (peak * 1e9),
+                 "frac_of_8tbs": b / (ms_step / 1e3) / (SPEC_HBM_GBS * 1e9),
+                 "one_pass_bound_ms": 2 * 4 * n / (peak * 1e9) * 1e3}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+        "data": "synthetic", "config": workload_config(args, n),
+        "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "sort_roofline": whole,
+        "kernel_ms_per_step": {"blocksort_keys": bs_ms / args.steps,
+                               "merge_partition": mp_ms / args.steps,
+                               "merge_keys": mk_ms / args.steps},
+        "wall_s_timed_region": t_wall,
+    }
+
+    del work
+    # ---- end to end through the host-buffer C-ABI call (pinned host memory)
+    if not args.no_e2e:
+        h_pristine = host
+        h_buf = torch.empty(n, dtype=torch.int32).pin_memory()
+        ws_h = torch.empty(hs.hs_sort_host_workspace_bytes(n), dtype=torch.uint8, device=dev)
+        for _ in range(max(1, min(args.warmup, 2))):
+            h_buf.numpy()[:] = h_pristine
+            hs.hs_sort_i32_host(h_buf, "merge", args.netset, ws=ws_h, stream=stream)
+        e2e_steps = max(1, min(args.steps, 10))
+        tot = 0.0
+        for _ in range(e2e_steps):
+            h_buf.numpy()[:] = h_pristine
+            if pg:
+                pg.barrier()
+            t0 = time.perf_counter()
+            hs.hs_sort_i32_host(h_buf, "merge", args.netset, ws=ws_h, stream=stream)
+            tot += time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([tot], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            tot = float(t.item())
+        assert bool(np.all(h_buf.numpy()[1:] >= h_buf.numpy()[:-1])), "e2e output not sorted"
+        line["e2e"] = {"value": ws_world * n * e2e_steps / tot, "unit": UNIT,
+                       "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
+                       "steps": e2e_steps, "api": "hs_sort_i32_host (pinned host buffer)"}
+        del ws_h, h_buf
+
+    # ---- extra forms (stable pairs), timed the same way
+    if not args.no_extras:
+        line["extras"] = run_extras(hs, torch, dev, stream, args, rank)
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    if rank == 0 and ws_world == 1 and not args.no_cpu:
+        sample_n = min(n, 1 << 22)
+        rate, reps = cpu_oracle_rate(host[:sample_n].copy(), args.cpu_seconds, args.netset)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first 2^22 keys of the workload, oracle Algorithm 1 ({args.netset}), "
+                      f"{reps} full sorts on one host core"}
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def run_extras(hs, torch, dev, stream, args, rank):
+    out = {}
+    # Stable pairs: 2^27 keys from 2^16 distinct values, value = index.
+    n = 1 << (args.log2n - 1)
+    k, v = hs_inputs.pair_keys_16bit(n, hs_inputs.config_seed(2, salt=1 + (rank << 8)))
+    pk, pv = torch.from_numpy(k).to(dev), torch.from_numpy(v).to(dev)
+    wk, wv = torch.empty_like(pk), torch.empty_like(pv)
+    wsb = torch.empty(hs.hs_sort_workspace_bytes(n, True), dtype=torch.uint8, device=dev)
+    times = []
+    for i in range(args.warmup + max(3, args.steps // 2)):
+        wk.copy_(pk)
+        wv.copy_(pv)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hs.hs_sort_pairs_i32(wk, wv, "merge", args.netset, ws=wsb, stream=stream)
+        e1.record(stream)
+        if i >= args.warmup:
+            times.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in times) / len(times)
+    out["pairs_stable_2p27"] = {"value": n / (ms / 1e3), "unit": "pairs/s", "ms_per_sort": ms,
+                                "workload": "2^27 (int32 key from 2^16 values, int32 index) "
+                                            "stable merge sort, 6To8 leaves"}
+    del pk, pv, wk, wv, wsb
+    return out
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

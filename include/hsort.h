@@ -1,0 +1,152 @@
+/*
+ * hsort: hybrid network-leaf sorting of int32 keys on one GB300 (sm_103a).
+ *
+ * The method is that of Aly, Jensen and ElAarag, "Improving Merge Sort and
+ * Quick Sort Performance by Utilizing AlphaDev's Sorting Networks as Base
+ * Cases" (ACMSE 2025):
+ *   - Algorithm 1 (Optimized Merge Sort with Sorting Networks): subarrays whose
+ *     size has a fixed sorting network are sorted by that network; everything
+ *     above them is sorted by Merge.
+ *   - Algorithm 2 (Optimized Quick Sort with Sorting Networks): the same leaves
+ *     under median-of-three partitioning.
+ *   - Table 3 (Sorting Network Configurations): which network sizes (3..8) a
+ *     configuration may use; see hs_netset below.
+ * On the GPU a leaf is a thread's register tile sorted by a branch-free
+ * network; merge-path partitioned merges (or 3-way partitions) do the rest.
+ *
+ * Conventions for every call:
+ *   - Device pointers come from cudaMalloc (or any allocation the device can
+ *     address); the caller owns every buffer.  Sorting is in place.
+ *   - Workspace is caller-provided: query its size first.  No call below
+ *     allocates device memory on the sorting path.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream) unless stated otherwise.  Argument errors are detected
+ *     on the host before any launch and return synchronously.
+ *   - Keys use the signed int32 order.  No C++ exception crosses this ABI.
+ *   - A failing call returns a status; hs_last_error() (thread-local) then
+ *     holds a one-line message.
+ */
+#ifndef HSORT_H
+#define HSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HS_API __attribute__((visibility("default")))
+#else
+#define HS_API
+#endif
+
+typedef void *hs_stream_t; /* a cudaStream_t */
+
+typedef enum {
+    HS_OK = 0,
+    HS_ERR_INVALID_ARG = 1, /* bad pointer, size, netset, algo or workspace */
+    HS_ERR_UNSUPPORTED = 2, /* valid request the library does not serve */
+    HS_ERR_NO_MEMORY = 3,   /* a host-side allocation failed */
+    HS_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed */
+    HS_ERR_TIMEOUT = 5,     /* a bounded device or host wait gave up */
+    HS_ERR_OVER_BUDGET = 6  /* request larger than a server's memory budget */
+} hs_status;
+
+typedef enum {
+    HS_ALGO_MERGE = 0, /* Algorithm 1: network leaves + merge passes */
+    HS_ALGO_QUICK = 1  /* Algorithm 2: network leaves + 3-way partitions */
+} hs_algo;
+
+/* Network set (Table 3): bit k set <=> the size-k network may be used,
+ * k in 3..8.  0 is the classical algorithm (no networks).  Any other bit is
+ * HS_ERR_INVALID_ARG.  The GPU leaf is the largest size in the set; a ragged
+ * last leaf of r keys uses the size-r network when the set has it, else the
+ * next larger size in the set padded with +infinity sentinels. */
+typedef uint32_t hs_netset;
+#define HS_NETS_NONE 0x000u
+#define HS_NETS_3 0x008u        /* {3} */
+#define HS_NETS_3TO4 0x018u     /* {3,4} */
+#define HS_NETS_3TO5 0x038u     /* {3,4,5} */
+#define HS_NETS_6TO8 0x1C0u     /* {6,7,8} */
+#define HS_NETS_3TO8 0x1F8u     /* {3,...,8} */
+#define HS_NETS_POWEROF2 0x110u /* {4,8} */
+#define HS_NETS_EVEN 0x150u     /* {4,6,8} */
+#define HS_NETS_ODD 0x0A8u      /* {3,5,7} */
+
+/* ---------------------------------------------------------------- sorting */
+
+/* Workspace bytes for sorting n keys (with_values != 0: key/value pairs) with
+ * algorithm a.  Valid for every network set.  The workspace must be 16-byte
+ * aligned; it holds a ping-pong copy of the keys (and values) plus
+ * partition indices. */
+HS_API size_t hs_sort_workspace_bytes(size_t n, int with_values, hs_algo a);
+
+/* Sorts d_keys[0..n-1] ascending in place (Algorithm 1 for HS_ALGO_MERGE,
+ * Algorithm 2 for HS_ALGO_QUICK) with the network set s.
+ *   d_keys   device pointer, 4-byte aligned (16-byte alignment enables the
+ *            vectorised paths); may be NULL only when n == 0.
+ *   n        number of keys; 0 and 1 are no-ops.
+ *   d_ws     device workspace of ws_bytes >= hs_sort_workspace_bytes(n, 0, a).
+ * MERGE is fully asynchronous.  QUICK reads one small counter back to the
+ * host per partition level, so it synchronises `stream` internally and cannot
+ * be captured in a CUDA graph.
+ * Errors: HS_ERR_INVALID_ARG for a NULL/unaligned pointer with n > 0, an
+ * unknown algo, netset bits outside 3..8 or a short workspace;
+ * HS_ERR_CUDA if a launch fails. */
+HS_API hs_status hs_sort_i32(int32_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
+                      size_t ws_bytes, hs_stream_t stream);
+
+/* Stable key/value sort: d_keys and d_vals (n each) are permuted together so
+ * that keys ascend and equal keys keep their input order.  Networks compare
+ * (key, input position); merges take the left run on ties.
+ *   a must be HS_ALGO_MERGE: QUICK is not stable -> HS_ERR_UNSUPPORTED.
+ *   d_ws: ws_bytes >= hs_sort_workspace_bytes(n, 1, HS_ALGO_MERGE).
+ * Other conventions and errors as hs_sort_i32. */
+HS_API hs_status hs_sort_pairs_i32(int32_t *d_keys, int32_t *d_vals, size_t n, hs_algo a,
+                            hs_netset s, void *d_ws, size_t ws_bytes, hs_stream_t stream);
+
+/* Host-buffer form, for callers whose keys live in host memory: copies
+ * h_keys to the device, sorts them as hs_sort_i32 does, copies the result
+ * back into h_keys and waits for `stream` before returning (synchronous).
+ * Pinned host memory makes the copies faster; pageable memory also works.
+ *   d_ws: ws_bytes >= hs_sort_host_workspace_bytes(n, a); it holds the
+ *   device copy of the keys followed by the sort workspace. */
+HS_API size_t hs_sort_host_workspace_bytes(size_t n, hs_algo a);
+HS_API hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
+                           size_t ws_bytes, hs_stream_t stream);
+
+/* ------------------------------------------------------- errors, counters */
+
+HS_API const char *hs_status_str(hs_status st);
+/* Message of the last failing call on this thread ("" if none). */
+HS_API const char *hs_last_error(void);
+/* Library version string. */
+HS_API const char *hs_version(void);
+
+/* Number of kernels this library has launched in this process. */
+HS_API uint64_t hs_launch_count(void);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * each launch while enabled (off by default; it adds two event records per
+ * launch).  hs_prof_read waits for the recorded events, then returns the
+ * launches and summed milliseconds of the kernel named `kernel` since the
+ * last reset; unknown names give 0 launches. */
+HS_API void hs_prof_enable(int on);
+HS_API void hs_prof_reset(void);
+HS_API hs_status hs_prof_read(const char *kernel, uint64_t *launches, double *total_ms);
+
+/* --------------------------------------------------------- host checking */
+
+/* The device networks compiled for the host, for exhaustive CPU checks of
+ * the comparator lists the kernels use.  hs_network_pairs writes up to cap
+ * (lo, hi) pairs of the size-m network and returns its comparator count
+ * (-1 if m is outside 2..8); hs_network_apply sorts a[0..m-1] with it. */
+HS_API int hs_network_pairs(int m, int *pairs, int cap);
+HS_API int hs_network_apply(int m, int32_t *a);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSORT_H */

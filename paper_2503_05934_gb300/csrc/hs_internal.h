@@ -1,0 +1,66 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/hsort.h"
+
+namespace hs {
+
+// Kernel ids for launch counting and the optional per-kernel event timing.
+enum KernelId {
+    K_BLOCKSORT_KEYS = 0,
+    K_BLOCKSORT_PAIRS,
+    K_MERGE_PARTITION,
+    K_MERGE_KEYS,
+    K_MERGE_PAIRS,
+    K_QS_PLAN,
+    K_QS_COUNT,
+    K_QS_SCAN,
+    K_QS_SCATTER,
+    K_QS_SMALL,
+    K_SEG_CLASSIFY,
+    K_SEG_SORT,
+    K_NOALLOC,
+    K_COUNT
+};
+const char *kernel_name(int id);
+
+// Sets the thread-local error message and returns st.
+hs_status fail(hs_status st, const std::string &msg);
+hs_status fail_cuda(cudaError_t e, const char *what);
+void clear_error();
+
+// Brackets one launch: counts it and, when timing is on, records events on
+// `stream` around it.  Usage: auto t = launch_begin(id, s); <<<...>>>;
+// st = launch_end(t).
+struct LaunchToken {
+    int id;
+    cudaStream_t stream;
+    cudaEvent_t ev_a, ev_b;  // non-null while per-kernel timing is on
+};
+LaunchToken launch_begin(int id, cudaStream_t stream);
+hs_status launch_end(const LaunchToken &t);
+
+// Validation shared by the entry points.
+inline bool netset_ok(hs_netset s) { return (s & ~0x1F8u) == 0; }
+inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per
+// device (the attribute is per function and device).
+hs_status ensure_smem(const void *func, int bytes);
+
+// Merge path internals exposed to the other translation units.
+size_t merge_workspace_bytes(size_t n, int with_values);
+hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, void *d_ws,
+                     size_t ws_bytes, cudaStream_t st);
+
+size_t quick_workspace_bytes(size_t n);
+hs_status quick_sort(int32_t *d_keys, size_t n, hs_netset s, void *d_ws, size_t ws_bytes,
+                     cudaStream_t st);
+
+}  // namespace hs

@@ -1,0 +1,131 @@
+// Host planner of the merge path (Algorithm 1 on the GPU): one block-sort
+// launch, then per global level a partition launch and a merge launch,
+// ping-ponging between the caller's array and the workspace so that the last
+// level lands in the caller's array.
+#include "hs_internal.h"
+#include "hs_merge_kernels.cuh"
+
+namespace hs {
+
+// Block sort: 1024 threads, one leaf of L keys each -> tiles of 1024*L keys
+// (8192 for the {6,7,8} set).  Merge levels: 256 threads x 16 keys (keys) or
+// 256 x 8 (pairs) per output tile.
+constexpr int BS_NT = 1024;
+constexpr int MK_NT = 256, MK_E = 16;
+constexpr int MP_NT = 256, MP_E = 8;
+
+// Output tiles per pass are at most n/TO + n/(2T) + 1 <= n/1024 + 2 for the
+// smallest TO (2048) and tile (1024); one more entry closes the last tile.
+static size_t partition_entries(size_t n) { return n / 1024 + 8; }
+
+size_t merge_workspace_bytes(size_t n, int with_values) {
+    size_t kb = align_up(n * sizeof(int32_t), 256);
+    return kb + (with_values ? kb : 0) + align_up(partition_entries(n) * sizeof(int64_t), 256);
+}
+
+template <int L, bool PAIRS>
+static hs_status launch_blocksort_t(const int32_t *kin, int32_t *kout, const int32_t *vin,
+                                    int32_t *vout, int64_t n, hs_netset s, int vec,
+                                    cudaStream_t st) {
+    constexpr int T = BS_NT * L;
+    const int smem = blocksort_smem_words<BS_NT, L>() * (int)sizeof(int32_t) * (PAIRS ? 2 : 1);
+    auto kern = k_blocksort<BS_NT, L, PAIRS>;
+    hs_status r = ensure_smem((const void *)kern, smem);
+    if (r != HS_OK) return r;
+    const int64_t grid = (n + T - 1) / T;
+    LaunchToken t = launch_begin(PAIRS ? K_BLOCKSORT_PAIRS : K_BLOCKSORT_KEYS, st);
+    kern<<<(unsigned)grid, BS_NT, smem, st>>>(kin, kout, vin, vout, n, s, vec);
+    return launch_end(t);
+}
+
+template <bool PAIRS>
+static hs_status launch_blocksort(int L, const int32_t *kin, int32_t *kout, const int32_t *vin,
+                                  int32_t *vout, int64_t n, hs_netset s, int vec, cudaStream_t st) {
+    switch (L) {
+        case 1: return launch_blocksort_t<1, PAIRS>(kin, kout, vin, vout, n, s, vec, st);
+        case 3: return launch_blocksort_t<3, PAIRS>(kin, kout, vin, vout, n, s, vec, st);
+        case 4: return launch_blocksort_t<4, PAIRS>(kin, kout, vin, vout, n, s, vec, st);
+        case 5: return launch_blocksort_t<5, PAIRS>(kin, kout, vin, vout, n, s, vec, st);
+        case 6: return launch_blocksort_t<6, PAIRS>(kin, kout, vin, vout, n, s, vec, st);
+        case 7: return launch_blocksort_t<7, PAIRS>(kin, kout, vin, vout, n, s, vec, st);
+        case 8: return launch_blocksort_t<8, PAIRS>(kin, kout, vin, vout, n, s, vec, st);
+    }
+    return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
+}
+
+template <int NT, int E, bool PAIRS>
+static hs_status launch_merge_level(const int32_t *kin, int32_t *kout, const int32_t *vin,
+                                    int32_t *vout, int64_t n, int64_t w, int64_t *part, int vec,
+                                    cudaStream_t st) {
+    constexpr int TO = NT * E;
+    const int64_t span = 2 * w;
+    const int64_t ngroups = (n + span - 1) / span;
+    const int64_t tpg = (span + TO - 1) / TO;
+    const int64_t last = n - (ngroups - 1) * span;
+    const int64_t nblocks = (ngroups - 1) * tpg + (last + TO - 1) / TO;
+
+    LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
+    k_merge_partition<<<(unsigned)((nblocks + 255) / 256), 256, 0, st>>>(kin, n, w, TO, (int)tpg,
+                                                                         nblocks, part);
+    hs_status r = launch_end(t);
+    if (r != HS_OK) return r;
+
+    const int smem = merge_smem_words<NT, E>() * (int)sizeof(int32_t) * (PAIRS ? 2 : 1);
+    auto kern = k_merge_pass<NT, E, PAIRS>;
+    r = ensure_smem((const void *)kern, smem);
+    if (r != HS_OK) return r;
+    t = launch_begin(PAIRS ? K_MERGE_PAIRS : K_MERGE_KEYS, st);
+    kern<<<(unsigned)nblocks, NT, smem, st>>>(kin, kout, vin, vout, n, w, part, (int)tpg, vec);
+    return launch_end(t);
+}
+
+hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, void *d_ws,
+                     size_t ws_bytes, cudaStream_t st) {
+    const bool pairs = d_vals != nullptr;
+    const int64_t n = (int64_t)n_;
+    const int L = leaf_size(s);
+    const int64_t T = (int64_t)BS_NT * L;
+    int passes = 0;
+    for (int64_t w = T; w < n; w *= 2) ++passes;
+
+    int32_t *kbuf = nullptr, *vbuf = nullptr;
+    int64_t *part = nullptr;
+    if (passes > 0) {
+        if (!d_ws || ws_bytes < merge_workspace_bytes(n_, pairs))
+            return fail(HS_ERR_INVALID_ARG, "merge sort: workspace smaller than hs_sort_workspace_bytes");
+        if (!aligned(d_ws, 16)) return fail(HS_ERR_INVALID_ARG, "merge sort: workspace not 16-byte aligned");
+        char *p = static_cast<char *>(d_ws);
+        size_t kb = align_up(n_ * sizeof(int32_t), 256);
+        kbuf = reinterpret_cast<int32_t *>(p);
+        p += kb;
+        if (pairs) {
+            vbuf = reinterpret_cast<int32_t *>(p);
+            p += kb;
+        }
+        part = reinterpret_cast<int64_t *>(p);
+    }
+    const int vec = aligned(d_keys, 16) && (!pairs || aligned(d_vals, 16)) ? 1 : 0;
+
+    // Land the last level in the caller's array: with an even number of
+    // global levels the block sort writes in place.
+    int32_t *kcur = (passes % 2 == 0) ? d_keys : kbuf;
+    int32_t *vcur = pairs ? ((passes % 2 == 0) ? d_vals : vbuf) : nullptr;
+    int32_t *kalt = (kcur == d_keys) ? kbuf : d_keys;
+    int32_t *valt = pairs ? ((vcur == d_vals) ? vbuf : d_vals) : nullptr;
+
+    hs_status r = pairs ? launch_blocksort<true>(L, d_keys, kcur, d_vals, vcur, n, s, vec, st)
+                        : launch_blocksort<false>(L, d_keys, kcur, nullptr, nullptr, n, s, vec, st);
+    if (r != HS_OK) return r;
+
+    for (int64_t w = T; w < n; w *= 2) {
+        r = pairs ? launch_merge_level<MP_NT, MP_E, true>(kcur, kalt, vcur, valt, n, w, part, vec, st)
+                  : launch_merge_level<MK_NT, MK_E, false>(kcur, kalt, nullptr, nullptr, n, w, part,
+                                                           vec, st);
+        if (r != HS_OK) return r;
+        std::swap(kcur, kalt);
+        std::swap(vcur, valt);
+    }
+    return HS_OK;
+}
+
+}  // namespace hs

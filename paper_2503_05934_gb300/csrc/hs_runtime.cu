@@ -1,0 +1,254 @@
+// Library runtime: error strings, launch counting, optional per-kernel event
+// timing, the top-level entry points and the host build of the networks.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "hs_internal.h"
+#include "hs_networks.cuh"
+
+namespace hs {
+
+static const char *const kKernelNames[K_COUNT] = {
+    "blocksort_keys", "blocksort_pairs", "merge_partition", "merge_keys",
+    "merge_pairs",    "qs_plan",         "qs_count",        "qs_scan",
+    "qs_scatter",     "qs_small",        "seg_classify",    "seg_sort",
+    "noalloc_sort"};
+
+const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kKernelNames[id] : "?"; }
+
+static thread_local std::string t_last_error;
+
+hs_status fail(hs_status st, const std::string &msg) {
+    t_last_error = msg;
+    return st;
+}
+
+hs_status fail_cuda(cudaError_t e, const char *what) {
+    t_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+                   ")";
+    return HS_ERR_CUDA;
+}
+
+void clear_error() { t_last_error.clear(); }
+
+// ------------------------------------------------------------ launch stats
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<int> g_prof_on{0};
+
+struct ProfSlot {
+    int id;
+    cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static std::vector<ProfSlot> g_prof_pending;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_event_pool;
+static uint64_t g_prof_count[K_COUNT];
+static double g_prof_ms[K_COUNT];
+
+LaunchToken launch_begin(int id, cudaStream_t stream) {
+    LaunchToken t{id, stream, nullptr, nullptr};
+    if (g_prof_on.load(std::memory_order_relaxed)) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+        if (!g_event_pool.empty()) {
+            ev = g_event_pool.back();
+            g_event_pool.pop_back();
+        } else if (cudaEventCreate(&ev.first) != cudaSuccess ||
+                   cudaEventCreate(&ev.second) != cudaSuccess) {
+            cudaGetLastError();
+            return t;
+        }
+        cudaEventRecord(ev.first, stream);
+        t.ev_a = ev.first;
+        t.ev_b = ev.second;
+    }
+    return t;
+}
+
+hs_status launch_end(const LaunchToken &t) {
+    cudaError_t e = cudaGetLastError();
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (t.ev_a) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        cudaEventRecord(t.ev_b, t.stream);
+        g_prof_pending.push_back({t.id, t.ev_a, t.ev_b});
+    }
+    if (e != cudaSuccess) return fail_cuda(e, kernel_name(t.id));
+    return HS_OK;
+}
+
+static void prof_drain_locked() {
+    for (auto &s : g_prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(s.b) == cudaSuccess && cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
+            g_prof_count[s.id] += 1;
+            g_prof_ms[s.id] += ms;
+        } else {
+            cudaGetLastError();
+        }
+        g_event_pool.push_back({s.a, s.b});
+    }
+    g_prof_pending.clear();
+}
+
+hs_status ensure_smem(const void *func, int bytes) {
+    if (bytes <= 48 * 1024) return HS_OK;
+    // One flag per (function, device): the attribute is set per device.
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &d : done)
+        if (d.first == func && d.second == dev) return HS_OK;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute");
+    done.push_back({func, dev});
+    return HS_OK;
+}
+
+}  // namespace hs
+
+using namespace hs;
+
+extern "C" {
+
+const char *hs_status_str(hs_status st) {
+    switch (st) {
+        case HS_OK: return "HS_OK";
+        case HS_ERR_INVALID_ARG: return "HS_ERR_INVALID_ARG";
+        case HS_ERR_UNSUPPORTED: return "HS_ERR_UNSUPPORTED";
+        case HS_ERR_NO_MEMORY: return "HS_ERR_NO_MEMORY";
+        case HS_ERR_CUDA: return "HS_ERR_CUDA";
+        case HS_ERR_TIMEOUT: return "HS_ERR_TIMEOUT";
+        case HS_ERR_OVER_BUDGET: return "HS_ERR_OVER_BUDGET";
+    }
+    return "HS_ERR_UNKNOWN";
+}
+
+const char *hs_last_error(void) { return t_last_error.c_str(); }
+
+const char *hs_version(void) { return "hsort 0.1 (sm_103a)"; }
+
+uint64_t hs_launch_count(void) { return g_launches.load(); }
+
+void hs_prof_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+void hs_prof_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain_locked();
+    for (int i = 0; i < K_COUNT; ++i) {
+        g_prof_count[i] = 0;
+        g_prof_ms[i] = 0.0;
+    }
+}
+
+hs_status hs_prof_read(const char *kernel, uint64_t *launches, double *total_ms) {
+    if (!kernel || !launches || !total_ms) return fail(HS_ERR_INVALID_ARG, "hs_prof_read: NULL argument");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain_locked();
+    *launches = 0;
+    *total_ms = 0.0;
+    for (int i = 0; i < K_COUNT; ++i)
+        if (std::strcmp(kernel, kKernelNames[i]) == 0) {
+            *launches = g_prof_count[i];
+            *total_ms = g_prof_ms[i];
+        }
+    return HS_OK;
+}
+
+size_t hs_sort_workspace_bytes(size_t n, int with_values, hs_algo a) {
+    if (a == HS_ALGO_QUICK) return quick_workspace_bytes(n);
+    return merge_workspace_bytes(n, with_values);
+}
+
+static hs_status check_common(const void *d_keys, size_t n, hs_algo a, hs_netset s, const char *fn) {
+    if (a != HS_ALGO_MERGE && a != HS_ALGO_QUICK)
+        return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": unknown algo");
+    if (!netset_ok(s))
+        return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": netset has bits outside sizes 3..8");
+    if (n > 0 && !d_keys) return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": NULL keys with n > 0");
+    if (n > 0 && !aligned(d_keys, 4)) return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": keys not 4-byte aligned");
+    if (n > (size_t)INT64_MAX / 16) return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": n too large");
+    return HS_OK;
+}
+
+hs_status hs_sort_i32(int32_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
+                      size_t ws_bytes, hs_stream_t stream) {
+    clear_error();
+    hs_status st = check_common(d_keys, n, a, s, "hs_sort_i32");
+    if (st != HS_OK) return st;
+    if (n <= 1) return HS_OK;
+    if (a == HS_ALGO_QUICK) return quick_sort(d_keys, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
+    return merge_sort(d_keys, nullptr, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+hs_status hs_sort_pairs_i32(int32_t *d_keys, int32_t *d_vals, size_t n, hs_algo a, hs_netset s,
+                            void *d_ws, size_t ws_bytes, hs_stream_t stream) {
+    clear_error();
+    hs_status st = check_common(d_keys, n, a, s, "hs_sort_pairs_i32");
+    if (st != HS_OK) return st;
+    if (n > 0 && (!d_vals || !aligned(d_vals, 4)))
+        return fail(HS_ERR_INVALID_ARG, "hs_sort_pairs_i32: NULL or unaligned values with n > 0");
+    if (a == HS_ALGO_QUICK)
+        return fail(HS_ERR_UNSUPPORTED, "hs_sort_pairs_i32: quick sort is not stable; use HS_ALGO_MERGE");
+    if (n <= 1) return HS_OK;
+    return merge_sort(d_keys, d_vals, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+size_t hs_sort_host_workspace_bytes(size_t n, hs_algo a) {
+    return align_up(n * sizeof(int32_t), 256) + hs_sort_workspace_bytes(n, 0, a);
+}
+
+hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
+                           size_t ws_bytes, hs_stream_t stream) {
+    clear_error();
+    hs_status st = check_common(h_keys, n, a, s, "hs_sort_i32_host");
+    if (st != HS_OK) return st;
+    if (n <= 1) return HS_OK;
+    size_t need = hs_sort_host_workspace_bytes(n, a);
+    if (!d_ws || ws_bytes < need)
+        return fail(HS_ERR_INVALID_ARG, "hs_sort_i32_host: workspace smaller than hs_sort_host_workspace_bytes");
+    if (!aligned(d_ws, 16)) return fail(HS_ERR_INVALID_ARG, "hs_sort_i32_host: workspace not 16-byte aligned");
+    cudaStream_t cs = (cudaStream_t)stream;
+    int32_t *d_keys = static_cast<int32_t *>(d_ws);
+    size_t kb = align_up(n * sizeof(int32_t), 256);
+    cudaError_t e = cudaMemcpyAsync(d_keys, h_keys, n * sizeof(int32_t), cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return fail_cuda(e, "hs_sort_i32_host: host-to-device copy");
+    st = hs_sort_i32(d_keys, n, a, s, static_cast<char *>(d_ws) + kb, ws_bytes - kb, stream);
+    if (st != HS_OK) return st;
+    e = cudaMemcpyAsync(h_keys, d_keys, n * sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess) return fail_cuda(e, "hs_sort_i32_host: device-to-host copy");
+    e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return fail_cuda(e, "hs_sort_i32_host: stream synchronize");
+    return HS_OK;
+}
+
+int hs_network_pairs(int m, int *pairs, int cap) {
+    if (m < 2 || m > 8) return -1;
+    CountCE op;
+    op.pairs = pairs;
+    op.cap = cap;
+    network_dyn(m, op);
+    return op.n;
+}
+
+int hs_network_apply(int m, int32_t *a) {
+    if (m < 2 || m > 8 || !a) return -1;
+    KeyCE op{a};
+    switch (m) {  // a[] is a caller array of exactly m keys
+        case 2: network<2>(op); break;
+        case 3: network<3>(op); break;
+        case 4: network<4>(op); break;
+        case 5: network<5>(op); break;
+        case 6: network<6>(op); break;
+        case 7: network<7>(op); break;
+        case 8: network<8>(op); break;
+    }
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+"""GPU parity of the merge path (Algorithm 1) against the CPU oracle.
+
+Every case compares the CUDA result with the oracle element by element on
+the same seeded input; keys and stable pairs have a unique correct output, so
+the bar is bit-exact equality.  Full-size cases (2^28 keys, 2^27 pairs) are
+checked by properties that hold at any size plus oracle order statistics."""
+import numpy as np
+import pytest
+
+import hs_inputs as g
+import oracle
+from helpers import (check_sorted_permutation, check_stable_pairs_index_values, hs_module,
+                     to_dev)
+
+pytestmark = pytest.mark.gpu
+
+ALL_NETSETS = list(oracle.NETSETS)
+PAPER_NETSETS = ["none", "3To5", "6To8", "3To8"]
+
+
+@pytest.fixture(scope="module")
+def hs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return hs_module()
+
+
+def gpu_sort(hs, a, algo="merge", netset="6To8", offset=0):
+    import torch
+    t = to_dev(a, offset)
+    hs.hs_sort_i32(t, algo, netset)
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def gpu_sort_pairs(hs, k, v, netset="6To8", offset=0):
+    import torch
+    tk, tv = to_dev(k, offset), to_dev(v, offset)
+    hs.hs_sort_pairs_i32(tk, tv, "merge", netset)
+    torch.cuda.synchronize()
+    return tk.cpu().numpy(), tv.cpu().numpy()
+
+
+def test_ten_thousand_uniform_6to8(hs):
+    """n = 10,000 uniform over the int32 range, {6,7,8} leaves, against the
+    oracle's classical merge sort and its 6To8 hybrid."""
+    a = g.random_i32(10_000, g.config_seed(0))
+    out = gpu_sort(hs, a, "merge", "6To8")
+    assert np.array_equal(out, oracle.merge_sort(a, "none"))
+    assert np.array_equal(out, oracle.merge_sort(a, "6To8"))
+
+
+@pytest.mark.parametrize("n", [25_000, 100_000, 1_000_000])
+@pytest.mark.parametrize("dist", g.DISTS)
+@pytest.mark.parametrize("netset", PAPER_NETSETS)
+def test_paper_sizes_merge(hs, n, dist, netset):
+    a = g.keys(n, dist, g.config_seed(1, salt=n))
+    assert np.array_equal(gpu_sort(hs, a, "merge", netset), oracle.merge_sort(a, netset))
+
+
+def _edge_sizes(netset):
+    T = 1024 * max([k for k in range(3, 9) if (oracle.NETSETS[netset] >> k) & 1] or [1])
+    sizes = set(range(0, 18)) | {31, 32, 33, 1023, 1024, 1025}
+    sizes |= {T - 1, T, T + 1, 2 * T - 1, 2 * T, 2 * T + 1, 3 * T + 5, 4 * T - 3}
+    sizes |= {(1 << k) + d for k in (14, 15, 16, 17, 20) for d in (-1, 0, 1)}
+    sizes |= {4096 * 3 + 7, 70_001}
+    return sorted(sizes)
+
+
+@pytest.mark.parametrize("netset", ALL_NETSETS)
+def test_edge_sizes_all_netsets(hs, netset):
+    for n in _edge_sizes(netset):
+        a = g.random_i32(n, 77 + n)
+        assert np.array_equal(gpu_sort(hs, a, "merge", netset), np.sort(a)), n
+        assert np.array_equal(gpu_sort(hs, a, "merge", netset), oracle.merge_sort(a, netset)), n
+
+
+@pytest.mark.parametrize("netset", ["6To8", "none", "Odd", "3To5"])
+def test_degenerate_inputs(hs, netset):
+    n = 50_003
+    cases = {
+        "all_equal": np.full(n, 7, np.int32),
+        "all_max": np.full(n, 2**31 - 1, np.int32),
+        "extremes": np.where(g.random_i32(n, 1) > 0, 2**31 - 1, -2**31).astype(np.int32),
+        "reverse": np.arange(n, 0, -1, dtype=np.int32),
+        "sorted": np.arange(n, dtype=np.int32),
+        "three_values": (g.random_i32(n, 2) % 3).astype(np.int32),
+        "max_then_min": np.concatenate([np.full(n // 2, 2**31 - 1, np.int32),
+                                        np.full(n - n // 2, -2**31, np.int32)]),
+    }
+    for name, a in cases.items():
+        assert np.array_equal(gpu_sort(hs, a, "merge", netset), oracle.merge_sort(a, netset)), name
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_unaligned_pointer_scalar_path(hs, offset):
+    for n in [5, 8193, 100_000, 300_001]:
+        a = g.random_i32(n, offset * 1000 + n)
+        assert np.array_equal(gpu_sort(hs, a, "merge", "6To8", offset=offset), np.sort(a))
+
+
+def test_small_words_bruteforce(hs):
+    """Every word of length <= 8 over {0,1,2}, each offset into its own key
+    band and the whole set shuffled: one sort must rebuild every word's sorted
+    block, with heavy duplication inside each band."""
+    import itertools
+    words = []
+    for n in range(1, 9):
+        words += [np.array(t, np.int64) for t in itertools.product(range(3), repeat=n)]
+    flat = np.concatenate([(i << 2) + w for i, w in enumerate(words)]).astype(np.int64)
+    flat = (flat - (1 << 20)).astype(np.int32)
+    perm = np.random.default_rng(5).permutation(flat.size)
+    a = flat[perm]
+    for netset in ["6To8", "3To8", "none", "PowerOf2"]:
+        assert np.array_equal(gpu_sort(hs, a, "merge", netset), oracle.merge_sort(a, netset))
+
+
+@pytest.mark.parametrize("netset", ["6To8", "3To8", "none", "Even"])
+def test_pairs_against_oracle(hs, netset):
+    for n in [1, 2, 7, 8, 9, 1000, 8191, 8192, 8193, 100_000, 1_000_003]:
+        k, v = g.pair_keys_16bit(n, 900 + n)
+        k = (k % 97).astype(np.int32)  # heavy ties make stability visible
+        ko, vo = gpu_sort_pairs(hs, k, v, netset)
+        ek, ev = oracle.merge_sort_pairs(k, v, netset)
+        assert np.array_equal(ko, ek), n
+        assert np.array_equal(vo, ev), n
+
+
+def test_pairs_unaligned(hs):
+    k, v = g.pair_keys_16bit(200_001, 4)
+    ko, vo = gpu_sort_pairs(hs, k, v, "6To8", offset=1)
+    ek, ev = oracle.merge_sort_pairs(k, v, "6To8")
+    assert np.array_equal(ko, ek) and np.array_equal(vo, ev)
+
+
+def test_host_buffer_entry(hs):
+    import torch
+    a = g.random_i32(1_000_000, 31)
+    h = torch.from_numpy(a.copy()).pin_memory()
+    hs.hs_sort_i32_host(h, "merge", "6To8")
+    assert np.array_equal(h.numpy(), oracle.merge_sort(a, "6To8"))
+
+
+def test_workspace_reuse_and_launch_count(hs):
+    import torch
+    n = 1 << 20
+    ws = torch.empty(hs.hs_sort_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    before = hs.hs_launch_count()
+    for seed in range(3):
+        a = g.random_i32(n, seed)
+        t = to_dev(a)
+        hs.hs_sort_i32(t, "merge", "6To8", ws=ws)
+        torch.cuda.synchronize()
+        assert np.array_equal(t.cpu().numpy(), np.sort(a))
+    # 1 block sort + 2 launches per global level, 2^20 / 8192 = 2^7 -> 7 levels
+    assert hs.hs_launch_count() - before == 3 * (1 + 2 * 7)
+
+
+def test_profiling_counters(hs):
+    import torch
+    hs.hs_prof_reset()
+    hs.hs_prof_enable(True)
+    try:
+        t = to_dev(g.random_i32(1 << 18, 1))
+        hs.hs_sort_i32(t, "merge", "6To8")
+        torch.cuda.synchronize()
+        n_bs, ms_bs = hs.hs_prof_read("blocksort_keys")
+        n_mk, ms_mk = hs.hs_prof_read("merge_keys")
+    finally:
+        hs.hs_prof_enable(False)
+    assert n_bs == 1 and n_mk == 5 and ms_bs > 0 and ms_mk > 0
+
+
+def test_full_size_keys_2p28(hs):
+    """2^28 uniform int32 keys, {6,7,8}: the benchmark's workload and launch
+    configuration, checked by sortedness, multiset fingerprint and sampled
+    order statistics from the oracle."""
+    import torch
+    n = 1 << 28
+    a = g.random_i32(n, g.config_seed(2))
+    t = to_dev(a)
+    hs.hs_sort_i32(t, "merge", "6To8")
+    torch.cuda.synchronize()
+    out = t.cpu().numpy()
+    del t
+    check_sorted_permutation(a, out, samples=6)
+
+
+def test_full_size_pairs_2p27(hs):
+    """2^27 stable pairs, keys from 2^16 distinct values, value = index."""
+    import torch
+    n = 1 << 27
+    k, v = g.pair_keys_16bit(n, g.config_seed(2, salt=1))
+    tk, tv = to_dev(k), to_dev(v)
+    hs.hs_sort_pairs_i32(tk, tv, "merge", "6To8")
+    torch.cuda.synchronize()
+    ko, vo = tk.cpu().numpy(), tv.cpu().numpy()
+    del tk, tv
+    check_stable_pairs_index_values(k, ko, vo)
