@@ -137,6 +137,12 @@ HS_API void hs_prof_enable(int on);
 HS_API void hs_prof_reset(void);
 HS_API hs_status hs_prof_read(const char *kernel, uint64_t *launches, double *total_ms);
 
+/* Process-wide tuning knob.  "quick_max_levels": partition levels the quick
+ * path runs before its depth guard merge-sorts the segments still open
+ * (default -1 = automatic, 4*ceil(log2 n) + 16).  Unknown names return
+ * HS_ERR_INVALID_ARG. */
+HS_API hs_status hs_set_option(const char *name, int64_t value);
+
 /* --------------------------------------------------------- host checking */
 
 /* The device networks compiled for the host, for exhaustive CPU checks of

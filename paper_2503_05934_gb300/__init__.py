@@ -26,7 +26,7 @@ __all__ = [
     "NETSETS", "ALGOS", "HsortError", "lib", "netset_mask", "algo_id",
     "hs_sort_workspace_bytes", "hs_sort_i32", "hs_sort_pairs_i32",
     "hs_sort_host_workspace_bytes", "hs_sort_i32_host", "hs_launch_count",
-    "hs_prof_enable", "hs_prof_reset", "hs_prof_read", "hs_version",
+    "hs_prof_enable", "hs_prof_reset", "hs_prof_read", "hs_version", "hs_set_option",
 ]
 
 
@@ -130,6 +130,10 @@ def hs_prof_read(kernel: str) -> tuple[int, float]:
     ms = ctypes.c_double()
     check(lib().hs_prof_read(kernel.encode(), ctypes.byref(n), ctypes.byref(ms)))
     return int(n.value), float(ms.value)
+
+
+def hs_set_option(name: str, value: int) -> None:
+    check(lib().hs_set_option(name.encode(), int(value)))
 
 
 def hs_version() -> str:

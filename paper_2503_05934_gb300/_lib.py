@@ -36,6 +36,7 @@ SIGNATURES = {
     "hs_prof_reset": (None, []),
     "hs_prof_read": (_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64),
                             ctypes.POINTER(ctypes.c_double)]),
+    "hs_set_option": (_int, [ctypes.c_char_p, ctypes.c_int64]),
     "hs_network_pairs": (_int, [_int, ctypes.POINTER(ctypes.c_int), _int]),
     "hs_network_apply": (_int, [_int, _c_i32p]),
 }

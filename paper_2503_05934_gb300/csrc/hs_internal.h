@@ -19,7 +19,7 @@ enum KernelId {
     K_MERGE_PAIRS,
     K_QS_PLAN,
     K_QS_COUNT,
-    K_QS_SCAN,
+    K_QS_FILL,
     K_QS_SCATTER,
     K_QS_SMALL,
     K_SEG_CLASSIFY,
@@ -59,7 +59,13 @@ size_t merge_workspace_bytes(size_t n, int with_values);
 hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, void *d_ws,
                      size_t ws_bytes, cudaStream_t st);
 
+// Block sort of [0, n) in tiles of 1024*L keys (the merge path's first pass;
+// the whole sort when n fits one tile).
+hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
+                           int vec, cudaStream_t st);
+
 size_t quick_workspace_bytes(size_t n);
+void quick_set_max_levels(int64_t v);
 hs_status quick_sort(int32_t *d_keys, size_t n, hs_netset s, void *d_ws, size_t ws_bytes,
                      cudaStream_t st);
 

@@ -53,6 +53,11 @@ static hs_status launch_blocksort(int L, const int32_t *kin, int32_t *kout, cons
     return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
 }
 
+hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
+                           int vec, cudaStream_t st) {
+    return launch_blocksort<false>(L, kin, kout, nullptr, nullptr, n, s, vec, st);
+}
+
 template <int NT, int E, bool PAIRS>
 static hs_status launch_merge_level(const int32_t *kin, int32_t *kout, const int32_t *vin,
                                     int32_t *vout, int64_t n, int64_t w, int64_t *part, int vec,

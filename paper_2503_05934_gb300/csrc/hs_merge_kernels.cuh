@@ -102,23 +102,20 @@ constexpr int blocksort_smem_words() {
 }
 
 // ---------------------------------------------------------------------------
-// Block sort.  Tile t covers keys [t*NT*L, (t+1)*NT*L); the last tile may be
-// short and is padded with sentinels (never written back).  kin/kout may
-// alias: each CTA reads its whole tile into shared memory before writing.
+// Block sort of one tile of cnt <= NT*L keys (kin -> kout, which may alias;
+// values ride along when PAIRS).  Positions past cnt are padded with
+// sentinels and never written back.  Merge levels stop once one run covers
+// every live key: the remaining runs hold only sentinels.
 template <int NT, int L, bool PAIRS>
-__global__ void __launch_bounds__(NT)
-    k_blocksort(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
-                int64_t n, uint32_t netset, int vec) {
+HS_DEV void block_sort_tile(const int32_t *kin, int32_t *kout, const int32_t *vin,
+                            int32_t *vout, int cnt, uint32_t netset, bool vec, int32_t *smem) {
     constexpr int T = NT * L;
     constexpr int SZ = blocksort_smem_words<NT, L>();
-    extern __shared__ int32_t smem[];
     int32_t *sk = smem;
     int32_t *sv = smem + SZ;
 
-    const int64_t base = (int64_t)blockIdx.x * T;
-    const int cnt = (int)((n - base) < T ? (n - base) : T);
-    load_tile_padded<T, NT>(kin + base, cnt, sk, vec, kKeyMax);
-    if constexpr (PAIRS) load_tile_padded<T, NT>(vin + base, cnt, sv, vec, 0);
+    load_tile_padded<T, NT>(kin, cnt, sk, vec, kKeyMax);
+    if constexpr (PAIRS) load_tile_padded<T, NT>(vin, cnt, sv, vec, 0);
     __syncthreads();
 
     const int my0 = threadIdx.x * L;
@@ -146,7 +143,7 @@ __global__ void __launch_bounds__(NT)
     }
 
     // Merge levels inside the tile: runs of w keys -> 2w keys.
-    for (int w = L; w < T; w *= 2) {
+    for (int w = L; w < T && w < cnt; w *= 2) {
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < L; ++j) {
@@ -168,8 +165,23 @@ __global__ void __launch_bounds__(NT)
         if constexpr (PAIRS) sv[pad32(my0 + j)] = v[j];
     }
     __syncthreads();
-    store_tile_padded<NT>(kout + base, cnt, sk, vec);
-    if constexpr (PAIRS) store_tile_padded<NT>(vout + base, cnt, sv, vec);
+    store_tile_padded<NT>(kout, cnt, sk, vec);
+    if constexpr (PAIRS) store_tile_padded<NT>(vout, cnt, sv, vec);
+}
+
+// Block sort.  Tile t covers keys [t*NT*L, (t+1)*NT*L); the last tile may be
+// short.  kin/kout may alias: each CTA reads its whole tile into shared
+// memory before writing.
+template <int NT, int L, bool PAIRS>
+__global__ void __launch_bounds__(NT)
+    k_blocksort(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
+                int64_t n, uint32_t netset, int vec) {
+    constexpr int T = NT * L;
+    extern __shared__ int32_t smem[];
+    const int64_t base = (int64_t)blockIdx.x * T;
+    const int cnt = (int)((n - base) < T ? (n - base) : T);
+    block_sort_tile<NT, L, PAIRS>(kin + base, kout + base, PAIRS ? vin + base : nullptr,
+                                  PAIRS ? vout + base : nullptr, cnt, netset, vec != 0, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -192,7 +204,7 @@ HS_DEV MergeGeom merge_geom(int64_t g, int64_t n, int64_t w) {
 }
 
 // part[b] = number of A elements before output tile b's first output.
-__global__ void k_merge_partition(const int32_t *in, int64_t n, int64_t w, int to, int tpg,
+static __global__ void k_merge_partition(const int32_t *in, int64_t n, int64_t w, int to, int tpg,
                                   int64_t nblocks, int64_t *part) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblocks) return;

@@ -1,13 +1,452 @@
-// Quick path (Algorithm 2 on the GPU).  Placeholder until the 3-way
-// partition kernels land: reports the request as unsupported.
+// Quick path: the GPU form of Algorithm 2 (Optimized Quick Sort with Sorting
+// Networks).
+//
+// Each level partitions every live segment larger than one block-sort tile
+// around its median-of-three pivot (MedianOfThree in Algorithm 2: first,
+// middle and last key).  The GPU partition is 3-way (<, =, > pivot) rather
+// than Hoare's 2-way scan: keys equal to the pivot are final at once, which
+// also ends all-equal segments.  Segments of at most one tile are finished
+// by the block sort, whose leaves are the network base cases.
+//
+// Per level (all segments at once, chunks of QS_C keys):
+//   k_qs_pivot    median of three per segment, zero its counters
+//   k_qs_count    per chunk: #<, #= ; atomically summed per segment
+//   k_qs_scatter  per chunk: reserve ranges with atomic cursors, write < and >
+//                 keys to the other buffer (coalesced runs per warp)
+//   k_qs_fill     per chunk: write the pivot over the chunk's share of the
+//                 segment's = range in the caller's array (final positions)
+//   k_qs_next     children -> next level (> tile) or small list (<= tile)
+//   k_qs_small    block sort of each small child into the caller's array
+//   k_qs_chunkmap chunk -> segment map of the next level
+// The host reads three counters back per level to size the next launches.
+#include <algorithm>
+#include <vector>
+
 #include "hs_internal.h"
+#include "hs_merge_kernels.cuh"
 
 namespace hs {
 
-size_t quick_workspace_bytes(size_t n) { return merge_workspace_bytes(n, 0); }
+constexpr int QS_NT = 256;
+constexpr int QS_IPT = 32;
+constexpr int QS_C = QS_NT * QS_IPT;  // keys per partition chunk
+constexpr int QS_BS_NT = 1024;        // small-segment sort: tile = 1024 * leaf
 
-hs_status quick_sort(int32_t *, size_t, hs_netset, void *, size_t, cudaStream_t) {
-    return fail(HS_ERR_UNSUPPORTED, "hs_sort_i32: HS_ALGO_QUICK is not built yet");
+struct QSeg {
+    int64_t begin, end, chunk0;
+    unsigned long long lt, eq;                  // totals from the count pass
+    unsigned long long cur_lt, cur_eq, cur_gt;  // reservation cursors
+    int32_t buf, pivot;                         // buf 0: caller's array, 1: workspace
+};
+
+struct QSmall {
+    int64_t begin, end;
+    int32_t buf, pad;
+};
+
+struct QCounters {
+    unsigned long long nseg, nchunks, nsmall, overflow;
+};
+
+static int64_t qs_option_max_levels = -1;  // < 0: automatic
+
+HS_DEV const int32_t *qs_src(const QSeg &s, const int32_t *X, const int32_t *Y) {
+    return s.buf ? Y : X;
+}
+
+__global__ void k_qs_init(QSeg *segs, int32_t *chunk_seg, int64_t n, int64_t nchunks) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        QSeg s{};
+        s.begin = 0;
+        s.end = n;
+        s.chunk0 = 0;
+        s.buf = 0;
+        segs[0] = s;
+    }
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x)
+        chunk_seg[c] = 0;
+}
+
+__global__ void k_qs_pivot(QSeg *segs, int64_t nseg, const int32_t *X, const int32_t *Y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nseg) return;
+    QSeg &s = segs[i];
+    const int32_t *src = qs_src(s, X, Y);
+    const int64_t len = s.end - s.begin;
+    const int32_t a = src[s.begin], b = src[s.begin + (len - 1) / 2], c = src[s.end - 1];
+    s.pivot = hs_max(hs_min(a, b), hs_min(hs_max(a, b), c));  // median of three
+    s.lt = s.eq = 0;
+    s.cur_lt = s.cur_eq = s.cur_gt = 0;
+}
+
+struct ChunkView {
+    int64_t start;
+    int len;
+    int s;
+};
+
+HS_DEV ChunkView chunk_view(const QSeg *segs, const int32_t *chunk_seg, int64_t c) {
+    ChunkView v;
+    v.s = chunk_seg[c];
+    const QSeg &sg = segs[v.s];
+    v.start = sg.begin + (c - sg.chunk0) * (int64_t)QS_C;
+    int64_t rest = sg.end - v.start;
+    v.len = (int)(rest < QS_C ? rest : QS_C);
+    return v;
+}
+
+template <int NT>
+HS_DEV int block_sum(int x, int *red) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    int tot = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) tot += red[w];
+    return tot;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(QS_NT)
+    k_qs_count(QSeg *segs, const int32_t *chunk_seg, const int32_t *X, const int32_t *Y) {
+    __shared__ int red[2][QS_NT / 32];
+    const ChunkView cv = chunk_view(segs, chunk_seg, blockIdx.x);
+    const QSeg &sg = segs[cv.s];
+    const int32_t p = sg.pivot;
+    const int32_t *src = qs_src(sg, X, Y) + cv.start;
+    int lt = 0, eq = 0;
+#pragma unroll 8
+    for (int j = 0; j < QS_IPT; ++j) {
+        int i = j * QS_NT + threadIdx.x;
+        if (i < cv.len) {
+            int32_t k = ld_stream(src + i);
+            lt += k < p;
+            eq += k == p;
+        }
+    }
+    int tlt = block_sum<QS_NT>(lt, red[0]);
+    int teq = block_sum<QS_NT>(eq, red[1]);
+    if (threadIdx.x == 0) {
+        if (tlt) atomicAdd(&segs[cv.s].lt, (unsigned long long)tlt);
+        if (teq) atomicAdd(&segs[cv.s].eq, (unsigned long long)teq);
+    }
+}
+
+__global__ void __launch_bounds__(QS_NT)
+    k_qs_scatter(QSeg *segs, const int32_t *chunk_seg, const int32_t *X, const int32_t *Y,
+                 int32_t *Xw, int32_t *Yw) {
+    constexpr int NW = QS_NT / 32;
+    constexpr int PER_LANE = QS_IPT * NW / 32;  // (j, warp) entries per lane in the scan
+    __shared__ int s_cnt[2][QS_IPT * NW];       // 0: <, 1: >  (index j*NW + warp)
+    __shared__ int s_tot[2];
+    __shared__ unsigned long long s_base[2];
+
+    const ChunkView cv = chunk_view(segs, chunk_seg, blockIdx.x);
+    const QSeg &sg = segs[cv.s];
+    const int32_t p = sg.pivot;
+    const int32_t *src = qs_src(sg, X, Y) + cv.start;
+    int32_t *dst = sg.buf ? Xw : Yw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+
+    int32_t k[QS_IPT];
+#pragma unroll
+    for (int j = 0; j < QS_IPT; ++j) {
+        int i = j * QS_NT + threadIdx.x;
+        k[j] = i < cv.len ? ld_stream(src + i) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < QS_IPT; ++j) {
+        bool valid = j * QS_NT + (int)threadIdx.x < cv.len;
+        unsigned ml = __ballot_sync(0xffffffffu, valid && k[j] < p);
+        unsigned mg = __ballot_sync(0xffffffffu, valid && k[j] > p);
+        if (lane == 0) {
+            s_cnt[0][j * NW + warp] = __popc(ml);
+            s_cnt[1][j * NW + warp] = __popc(mg);
+        }
+    }
+    __syncthreads();
+    // Exclusive scan of the per-(slice, warp) counts in slice-major order:
+    // warp 0 scans "<", warp 1 scans ">".
+    if (warp < 2) {
+        int *c = s_cnt[warp];
+        int loc[PER_LANE];
+        int sum = 0;
+#pragma unroll
+        for (int e = 0; e < PER_LANE; ++e) {
+            loc[e] = c[lane * PER_LANE + e];
+            sum += loc[e];
+        }
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int e = 0; e < PER_LANE; ++e) {
+            c[lane * PER_LANE + e] = run;
+            run += loc[e];
+        }
+        if (lane == 31) s_tot[warp] = incl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        QSeg &sw = segs[cv.s];
+        s_base[0] = s_tot[0] ? atomicAdd(&sw.cur_lt, (unsigned long long)s_tot[0]) : 0ull;
+        s_base[1] = s_tot[1] ? atomicAdd(&sw.cur_gt, (unsigned long long)s_tot[1]) : 0ull;
+    }
+    __syncthreads();
+    const int64_t lt_base = sg.begin + (int64_t)s_base[0];
+    const int64_t gt_base = sg.begin + (int64_t)sg.lt + (int64_t)sg.eq + (int64_t)s_base[1];
+#pragma unroll
+    for (int j = 0; j < QS_IPT; ++j) {
+        bool valid = j * QS_NT + (int)threadIdx.x < cv.len;
+        bool is_lt = valid && k[j] < p;
+        bool is_gt = valid && k[j] > p;
+        unsigned ml = __ballot_sync(0xffffffffu, is_lt);
+        unsigned mg = __ballot_sync(0xffffffffu, is_gt);
+        if (is_lt) dst[lt_base + s_cnt[0][j * NW + warp] + __popc(ml & below)] = k[j];
+        if (is_gt) dst[gt_base + s_cnt[1][j * NW + warp] + __popc(mg & below)] = k[j];
+    }
+}
+
+// The = range of a segment is final: write the pivot over the part of it that
+// falls inside this chunk's index range.
+__global__ void k_qs_fill(const QSeg *segs, const int32_t *chunk_seg, int32_t *X) {
+    const ChunkView cv = chunk_view(segs, chunk_seg, blockIdx.x);
+    const QSeg &sg = segs[cv.s];
+    const int64_t e0 = sg.begin + (int64_t)sg.lt, e1 = e0 + (int64_t)sg.eq;
+    const int64_t lo = hs_max(e0, cv.start), hi = hs_min(e1, cv.start + cv.len);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) X[i] = sg.pivot;
+}
+
+HS_DEV void qs_emit(int64_t b, int64_t e, int32_t buf, int64_t tile, QSeg *next, int64_t cap_seg,
+                    QSmall *small, int64_t cap_small, QCounters *ctr) {
+    const int64_t len = e - b;
+    if (len <= 0) return;
+    if (len > tile) {
+        unsigned long long idx = atomicAdd(&ctr->nseg, 1ull);
+        unsigned long long nch = (unsigned long long)((len + QS_C - 1) / QS_C);
+        unsigned long long c0 = atomicAdd(&ctr->nchunks, nch);
+        if ((int64_t)idx >= cap_seg) {
+            atomicExch(&ctr->overflow, 1ull);
+            return;
+        }
+        QSeg s{};
+        s.begin = b;
+        s.end = e;
+        s.chunk0 = (int64_t)c0;
+        s.buf = buf;
+        next[idx] = s;
+    } else {
+        unsigned long long idx = atomicAdd(&ctr->nsmall, 1ull);
+        if ((int64_t)idx >= cap_small) {
+            atomicExch(&ctr->overflow, 1ull);
+            return;
+        }
+        QSmall s{b, e, buf, 0};
+        small[idx] = s;
+    }
+}
+
+__global__ void k_qs_next(const QSeg *segs, int64_t nseg, int64_t tile, QSeg *next,
+                          int64_t cap_seg, QSmall *small, int64_t cap_small, QCounters *ctr) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nseg) return;
+    const QSeg s = segs[i];
+    const int32_t dbuf = s.buf ^ 1;
+    const int64_t lt_end = s.begin + (int64_t)s.lt;
+    const int64_t gt_begin = lt_end + (int64_t)s.eq;
+    qs_emit(s.begin, lt_end, dbuf, tile, next, cap_seg, small, cap_small, ctr);
+    qs_emit(gt_begin, s.end, dbuf, tile, next, cap_seg, small, cap_small, ctr);
+}
+
+__global__ void k_qs_chunkmap(const QSeg *segs, int32_t *chunk_seg, int64_t cap_chunk) {
+    const QSeg &s = segs[blockIdx.x];
+    const int64_t nch = (s.end - s.begin + QS_C - 1) / QS_C;
+    for (int64_t c = threadIdx.x; c < nch; c += blockDim.x)
+        if (s.chunk0 + c < cap_chunk) chunk_seg[s.chunk0 + c] = (int32_t)blockIdx.x;
+}
+
+template <int L>
+__global__ void __launch_bounds__(QS_BS_NT)
+    k_qs_small(const QSmall *small, const int32_t *X, const int32_t *Y, int32_t *Xw,
+               uint32_t netset) {
+    extern __shared__ int32_t smem[];
+    const QSmall s = small[blockIdx.x];
+    const int32_t *src = s.buf ? Y : X;
+    block_sort_tile<QS_BS_NT, L, false>(src + s.begin, Xw + s.begin, nullptr, nullptr,
+                                        (int)(s.end - s.begin), netset, false, smem);
+}
+
+// ---------------------------------------------------------------- host side
+
+struct QLayout {
+    size_t y, part, seg_a, seg_b, chunk_a, chunk_b, small, ctr, total;
+    int64_t cap_seg, cap_chunk, cap_small;
+};
+
+static QLayout qs_layout(size_t n) {
+    QLayout q{};
+    // Segments of one level are disjoint and longer than the smallest tile
+    // (1024 keys), so a level holds at most n/1024 of them; each contributes
+    // at most one partial chunk; each yields at most two small children.
+    q.cap_seg = (int64_t)(n / 1024 + 2);
+    q.cap_chunk = (int64_t)(n / QS_C) + q.cap_seg + 2;
+    q.cap_small = 2 * q.cap_seg + 2;
+    size_t off = 0;
+    q.y = off;
+    off += align_up(n * sizeof(int32_t), 256);
+    q.part = off;  // merge partitions for the depth fallback (contiguous after y)
+    off += align_up(merge_workspace_bytes(n, 0) - align_up(n * sizeof(int32_t), 256), 256);
+    q.seg_a = off;
+    off += align_up((size_t)q.cap_seg * sizeof(QSeg), 256);
+    q.seg_b = off;
+    off += align_up((size_t)q.cap_seg * sizeof(QSeg), 256);
+    q.chunk_a = off;
+    off += align_up((size_t)q.cap_chunk * sizeof(int32_t), 256);
+    q.chunk_b = off;
+    off += align_up((size_t)q.cap_chunk * sizeof(int32_t), 256);
+    q.small = off;
+    off += align_up((size_t)q.cap_small * sizeof(QSmall), 256);
+    q.ctr = off;
+    off += 256;
+    q.total = off;
+    return q;
+}
+
+size_t quick_workspace_bytes(size_t n) { return qs_layout(n).total; }
+
+void quick_set_max_levels(int64_t v) { qs_option_max_levels = v; }
+
+template <int L>
+static hs_status launch_small_t(const QSmall *small, int64_t nsmall, const int32_t *X,
+                                const int32_t *Y, int32_t *Xw, hs_netset s, cudaStream_t st) {
+    const int smem = blocksort_smem_words<QS_BS_NT, L>() * (int)sizeof(int32_t);
+    auto kern = k_qs_small<L>;
+    hs_status r = ensure_smem((const void *)kern, smem);
+    if (r != HS_OK) return r;
+    LaunchToken t = launch_begin(K_QS_SMALL, st);
+    kern<<<(unsigned)nsmall, QS_BS_NT, smem, st>>>(small, X, Y, Xw, s);
+    return launch_end(t);
+}
+
+static hs_status launch_small(int L, const QSmall *small, int64_t nsmall, const int32_t *X,
+                              const int32_t *Y, int32_t *Xw, hs_netset s, cudaStream_t st) {
+    switch (L) {
+        case 1: return launch_small_t<1>(small, nsmall, X, Y, Xw, s, st);
+        case 3: return launch_small_t<3>(small, nsmall, X, Y, Xw, s, st);
+        case 4: return launch_small_t<4>(small, nsmall, X, Y, Xw, s, st);
+        case 5: return launch_small_t<5>(small, nsmall, X, Y, Xw, s, st);
+        case 6: return launch_small_t<6>(small, nsmall, X, Y, Xw, s, st);
+        case 7: return launch_small_t<7>(small, nsmall, X, Y, Xw, s, st);
+        case 8: return launch_small_t<8>(small, nsmall, X, Y, Xw, s, st);
+    }
+    return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
+}
+
+// Depth guard: segments still live after the level cap (adversarial inputs
+// for median-of-three) are moved into the caller's array and merge-sorted one
+// by one, with the workspace's key area as merge scratch.
+static hs_status qs_fallback(int32_t *X, int32_t *Y, const QSeg *d_segs, int64_t nseg,
+                             hs_netset s, void *merge_ws, size_t merge_ws_bytes, cudaStream_t st) {
+    std::vector<QSeg> h((size_t)nseg);
+    cudaError_t e = cudaMemcpyAsync(h.data(), d_segs, (size_t)nseg * sizeof(QSeg),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(e, "quick sort: reading segments");
+    for (const QSeg &g : h)
+        if (g.buf) {
+            e = cudaMemcpyAsync(X + g.begin, Y + g.begin, (size_t)(g.end - g.begin) * sizeof(int32_t),
+                                cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return fail_cuda(e, "quick sort: fallback copy");
+        }
+    for (const QSeg &g : h) {
+        hs_status r = merge_sort(X + g.begin, nullptr, (size_t)(g.end - g.begin), s, merge_ws,
+                                 merge_ws_bytes, st);
+        if (r != HS_OK) return r;
+    }
+    return HS_OK;
+}
+
+hs_status quick_sort(int32_t *d_keys, size_t n_, hs_netset s, void *d_ws, size_t ws_bytes,
+                     cudaStream_t st) {
+    const int64_t n = (int64_t)n_;
+    const int L = leaf_size(s);
+    const int64_t tile = (int64_t)QS_BS_NT * L;
+    const int vec = aligned(d_keys, 16) ? 1 : 0;
+    if (n <= tile) return blocksort_launch(L, d_keys, d_keys, n, s, vec, st);
+
+    const QLayout q = qs_layout(n_);
+    if (!d_ws || ws_bytes < q.total)
+        return fail(HS_ERR_INVALID_ARG, "quick sort: workspace smaller than hs_sort_workspace_bytes");
+    if (!aligned(d_ws, 16)) return fail(HS_ERR_INVALID_ARG, "quick sort: workspace not 16-byte aligned");
+    char *base = static_cast<char *>(d_ws);
+    int32_t *X = d_keys;
+    int32_t *Y = reinterpret_cast<int32_t *>(base + q.y);
+    QSeg *cur = reinterpret_cast<QSeg *>(base + q.seg_a);
+    QSeg *nxt = reinterpret_cast<QSeg *>(base + q.seg_b);
+    int32_t *ccur = reinterpret_cast<int32_t *>(base + q.chunk_a);
+    int32_t *cnxt = reinterpret_cast<int32_t *>(base + q.chunk_b);
+    QSmall *small = reinterpret_cast<QSmall *>(base + q.small);
+    QCounters *ctr = reinterpret_cast<QCounters *>(base + q.ctr);
+
+    int64_t nseg = 1, nchunks = (n + QS_C - 1) / QS_C;
+    LaunchToken t = launch_begin(K_QS_PLAN, st);
+    k_qs_init<<<(unsigned)std::min<int64_t>((nchunks + 255) / 256, 4096), 256, 0, st>>>(cur, ccur, n,
+                                                                                      nchunks);
+    hs_status r = launch_end(t);
+    if (r != HS_OK) return r;
+
+    int lg = 0;
+    while ((int64_t(1) << lg) < n) ++lg;
+    const int64_t max_levels = qs_option_max_levels >= 0 ? qs_option_max_levels : 4 * lg + 16;
+
+    for (int64_t level = 0; nseg > 0; ++level) {
+        if (level >= max_levels)
+            return qs_fallback(X, Y, cur, nseg, s, base + q.y,
+                               merge_workspace_bytes(n_, 0), st);
+        cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(QCounters), st);
+        if (e != cudaSuccess) return fail_cuda(e, "quick sort: counter reset");
+        const unsigned gseg = (unsigned)((nseg + 255) / 256);
+        t = launch_begin(K_QS_PLAN, st);
+        k_qs_pivot<<<gseg, 256, 0, st>>>(cur, nseg, X, Y);
+        if ((r = launch_end(t)) != HS_OK) return r;
+        t = launch_begin(K_QS_COUNT, st);
+        k_qs_count<<<(unsigned)nchunks, QS_NT, 0, st>>>(cur, ccur, X, Y);
+        if ((r = launch_end(t)) != HS_OK) return r;
+        t = launch_begin(K_QS_SCATTER, st);
+        k_qs_scatter<<<(unsigned)nchunks, QS_NT, 0, st>>>(cur, ccur, X, Y, X, Y);
+        if ((r = launch_end(t)) != HS_OK) return r;
+        t = launch_begin(K_QS_FILL, st);
+        k_qs_fill<<<(unsigned)nchunks, 256, 0, st>>>(cur, ccur, X);
+        if ((r = launch_end(t)) != HS_OK) return r;
+        t = launch_begin(K_QS_PLAN, st);
+        k_qs_next<<<gseg, 256, 0, st>>>(cur, nseg, tile, nxt, q.cap_seg, small, q.cap_small, ctr);
+        if ((r = launch_end(t)) != HS_OK) return r;
+
+        QCounters h{};
+        e = cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail_cuda(e, "quick sort: reading level counters");
+        if (h.overflow || (int64_t)h.nchunks > q.cap_chunk)
+            return fail(HS_ERR_CUDA, "quick sort: internal work-list overflow");
+        if (h.nsmall > 0 &&
+            (r = launch_small(L, small, (int64_t)h.nsmall, X, Y, X, s, st)) != HS_OK)
+            return r;
+        nseg = (int64_t)h.nseg;
+        nchunks = (int64_t)h.nchunks;
+        if (nseg > 0) {
+            t = launch_begin(K_QS_PLAN, st);
+            k_qs_chunkmap<<<(unsigned)nseg, 256, 0, st>>>(nxt, cnxt, q.cap_chunk);
+            if ((r = launch_end(t)) != HS_OK) return r;
+        }
+        std::swap(cur, nxt);
+        std::swap(ccur, cnxt);
+    }
+    return HS_OK;
 }
 
 }  // namespace hs

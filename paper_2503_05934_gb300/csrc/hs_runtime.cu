@@ -12,7 +12,7 @@ namespace hs {
 
 static const char *const kKernelNames[K_COUNT] = {
     "blocksort_keys", "blocksort_pairs", "merge_partition", "merge_keys",
-    "merge_pairs",    "qs_plan",         "qs_count",        "qs_scan",
+    "merge_pairs",    "qs_plan",         "qs_count",        "qs_fill",
     "qs_scatter",     "qs_small",        "seg_classify",    "seg_sort",
     "noalloc_sort"};
 
@@ -225,6 +225,16 @@ hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, vo
     e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) return fail_cuda(e, "hs_sort_i32_host: stream synchronize");
     return HS_OK;
+}
+
+hs_status hs_set_option(const char *name, int64_t value) {
+    clear_error();
+    if (!name) return fail(HS_ERR_INVALID_ARG, "hs_set_option: NULL name");
+    if (std::strcmp(name, "quick_max_levels") == 0) {
+        quick_set_max_levels(value);
+        return HS_OK;
+    }
+    return fail(HS_ERR_INVALID_ARG, std::string("hs_set_option: unknown option ") + name);
 }
 
 int hs_network_pairs(int m, int *pairs, int cap) {
