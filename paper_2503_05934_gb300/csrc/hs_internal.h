@@ -24,7 +24,6 @@ enum KernelId {
     K_QS_SMALL,
     K_SEG_CLASSIFY,
     K_SEG_SORT,
-    K_NOALLOC,
     K_COUNT
 };
 const char *kernel_name(int id);

@@ -13,8 +13,7 @@ namespace hs {
 static const char *const kKernelNames[K_COUNT] = {
     "blocksort_keys", "blocksort_pairs", "merge_partition", "merge_keys",
     "merge_pairs",    "qs_plan",         "qs_count",        "qs_fill",
-    "qs_scatter",     "qs_small",        "seg_classify",    "seg_sort",
-    "noalloc_sort"};
+    "qs_scatter",     "qs_small",        "seg_classify",    "seg_sort"};
 
 const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kKernelNames[id] : "?"; }
 
