@@ -364,7 +364,7 @@ def run_ours(args):
 
     # ---- extra forms (stable pairs), timed the same way
     if not args.no_extras:
-        line["extras"] = run_extras(hs, torch, dev, stream, args, rank)
+        line["extras"] = run_extras(hs, torch, dev, stream, args, rank, pristine)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     if rank == 0 and ws_world == 1 and not args.no_cpu:
@@ -383,8 +383,37 @@ def run_ours(args):
     return 0
 
 
-def run_extras(hs, torch, dev, stream, args, rank):
+def time_sorts(torch, stream, reps, warmup, restore, sort):
+    """Mean CUDA-event milliseconds of `sort` over `reps` runs after `warmup`;
+    `restore` (untimed) re-creates the unsorted input before each run."""
+    evs = []
+    for i in range(warmup + reps):
+        restore()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sort()
+        e1.record(stream)
+        if i >= warmup:
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+
+
+def run_extras(hs, torch, dev, stream, args, rank, pristine):
     out = {}
+    n_keys = pristine.numel()
+    # Quick path (Algorithm 2) on the same 2^28 uniform keys.
+    work = torch.empty_like(pristine)
+    wsq = torch.empty(hs.hs_sort_workspace_bytes(n_keys, False, "quick"), dtype=torch.uint8,
+                      device=dev)
+    ms = time_sorts(torch, stream, max(3, args.steps // 4), 2, lambda: work.copy_(pristine),
+                    lambda: hs.hs_sort_i32(work, "quick", args.netset, ws=wsq, stream=stream))
+    assert bool((work[1:] >= work[:-1]).all().item()), "quick sort output not sorted"
+    out["quick_2p28_uniform"] = {"value": n_keys / (ms / 1e3), "unit": "keys/s", "ms_per_sort": ms,
+                                 "workload": "2^28 uniform int32, median-of-three 3-way "
+                                             "partitions, 6To8 leaves"}
+    del work, wsq
     # Stable pairs: 2^27 keys from 2^16 distinct values, value = index.
     n = 1 << (args.log2n - 1)
     k, v = hs_inputs.pair_keys_16bit(n, hs_inputs.config_seed(2, salt=1 + (rank << 8)))
