@@ -117,6 +117,31 @@ HS_API size_t hs_sort_host_workspace_bytes(size_t n, hs_algo a);
 HS_API hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
                            size_t ws_bytes, hs_stream_t stream);
 
+/* Allocation-free merge sort, for callers that cannot allocate device memory:
+ * for example a plugin whose host application owns every device allocation
+ * and forbids side allocations, code that runs under a device-memory budget
+ * fixed at start-up, or a latency-critical path where cudaMalloc may
+ * synchronise the device and stall.  The paper has no counterpart; this is a
+ * library convenience around the HS_ALGO_MERGE path of hs_sort_i32.
+ *   d_keys, n, s, stream   as hs_sort_i32; no workspace argument.
+ *   Scratch: a fixed __device__ array of about 16 MiB inside the library (keys
+ *     copy + partition indices for HS_NOALLOC_MAX_KEYS keys).  Every GPU where
+ *     the library's code is loaded holds it until the process exits.
+ *   Limit: n <= HS_NOALLOC_MAX_KEYS (2^22 = 4,194,304 keys); a larger n returns
+ *     HS_ERR_INVALID_ARG before any launch.
+ *   Set-up: the first call on a device, with that device current, looks up the
+ *     scratch array's device address (cudaGetSymbolAddress) and caches it; make
+ *     that first call before any stream capture.  The current device must be
+ *     the one that owns d_keys and stream.
+ *   Sharing: every call uses the same scratch array, which keeps the previous
+ *     call's contents (nothing in it needs to start at zero).  Calls whose GPU
+ *     work overlaps (other streams, other host threads) race on it: serialise
+ *     them.
+ *   Calls no cudaMalloc, cudaFree or other allocating routine.  Asynchronous
+ *   on stream; other errors as hs_sort_i32. */
+#define HS_NOALLOC_MAX_KEYS 4194304u
+HS_API hs_status hs_sort_i32_noalloc(int32_t *d_keys, size_t n, hs_netset s, hs_stream_t stream);
+
 /* ------------------------------------------------------- errors, counters */
 
 HS_API const char *hs_status_str(hs_status st);

@@ -27,6 +27,7 @@ __all__ = [
     "hs_sort_workspace_bytes", "hs_sort_i32", "hs_sort_pairs_i32",
     "hs_sort_host_workspace_bytes", "hs_sort_i32_host", "hs_launch_count",
     "hs_prof_enable", "hs_prof_reset", "hs_prof_read", "hs_version", "hs_set_option",
+    "hs_sort_i32_noalloc", "NOALLOC_MAX_KEYS",
 ]
 
 
@@ -109,6 +110,19 @@ def hs_sort_i32_host(keys: torch.Tensor, algo="merge", netset="6To8", ws: torch.
     check(lib().hs_sort_i32_host(keys.data_ptr() if n else None, n, algo_id(algo),
                                  netset_mask(netset), ws.data_ptr(),
                                  ws.numel() * ws.element_size(), _stream_ptr(stream)))
+    return keys
+
+
+NOALLOC_MAX_KEYS = 4194304
+
+
+def hs_sort_i32_noalloc(keys: torch.Tensor, netset="6To8", stream=None) -> torch.Tensor:
+    """Merge-sorts ``keys`` in place with the library's built-in scratch (no
+    workspace, no device allocation); ``keys.numel()`` <= NOALLOC_MAX_KEYS."""
+    _check_i32(keys, "keys")
+    n = keys.numel()
+    check(lib().hs_sort_i32_noalloc(keys.data_ptr() if n else None, n, netset_mask(netset),
+                                    _stream_ptr(stream)))
     return keys
 
 

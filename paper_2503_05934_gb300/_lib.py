@@ -28,6 +28,7 @@ SIGNATURES = {
     "hs_sort_pairs_i32": (_int, [_vp, _vp, _sz, _int, _u32, _vp, _sz, _vp]),
     "hs_sort_host_workspace_bytes": (_sz, [_sz, _int]),
     "hs_sort_i32_host": (_int, [_vp, _sz, _int, _u32, _vp, _sz, _vp]),
+    "hs_sort_i32_noalloc": (_int, [_vp, _sz, _u32, _vp]),
     "hs_status_str": (ctypes.c_char_p, [_int]),
     "hs_last_error": (ctypes.c_char_p, []),
     "hs_version": (ctypes.c_char_p, []),
