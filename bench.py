@@ -54,6 +54,8 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--option", action="append", default=[],
+                   help="library tuning option name=value (hs_set_option)")
     return p.parse_args()
 
 
@@ -241,6 +243,9 @@ def run_ours(args):
     hs_build.build()
     import paper_2503_05934_gb300 as hs
 
+    for opt in args.option:
+        name, value = opt.split("=")
+        hs.hs_set_option(name, int(value))
     n = 1 << args.log2n
     seed = hs_inputs.config_seed(2, salt=rank)
     host = hs_inputs.random_i32(n, seed)
@@ -307,7 +312,7 @@ def run_ours(args):
         "algorithmic_bytes_per_launch": alg_bytes,
         "launch_ms": avg_mk_s * 1e3 if avg_mk_s else None,
     }
-    tile = 1024 * 8 if args.netset in ("6To8", "3To8", "PowerOf2", "Even") else None
+    tile = int(hs.lib().hs_keys_tile(hs.netset_mask(args.netset)))
     passes = sort_passes(n, tile) if tile else None
     p_ref = sort_passes(n, 8192)
     ms_step = total_ms / args.steps

@@ -142,6 +142,77 @@ HS_API hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netse
 #define HS_NOALLOC_MAX_KEYS 4194304u
 HS_API hs_status hs_sort_i32_noalloc(int32_t *d_keys, size_t n, hs_netset s, hs_stream_t stream);
 
+/* ----------------------------------------------------------- batched form */
+
+/* Launch plan of the batched form: which network set forms the leaves and
+ * how the persistent kernel is shaped.  hs_segsort_autotune picks one by
+ * timing candidates on the caller's data. */
+typedef struct {
+    hs_netset netset;      /* leaf networks (Table 3 set; leaf = largest size) */
+    int32_t block_threads; /* 512 or 1024; one tile holds 2*leaf*block_threads keys */
+    int32_t ctas_per_sm;   /* persistent CTAs per SM, 1..8; 0 = as many as fit */
+    int32_t reserved;      /* must be 0 */
+} hs_plan;
+
+/* Workspace for hs_segsort_i32 over n_keys keys in num_segs segments:
+ * scratch for every key plus one descriptor per segment. */
+HS_API size_t hs_segsort_workspace_bytes(size_t n_keys, size_t num_segs);
+
+/* Sorts every segment d_keys[off[i] .. off[i+1]) (i < num_segs) independently,
+ * each ascending, in one persistent launch: one CTA per segment at a time,
+ * network leaves and merge levels as in Algorithm 1; segments longer than a
+ * tile merge through their own scratch range.
+ *   d_offsets  device int64[num_segs + 1], non-decreasing, within [0, n_keys].
+ *              Malformed offsets are detected on the device: the segment is
+ *              skipped and hs_device_check reports HS_ERR_INVALID_ARG.
+ *   a          HS_ALGO_MERGE (QUICK -> HS_ERR_UNSUPPORTED).
+ *   s, plan    plan == NULL: network set s with the default shape; otherwise
+ *              the plan (its netset replaces s).
+ *   d_ws       ws_bytes >= hs_segsort_workspace_bytes(n_keys, num_segs).
+ * No host synchronisation: the call can be captured (see hs_segsort_capture).
+ * Designed for segments up to about 2^20 keys (larger ones work but are
+ * sorted by a single CTA; use hs_sort_i32 for those). */
+HS_API hs_status hs_segsort_i32(int32_t *d_keys, size_t n_keys, const int64_t *d_offsets,
+                                size_t num_segs, hs_algo a, hs_netset s, const hs_plan *plan,
+                                void *d_ws, size_t ws_bytes, hs_stream_t stream);
+
+/* The same result with one hs_sort_i32 call per segment (the per-array plain
+ * launches the batched form is measured against).  h_offsets is a HOST array
+ * of num_segs + 1 offsets; d_ws must satisfy hs_sort_workspace_bytes for the
+ * longest segment.  Asynchronous on `stream`; stops at the first error. */
+HS_API hs_status hs_sort_i32_many(int32_t *d_keys, size_t n_keys, const int64_t *h_offsets,
+                                  size_t num_segs, hs_algo a, hs_netset s, void *d_ws,
+                                  size_t ws_bytes, hs_stream_t stream);
+
+/* CUDA-graph form: captures the whole hs_segsort_i32 sequence (queue reset,
+ * descriptor build, persistent sort) for these exact buffers into a graph;
+ * hs_graph_launch replays it on any stream.  The buffers must outlive the
+ * graph.  hs_graph_destroy(NULL) is a no-op. */
+typedef struct hs_graph hs_graph;
+HS_API hs_status hs_segsort_capture(int32_t *d_keys, size_t n_keys, const int64_t *d_offsets,
+                                    size_t num_segs, const hs_plan *plan, void *d_ws,
+                                    size_t ws_bytes, hs_graph **out);
+HS_API hs_status hs_graph_launch(hs_graph *g, hs_stream_t stream);
+HS_API void hs_graph_destroy(hs_graph *g);
+
+/* Autotuner: times candidate plans (leaf network set x CTA size x CTAs per
+ * SM) on the caller's segments and returns the fastest in *best (and its
+ * time in *best_ms).  The keys are restored to their input order afterwards.
+ * Results are cached in-process, keyed by device name and size buckets
+ * (log2 of n_keys, of num_segs and of the mean segment); a cached entry is
+ * returned without timing.  Synchronous.
+ *   d_ws: ws_bytes >= hs_segsort_autotune_workspace_bytes(n_keys, num_segs)
+ *   (the segsort workspace plus a copy of the keys). */
+HS_API size_t hs_segsort_autotune_workspace_bytes(size_t n_keys, size_t num_segs);
+HS_API hs_status hs_segsort_autotune(int32_t *d_keys, size_t n_keys, const int64_t *d_offsets,
+                                     size_t num_segs, void *d_ws, size_t ws_bytes,
+                                     hs_stream_t stream, hs_plan *best, double *best_ms);
+/* The autotuner cache as a JSON file: save writes every entry; load merges
+ * the file's entries into the in-process cache (HS_ERR_INVALID_ARG if the
+ * file cannot be read or parsed). */
+HS_API hs_status hs_tune_cache_save(const char *path);
+HS_API hs_status hs_tune_cache_load(const char *path);
+
 /* ------------------------------------------------------- errors, counters */
 
 HS_API const char *hs_status_str(hs_status st);
@@ -162,11 +233,28 @@ HS_API void hs_prof_enable(int on);
 HS_API void hs_prof_reset(void);
 HS_API hs_status hs_prof_read(const char *kernel, uint64_t *launches, double *total_ms);
 
-/* Process-wide tuning knob.  "quick_max_levels": partition levels the quick
- * path runs before its depth guard merge-sorts the segments still open
- * (default -1 = automatic, 4*ceil(log2 n) + 16).  Unknown names return
- * HS_ERR_INVALID_ARG. */
+/* Waits for `stream`, then reads and clears the current device's kernel
+ * status word.  Kernels never trap: a bounded wait inside a kernel (an
+ * mbarrier on a bulk copy) that gives up raises this word and the kernel
+ * returns early.  Returns HS_ERR_TIMEOUT if that happened since the last
+ * check, HS_ERR_CUDA on a CUDA error, else HS_OK.  Synchronous. */
+HS_API hs_status hs_device_check(hs_stream_t stream);
+
+/* Process-wide tuning knobs (set them while no sort is in flight).
+ *   "quick_max_levels": partition levels the quick path runs before its depth
+ *     guard merge-sorts the segments still open (default -1 = automatic,
+ *     4*ceil(log2 n) + 16).
+ *   "blocksort_threads": 512 or 1024 (default) threads per CTA in the keys
+ *     block sort; the first merge tile holds 2 * leaf * threads keys.
+ *   "merge_kernel": 0 (default) staged-load merge levels, 1 persistent
+ *     bulk-copy (TMA) merge levels; both give identical results.
+ * Unknown names or values return HS_ERR_INVALID_ARG. */
 HS_API hs_status hs_set_option(const char *name, int64_t value);
+
+/* Keys per block-sort tile of the merge path for network set s under the
+ * current options (the global merge levels above it number
+ * ceil(log2(n / tile))); 0 for an invalid set. */
+HS_API size_t hs_keys_tile(hs_netset s);
 
 /* --------------------------------------------------------- host checking */
 

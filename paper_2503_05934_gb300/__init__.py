@@ -14,7 +14,7 @@ import ctypes
 
 import torch
 
-from ._lib import HsortError, check, lib
+from ._lib import HsortError, Plan, check, lib
 
 NETSETS = {
     "none": 0x000, "3": 0x008, "3To4": 0x018, "3To5": 0x038, "6To8": 0x1C0,
@@ -27,7 +27,9 @@ __all__ = [
     "hs_sort_workspace_bytes", "hs_sort_i32", "hs_sort_pairs_i32",
     "hs_sort_host_workspace_bytes", "hs_sort_i32_host", "hs_launch_count",
     "hs_prof_enable", "hs_prof_reset", "hs_prof_read", "hs_version", "hs_set_option",
-    "hs_sort_i32_noalloc", "NOALLOC_MAX_KEYS",
+    "hs_sort_i32_noalloc", "NOALLOC_MAX_KEYS", "hs_device_check", "Plan", "make_plan",
+    "hs_segsort_workspace_bytes", "hs_segsort_i32", "hs_sort_i32_many", "Graph",
+    "hs_segsort_capture", "hs_segsort_autotune", "hs_tune_cache_save", "hs_tune_cache_load",
 ]
 
 
@@ -113,6 +115,104 @@ def hs_sort_i32_host(keys: torch.Tensor, algo="merge", netset="6To8", ws: torch.
     return keys
 
 
+def _i64_dev(t: torch.Tensor, name: str) -> None:
+    if t.dtype != torch.int64 or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError(f"{name} must be a contiguous int64 CUDA tensor")
+
+
+def make_plan(netset="6To8", block_threads=512, ctas_per_sm=0) -> Plan:
+    return Plan(netset_mask(netset), int(block_threads), int(ctas_per_sm), 0)
+
+
+def hs_segsort_workspace_bytes(n_keys: int, num_segs: int) -> int:
+    return int(lib().hs_segsort_workspace_bytes(n_keys, num_segs))
+
+
+def hs_segsort_i32(keys: torch.Tensor, offsets: torch.Tensor, algo="merge", netset="6To8",
+                   plan: Plan | None = None, ws: torch.Tensor | None = None, stream=None):
+    """Sorts every segment keys[offsets[i]:offsets[i+1]] in place, one launch."""
+    _check_i32(keys, "keys")
+    _i64_dev(offsets, "offsets")
+    n, s = keys.numel(), offsets.numel() - 1
+    ws = _workspace(hs_segsort_workspace_bytes(n, s), keys.device, ws)
+    check(lib().hs_segsort_i32(keys.data_ptr(), n, offsets.data_ptr(), s, algo_id(algo),
+                               netset_mask(netset), ctypes.byref(plan) if plan else None,
+                               ws.data_ptr(), ws.numel() * ws.element_size(), _stream_ptr(stream)))
+    return keys
+
+
+def hs_sort_i32_many(keys: torch.Tensor, offsets_host, algo="merge", netset="6To8",
+                     ws: torch.Tensor | None = None, stream=None):
+    """One hs_sort_i32 call per segment (offsets on the host)."""
+    import numpy as np
+    _check_i32(keys, "keys")
+    off = np.ascontiguousarray(offsets_host, dtype=np.int64)
+    longest = int(np.max(np.diff(off))) if off.size > 1 else 0
+    ws = _workspace(hs_sort_workspace_bytes(longest, False, algo), keys.device, ws)
+    check(lib().hs_sort_i32_many(keys.data_ptr(), keys.numel(), off.ctypes.data, off.size - 1,
+                                 algo_id(algo), netset_mask(netset), ws.data_ptr(),
+                                 ws.numel() * ws.element_size(), _stream_ptr(stream)))
+    return keys
+
+
+class Graph:
+    """A captured batched sort (hs_graph); replay with launch()."""
+
+    def __init__(self, handle: int, keep: tuple):
+        self.handle = handle
+        self._keep = keep  # buffers the graph reads and writes
+
+    def launch(self, stream=None) -> None:
+        check(lib().hs_graph_launch(self.handle, _stream_ptr(stream)))
+
+    def destroy(self) -> None:
+        if self.handle:
+            lib().hs_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def hs_segsort_capture(keys: torch.Tensor, offsets: torch.Tensor, plan: Plan | None = None,
+                       ws: torch.Tensor | None = None) -> Graph:
+    _check_i32(keys, "keys")
+    _i64_dev(offsets, "offsets")
+    n, s = keys.numel(), offsets.numel() - 1
+    ws = _workspace(hs_segsort_workspace_bytes(n, s), keys.device, ws)
+    h = ctypes.c_void_p()
+    check(lib().hs_segsort_capture(keys.data_ptr(), n, offsets.data_ptr(), s,
+                                   ctypes.byref(plan) if plan else None, ws.data_ptr(),
+                                   ws.numel() * ws.element_size(), ctypes.byref(h)))
+    return Graph(h.value, (keys, offsets, ws))
+
+
+def hs_segsort_autotune(keys: torch.Tensor, offsets: torch.Tensor, ws: torch.Tensor | None = None,
+                        stream=None):
+    """Returns (Plan, milliseconds) of the fastest candidate; keys unchanged."""
+    _check_i32(keys, "keys")
+    _i64_dev(offsets, "offsets")
+    n, s = keys.numel(), offsets.numel() - 1
+    ws = _workspace(int(lib().hs_segsort_autotune_workspace_bytes(n, s)), keys.device, ws)
+    plan = Plan()
+    ms = ctypes.c_double()
+    check(lib().hs_segsort_autotune(keys.data_ptr(), n, offsets.data_ptr(), s, ws.data_ptr(),
+                                    ws.numel() * ws.element_size(), _stream_ptr(stream),
+                                    ctypes.byref(plan), ctypes.byref(ms)))
+    return plan, float(ms.value)
+
+
+def hs_tune_cache_save(path: str) -> None:
+    check(lib().hs_tune_cache_save(path.encode()))
+
+
+def hs_tune_cache_load(path: str) -> None:
+    check(lib().hs_tune_cache_load(path.encode()))
+
+
 NOALLOC_MAX_KEYS = 4194304
 
 
@@ -144,6 +244,11 @@ def hs_prof_read(kernel: str) -> tuple[int, float]:
     ms = ctypes.c_double()
     check(lib().hs_prof_read(kernel.encode(), ctypes.byref(n), ctypes.byref(ms)))
     return int(n.value), float(ms.value)
+
+
+def hs_device_check(stream=None) -> None:
+    """Waits for the stream and raises if a kernel reported a timed-out wait."""
+    check(lib().hs_device_check(_stream_ptr(stream)))
 
 
 def hs_set_option(name: str, value: int) -> None:

@@ -29,6 +29,17 @@ SIGNATURES = {
     "hs_sort_host_workspace_bytes": (_sz, [_sz, _int]),
     "hs_sort_i32_host": (_int, [_vp, _sz, _int, _u32, _vp, _sz, _vp]),
     "hs_sort_i32_noalloc": (_int, [_vp, _sz, _u32, _vp]),
+    "hs_segsort_workspace_bytes": (_sz, [_sz, _sz]),
+    "hs_segsort_i32": (_int, [_vp, _sz, _vp, _sz, _int, _u32, _vp, _vp, _sz, _vp]),
+    "hs_sort_i32_many": (_int, [_vp, _sz, _vp, _sz, _int, _u32, _vp, _sz, _vp]),
+    "hs_segsort_capture": (_int, [_vp, _sz, _vp, _sz, _vp, _vp, _sz, ctypes.POINTER(_vp)]),
+    "hs_graph_launch": (_int, [_vp, _vp]),
+    "hs_graph_destroy": (None, [_vp]),
+    "hs_segsort_autotune_workspace_bytes": (_sz, [_sz, _sz]),
+    "hs_segsort_autotune": (_int, [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp,
+                                   ctypes.POINTER(ctypes.c_double)]),
+    "hs_tune_cache_save": (_int, [ctypes.c_char_p]),
+    "hs_tune_cache_load": (_int, [ctypes.c_char_p]),
     "hs_status_str": (ctypes.c_char_p, [_int]),
     "hs_last_error": (ctypes.c_char_p, []),
     "hs_version": (ctypes.c_char_p, []),
@@ -38,9 +49,21 @@ SIGNATURES = {
     "hs_prof_read": (_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64),
                             ctypes.POINTER(ctypes.c_double)]),
     "hs_set_option": (_int, [ctypes.c_char_p, ctypes.c_int64]),
+    "hs_device_check": (_int, [_vp]),
+    "hs_keys_tile": (_sz, [_u32]),
     "hs_network_pairs": (_int, [_int, ctypes.POINTER(ctypes.c_int), _int]),
     "hs_network_apply": (_int, [_int, _c_i32p]),
 }
+
+
+class Plan(ctypes.Structure):
+    """hs_plan: leaf network set and persistent-kernel shape of the batched form."""
+    _fields_ = [("netset", ctypes.c_uint32), ("block_threads", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"netset": int(self.netset), "block_threads": int(self.block_threads),
+                "ctas_per_sm": int(self.ctas_per_sm)}
 
 
 class HsortError(RuntimeError):

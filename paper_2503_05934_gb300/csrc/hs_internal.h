@@ -42,6 +42,8 @@ struct LaunchToken {
     cudaEvent_t ev_a, ev_b;  // non-null while per-kernel timing is on
 };
 LaunchToken launch_begin(int id, cudaStream_t stream);
+// Adds k kernels launched indirectly (graph replays) to the launch count.
+void count_launches(uint64_t k);
 hs_status launch_end(const LaunchToken &t);
 
 // Validation shared by the entry points.
@@ -58,10 +60,20 @@ size_t merge_workspace_bytes(size_t n, int with_values);
 hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, void *d_ws,
                      size_t ws_bytes, cudaStream_t st);
 
-// Block sort of [0, n) in tiles of 1024*L keys (the merge path's first pass;
+// Tile of the keys block sort for leaf size L, and its thread-count option.
+int64_t keys_tile(int L);
+void merge_set_blocksort_threads(int nt);
+void merge_set_kernel(int k);
+
+// Block sort of [0, n) in tiles of keys_tile(L) keys (the merge path's first pass;
 // the whole sort when n fits one tile).
 hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
                            int vec, cudaStream_t st);
+
+// Device address of the current device's status word (kernels OR status bits
+// into it), and the check that waits for `st`, then reads and clears it.
+hs_status device_status(unsigned **out);
+hs_status device_check(cudaStream_t st);
 
 size_t quick_workspace_bytes(size_t n);
 void quick_set_max_levels(int64_t v);

@@ -2,10 +2,21 @@
 // launch, then per global level a partition launch and a merge launch,
 // ping-ponging between the caller's array and the workspace so that the last
 // level lands in the caller's array.
+#include <algorithm>
+#include <mutex>
+
 #include "hs_internal.h"
 #include "hs_merge_kernels.cuh"
 
 namespace hs {
+
+struct DeviceInfo {
+    int sms = 0;
+    unsigned *status = nullptr;
+    int tma_occ = 0;
+};
+
+static hs_status device_info(DeviceInfo **out);
 
 // Block sort: 1024 threads, one leaf of L keys each -> tiles of 1024*L keys
 // (8192 for the {6,7,8} set).  Merge levels: 256 threads x 16 keys (keys) or
@@ -38,9 +49,49 @@ static hs_status launch_blocksort_t(const int32_t *kin, int32_t *kout, const int
     return launch_end(t);
 }
 
+// Keys: two leaves per thread (block_sort_tile2).  512 or 1024 threads per
+// CTA (tile 1024*L or 2048*L keys); 1024 by default.
+static int g_bs2_threads = 1024;
+
+int64_t keys_tile(int L) { return (int64_t)g_bs2_threads * 2 * L; }
+
+void merge_set_blocksort_threads(int nt) { g_bs2_threads = (nt == 512) ? 512 : 1024; }
+
+template <int NT, int L>
+static hs_status launch_blocksort2_t(const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
+                                     int vec, cudaStream_t st) {
+    using C = BlockSort2<NT, L>;
+    auto kern = k_blocksort2<NT, L>;
+    hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
+    if (r != HS_OK) return r;
+    const int64_t grid = (n + C::T - 1) / C::T;
+    LaunchToken t = launch_begin(K_BLOCKSORT_KEYS, st);
+    kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, vec);
+    return launch_end(t);
+}
+
+template <int NT>
+static hs_status launch_blocksort2_nt(int L, const int32_t *kin, int32_t *kout, int64_t n,
+                                      hs_netset s, int vec, cudaStream_t st) {
+    switch (L) {
+        case 1: return launch_blocksort2_t<NT, 1>(kin, kout, n, s, vec, st);
+        case 3: return launch_blocksort2_t<NT, 3>(kin, kout, n, s, vec, st);
+        case 4: return launch_blocksort2_t<NT, 4>(kin, kout, n, s, vec, st);
+        case 5: return launch_blocksort2_t<NT, 5>(kin, kout, n, s, vec, st);
+        case 6: return launch_blocksort2_t<NT, 6>(kin, kout, n, s, vec, st);
+        case 7: return launch_blocksort2_t<NT, 7>(kin, kout, n, s, vec, st);
+        case 8: return launch_blocksort2_t<NT, 8>(kin, kout, n, s, vec, st);
+    }
+    return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
+}
+
 template <bool PAIRS>
 static hs_status launch_blocksort(int L, const int32_t *kin, int32_t *kout, const int32_t *vin,
                                   int32_t *vout, int64_t n, hs_netset s, int vec, cudaStream_t st) {
+    if constexpr (!PAIRS) {
+        return g_bs2_threads == 512 ? launch_blocksort2_nt<512>(L, kin, kout, n, s, vec, st)
+                                    : launch_blocksort2_nt<1024>(L, kin, kout, n, s, vec, st);
+    }
     switch (L) {
         case 1: return launch_blocksort_t<1, PAIRS>(kin, kout, vin, vout, n, s, vec, st);
         case 3: return launch_blocksort_t<3, PAIRS>(kin, kout, vin, vout, n, s, vec, st);
@@ -58,11 +109,19 @@ hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, 
     return launch_blocksort<false>(L, kin, kout, nullptr, nullptr, n, s, vec, st);
 }
 
+// Keys, 16-byte aligned buffers: persistent bulk-copy merge kernel, used when
+// the "merge_kernel" option is 1 (default 0: the staged-load kernel).
+constexpr int MT_NT = 256, MT_E = 16;
+static int g_merge_kernel = 0;
+
+void merge_set_kernel(int k) { g_merge_kernel = k; }
+
 template <int NT, int E, bool PAIRS>
 static hs_status launch_merge_level(const int32_t *kin, int32_t *kout, const int32_t *vin,
                                     int32_t *vout, int64_t n, int64_t w, int64_t *part, int vec,
                                     cudaStream_t st) {
     constexpr int TO = NT * E;
+    static_assert(PAIRS || TO == MT_NT * MT_E, "keys tiles of both merge kernels must agree");
     const int64_t span = 2 * w;
     const int64_t ngroups = (n + span - 1) / span;
     const int64_t tpg = (span + TO - 1) / TO;
@@ -75,6 +134,16 @@ static hs_status launch_merge_level(const int32_t *kin, int32_t *kout, const int
     hs_status r = launch_end(t);
     if (r != HS_OK) return r;
 
+    if (!PAIRS && vec && g_merge_kernel == 1) {
+        DeviceInfo *di = nullptr;
+        if ((r = device_info(&di)) != HS_OK) return r;
+        using C = TmaMerge<MT_NT, MT_E>;
+        const int64_t grid = std::min<int64_t>(nblocks, (int64_t)di->sms * di->tma_occ);
+        t = launch_begin(K_MERGE_KEYS, st);
+        k_merge_tma<MT_NT, MT_E><<<(unsigned)grid, MT_NT, C::SMEM_BYTES, st>>>(
+            kin, kout, n, w, part, (int)tpg, nblocks, di->status);
+        return launch_end(t);
+    }
     const int smem = merge_smem_words<NT, E>() * (int)sizeof(int32_t) * (PAIRS ? 2 : 1);
     auto kern = k_merge_pass<NT, E, PAIRS>;
     r = ensure_smem((const void *)kern, smem);
@@ -84,12 +153,40 @@ static hs_status launch_merge_level(const int32_t *kin, int32_t *kout, const int
     return launch_end(t);
 }
 
+static hs_status device_info(DeviceInfo **out) {
+    static std::mutex mu;
+    static DeviceInfo table[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(HS_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lk(mu);
+    DeviceInfo &d = table[dev];
+    if (d.sms == 0) {
+        using C = TmaMerge<MT_NT, MT_E>;
+        auto kern = k_merge_tma<MT_NT, MT_E>;
+        hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
+        if (r != HS_OK) return r;
+        int sms = 0, occ = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return fail_cuda(e, "cudaDeviceGetAttribute");
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, MT_NT, C::SMEM_BYTES)) !=
+            cudaSuccess)
+            return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if ((r = device_status(&d.status)) != HS_OK) return r;
+        d.tma_occ = occ > 0 ? occ : 1;
+        d.sms = sms;
+    }
+    *out = &d;
+    return HS_OK;
+}
+
 hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, void *d_ws,
                      size_t ws_bytes, cudaStream_t st) {
     const bool pairs = d_vals != nullptr;
     const int64_t n = (int64_t)n_;
     const int L = leaf_size(s);
-    const int64_t T = (int64_t)BS_NT * L;
+    const int64_t T = pairs ? (int64_t)BS_NT * L : keys_tile(L);
     int passes = 0;
     for (int64_t w = T; w < n; w *= 2) ++passes;
 

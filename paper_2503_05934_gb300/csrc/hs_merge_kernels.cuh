@@ -184,6 +184,198 @@ __global__ void __launch_bounds__(NT)
                                   PAIRS ? vout + base : nullptr, cnt, netset, vec != 0, smem);
 }
 
+template <int E>
+HS_DEV void bitonic_half_clean(int32_t (&x)[E]) {
+#pragma unroll
+    for (int d = E / 2; d > 0; d >>= 1) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            if ((i & d) == 0) {
+                int32_t lo = hs_min(x[i], x[i + d]);
+                int32_t hi = hs_max(x[i], x[i + d]);
+                x[i] = lo;
+                x[i + d] = hi;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block sort, two leaves per thread (keys).  Each of the NT threads holds
+// E = 2L consecutive keys: two leaves of L keys, each sorted by the size-L
+// network, then merged in registers by a bitonic merge.  The shared-memory
+// levels then merge runs of w -> 2w: every thread finds its merge-path split
+// and forms its E outputs as the lower half of a bitonic merge of the two
+// E-key windows at the split (no dependent load chain).
+//
+// Shared layout: logical index i lives at i + 4*(i/32), which keeps the
+// threads' 16-byte accesses to their own E keys free of bank conflicts.
+
+HS_HD constexpr int pow2_at_least(int x) {
+    int p = 1;
+    while (p < x) p *= 2;
+    return p;
+}
+
+HS_DEV int pad4(int i) { return i + ((i >> 5) << 2); }
+
+template <int NT, int L>
+struct BlockSort2 {
+    static constexpr int E = 2 * L;
+    static constexpr int P = pow2_at_least(E);
+    static constexpr int T = NT * E;
+    static constexpr int SZ = T + T / 8 + 64;  // padded tile (+ window slack)
+    static constexpr int SMEM_BYTES = SZ * 4;
+};
+
+// Full bitonic merge of two sorted runs of n <= P/2 keys held in x[0..n) and
+// x[n..2n); the result (ascending) is written back to x[0..2n).
+template <int N, int P>
+HS_DEV void register_merge_two(int32_t *x) {
+    int32_t lo[P / 2], hi[P / 2];
+#pragma unroll
+    for (int i = 0; i < P / 2; ++i) {
+        const int32_t a = i < N ? x[i] : kKeyMax;
+        const int j = P / 2 - 1 - i;  // reversed second run
+        const int32_t b = j < N ? x[N + j] : kKeyMax;
+        lo[i] = hs_min(a, b);
+        hi[i] = hs_max(a, b);
+    }
+    bitonic_half_clean<P / 2>(lo);
+    bitonic_half_clean<P / 2>(hi);
+#pragma unroll
+    for (int i = 0; i < 2 * N; ++i) x[i] = i < P / 2 ? lo[i] : hi[i - P / 2];
+}
+
+// A thread's own E keys at logical [my0, my0 + E): 16-byte accesses when E is
+// a multiple of 4 (my0 is then a multiple of 4 and no group of 4 crosses a
+// padding point).
+template <int E>
+HS_DEV void read_own(const int32_t *s, int my0, int32_t (&k)[E]) {
+    if constexpr (E % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < E / 4; ++q) {
+            const int4 v = *reinterpret_cast<const int4 *>(s + pad4(my0 + 4 * q));
+            k[4 * q] = v.x;
+            k[4 * q + 1] = v.y;
+            k[4 * q + 2] = v.z;
+            k[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) k[j] = s[pad4(my0 + j)];
+    }
+}
+
+template <int E>
+HS_DEV void write_own(int32_t *s, int my0, const int32_t (&k)[E]) {
+    if constexpr (E % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < E / 4; ++q)
+            *reinterpret_cast<int4 *>(s + pad4(my0 + 4 * q)) =
+                make_int4(k[4 * q], k[4 * q + 1], k[4 * q + 2], k[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) s[pad4(my0 + j)] = k[j];
+    }
+}
+
+template <int NT, int L>
+HS_DEV void block_sort_tile2(const int32_t *kin, int32_t *kout, int cnt, uint32_t netset,
+                             bool vec, int32_t *s) {
+    using C = BlockSort2<NT, L>;
+    constexpr int E = C::E, P = C::P, T = C::T;
+
+    // Load the tile (sentinels past cnt).
+    if (vec && cnt == T) {
+        const int4 *s4 = reinterpret_cast<const int4 *>(kin);
+#pragma unroll 4
+        for (int q = threadIdx.x; q < T / 4; q += NT)
+            *reinterpret_cast<int4 *>(s + pad4(4 * q)) = ld_stream(s4 + q);
+    } else {
+        for (int i = threadIdx.x; i < T; i += NT) s[pad4(i)] = i < cnt ? kin[i] : kKeyMax;
+    }
+    __syncthreads();
+
+    const int my0 = threadIdx.x * E;
+    int32_t k[E];
+    read_own<E>(s, my0, k);
+
+    // Leaves ("ApplySortingNetwork" on each of the thread's two leaves).
+    if constexpr (L > 1) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            KeyCE op{k + h * L};
+            const int r = cnt - (my0 + h * L);
+            if (r >= L) network<L>(op);
+            else if (r > 0) network_dyn(ragged_net_size(r, netset), op);
+        }
+    }
+    register_merge_two<L, P>(k);
+
+    // Shared-memory merge levels (padded layout throughout).
+    for (int w = E; w < T && w < cnt; w *= 2) {
+        __syncthreads();
+        write_own<E>(s, my0, k);
+        __syncthreads();
+        const int gs = ((E & (E - 1)) == 0) ? (my0 & ~(2 * w - 1)) : (my0 / (2 * w)) * (2 * w);
+        const int diag = my0 - gs;
+        int lo = diag > w ? diag - w : 0;
+        int hi = diag < w ? diag : w;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s[pad4(gs + mid)] <= s[pad4(gs + w + diag - 1 - mid)]) lo = mid + 1;
+            else hi = mid;
+        }
+        const int a0 = gs + lo, b0 = gs + w + diag - lo;
+        const int ra = w - lo, rb = w - (diag - lo);
+        int32_t o[P];
+        if (ra >= E && rb >= E) {
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const int j = P - 1 - i;
+                const int32_t a = i < E ? s[pad4(a0 + i)] : kKeyMax;
+                const int32_t b = j < E ? s[pad4(b0 + j)] : kKeyMax;
+                o[i] = hs_min(a, b);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const int j = P - 1 - i;
+                const int32_t a = (i < E && i < ra) ? s[pad4(a0 + i)] : kKeyMax;
+                const int32_t b = (j < E && j < rb) ? s[pad4(b0 + j)] : kKeyMax;
+                o[i] = hs_min(a, b);
+            }
+        }
+        bitonic_half_clean<P>(o);
+#pragma unroll
+        for (int j = 0; j < E; ++j) k[j] = o[j];
+    }
+
+    __syncthreads();
+    write_own<E>(s, my0, k);
+    __syncthreads();
+    if (vec) {
+        const int n4 = cnt >> 2;
+        int4 *d4 = reinterpret_cast<int4 *>(kout);
+        for (int q = threadIdx.x; q < n4; q += NT)
+            st_stream(d4 + q, *reinterpret_cast<const int4 *>(s + pad4(4 * q)));
+        for (int i = 4 * n4 + threadIdx.x; i < cnt; i += NT) kout[i] = s[pad4(i)];
+    } else {
+        for (int i = threadIdx.x; i < cnt; i += NT) kout[i] = s[pad4(i)];
+    }
+}
+
+template <int NT, int L>
+__global__ void __launch_bounds__(NT)
+    k_blocksort2(const int32_t *kin, int32_t *kout, int64_t n, uint32_t netset, int vec) {
+    constexpr int T = BlockSort2<NT, L>::T;
+    extern __shared__ __align__(16) int32_t smem[];
+    const int64_t base = (int64_t)blockIdx.x * T;
+    const int cnt = (int)((n - base) < T ? (n - base) : T);
+    block_sort_tile2<NT, L>(kin + base, kout + base, cnt, netset, vec != 0, smem);
+}
+
 // ---------------------------------------------------------------------------
 // Global merge level.  Group g merges A = [g*2w, g*2w+w) with
 // B = [g*2w+w, g*2w+2w) (both clipped to n).  Each group is cut into tpg
@@ -295,6 +487,194 @@ __global__ void __launch_bounds__(NT)
     __syncthreads();
     store_tile_padded<NT>(kout + m.gs + o0, tot, sk, vec);
     if constexpr (PAIRS) store_tile_padded<NT>(vout + m.gs + o0, tot, sv, vec);
+}
+
+// ---------------------------------------------------------------------------
+// Global merge level, bulk-copy form (keys, 16-byte aligned buffers).
+//
+// Persistent CTAs walk the output tiles b = blockIdx.x, +gridDim.x, ...  The
+// tile's A and B input ranges arrive in shared memory by 1-D bulk copies
+// (cp.async.bulk, completion on an mbarrier), double-buffered: the copy of the
+// next tile is in flight while the current one is merged.  Each thread then
+// takes its merge-path split and forms its E outputs as the lower half of a
+// bitonic merge of A[ai, ai+E) and B[bi, bi+E) (no dependent load chain), and
+// stores them straight from registers with 16-byte stores.  Ties between A and
+// B keys are indistinguishable for keys alone, so the unstable bitonic step
+// yields the same bytes as a stable merge.
+
+template <int NT, int E>
+struct TmaMerge {
+    static constexpr int TO = NT * E;
+    // head (<= 3) + TO keys + E words of over-read slack, kept a multiple of 4
+    static constexpr int REG = TO + E + 8;
+    static constexpr int STAGE = 2 * REG;
+    static constexpr int SMEM_BYTES = 2 * STAGE * 4 + 2 * 8;
+};
+
+struct TileGeom {
+    int64_t ga, gb, out;  // global start of A range, of B range, of output
+    int na, nb, tot;
+};
+
+HS_DEV TileGeom tile_geom(int64_t b, int64_t n, int64_t w, int tpg, int to, const int64_t *part) {
+    const int64_t g = b / tpg;
+    const int t = (int)(b - g * tpg);
+    const MergeGeom m = merge_geom(g, n, w);
+    const int64_t glen = m.alen + m.blen;
+    const int64_t o0 = (int64_t)t * to;
+    const int64_t o1 = (o0 + to) < glen ? (o0 + to) : glen;
+    const int64_t a0 = part[b];
+    const int64_t a1 = (o1 == glen) ? m.alen : part[b + 1];
+    TileGeom tg;
+    tg.ga = m.gs + a0;
+    tg.na = (int)(a1 - a0);
+    tg.gb = m.gs + w + (o0 - a0);
+    tg.nb = (int)((o1 - a1) - (o0 - a0));
+    tg.out = m.gs + o0;
+    tg.tot = (int)(o1 - o0);
+    return tg;
+}
+
+// Copy window of a range [g, g+cnt): 16-byte aligned start, end rounded up but
+// never past n4 (the last multiple of 4 <= n); keys in [hi, g+cnt) are loaded
+// by plain loads afterwards.
+struct CopyWin {
+    int64_t lo, hi;
+};
+HS_DEV CopyWin copy_window(int64_t g, int cnt, int64_t n4) {
+    CopyWin c;
+    c.lo = g & ~int64_t(3);
+    int64_t hi = (g + cnt + 3) & ~int64_t(3);
+    c.hi = hi < n4 ? hi : n4;
+    if (c.hi < c.lo) c.hi = c.lo;
+    return c;
+}
+
+template <int NT, int E>
+HS_DEV void tma_issue(const TileGeom &tg, const int32_t *in, int64_t n4, int32_t *stage,
+                      uint64_t *bar) {
+    using C = TmaMerge<NT, E>;
+    const CopyWin ca = copy_window(tg.ga, tg.na, n4);
+    const CopyWin cb = copy_window(tg.gb, tg.nb, n4);
+    const uint32_t bytes_a = (uint32_t)(ca.hi - ca.lo) * 4u;
+    const uint32_t bytes_b = (uint32_t)(cb.hi - cb.lo) * 4u;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, bytes_a + bytes_b);
+    if (bytes_a) bulk_load(stage, in + ca.lo, bytes_a, bar);
+    if (bytes_b) bulk_load(stage + C::REG, in + cb.lo, bytes_b, bar);
+}
+
+// Merge-path split of two separate sorted arrays.
+HS_DEV int merge_path2(const int32_t *A, int na, const int32_t *B, int nb, int diag) {
+    int lo = diag > nb ? diag - nb : 0;
+    int hi = diag < na ? diag : na;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The E smallest keys of A[ai..] and B[bi..] in ascending order: lower half of
+// the bitonic merge of A[ai, ai+E) and reversed B[bi, bi+E), then sorted.
+template <int E>
+HS_DEV void merge_window(const int32_t *A, int ra, const int32_t *B, int rb, int32_t (&lo)[E]) {
+    int32_t a[E], b[E];
+    if (ra >= E && rb >= E) {
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            a[k] = A[k];
+            b[k] = B[k];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            a[k] = k < ra ? A[k] : kKeyMax;
+            b[k] = k < rb ? B[k] : kKeyMax;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < E; ++k) lo[k] = hs_min(a[k], b[E - 1 - k]);
+    bitonic_half_clean<E>(lo);
+}
+
+template <int NT, int E>
+__global__ void __launch_bounds__(NT)
+    k_merge_tma(const int32_t *in, int32_t *out, int64_t n, int64_t w, const int64_t *part,
+                int tpg, int64_t ntiles, unsigned *status) {
+    using C = TmaMerge<NT, E>;
+    extern __shared__ __align__(16) int32_t smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * C::STAGE);
+    const int64_t n4 = n & ~int64_t(3);
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    int64_t b = blockIdx.x;
+    if (b >= ntiles) return;
+    if (threadIdx.x == 0) tma_issue<NT, E>(tile_geom(b, n, w, tpg, C::TO, part), in, n4, smem, &bars[0]);
+
+    int stage = 0;
+    uint32_t parities = 0;  // bit s: parity of the next phase of barrier s
+    for (; b < ntiles; b += gridDim.x) {
+        const int64_t bn = b + gridDim.x;
+        int32_t *cur = smem + stage * C::STAGE;
+        if (bn < ntiles && threadIdx.x == 0)
+            tma_issue<NT, E>(tile_geom(bn, n, w, tpg, C::TO, part), in, n4,
+                             smem + (stage ^ 1) * C::STAGE, &bars[stage ^ 1]);
+
+        const bool ok = mbar_wait(&bars[stage], (parities >> stage) & 1u);
+        if (__syncthreads_or(!ok)) {
+            // A bulk copy did not complete in time: report it, give the copies
+            // still in flight a bounded chance to land, and leave.
+            if (threadIdx.x == 0) {
+                atomicOr(status, kStatusTimeout);
+                mbar_wait(&bars[stage], (parities >> stage) & 1u);
+                if (bn < ntiles) mbar_wait(&bars[stage ^ 1], (parities >> (stage ^ 1)) & 1u);
+            }
+            return;
+        }
+        parities ^= 1u << stage;
+
+        const TileGeom tg = tile_geom(b, n, w, tpg, C::TO, part);
+        const CopyWin ca = copy_window(tg.ga, tg.na, n4);
+        const CopyWin cb = copy_window(tg.gb, tg.nb, n4);
+        int32_t *sA = cur + (int)(tg.ga - ca.lo);
+        int32_t *sB = cur + C::REG + (int)(tg.gb - cb.lo);
+        // Keys past the last multiple of 4 of the array: plain loads.
+        const int64_t tail_a = tg.ga + tg.na - ca.hi, tail_b = tg.gb + tg.nb - cb.hi;
+        if (tail_a > 0 || tail_b > 0) {
+            if (threadIdx.x < tail_a) sA[(int)(ca.hi - tg.ga) + threadIdx.x] = in[ca.hi + threadIdx.x];
+            if (threadIdx.x < tail_b) sB[(int)(cb.hi - tg.gb) + threadIdx.x] = in[cb.hi + threadIdx.x];
+            __syncthreads();
+        }
+
+        const int diag = threadIdx.x * E;
+        if (diag < tg.tot) {
+            const int ai = merge_path2(sA, tg.na, sB, tg.nb, diag);
+            const int bi = diag - ai;
+            int32_t o[E];
+            merge_window<E>(sA + ai, tg.na - ai, sB + bi, tg.nb - bi, o);
+            int32_t *dst = out + tg.out + diag;
+            if (diag + E <= tg.tot) {
+#pragma unroll
+                for (int q = 0; q < E / 4; ++q)
+                    st_stream(reinterpret_cast<int4 *>(dst) + q,
+                              make_int4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]));
+            } else {
+#pragma unroll
+                for (int k = 0; k < E; ++k)
+                    if (diag + k < tg.tot) dst[k] = o[k];
+            }
+        }
+        __syncthreads();
+        stage ^= 1;
+    }
 }
 
 }  // namespace hs

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "hs_internal.h"
+#include "hs_common.cuh"
 #include "hs_networks.cuh"
 
 namespace hs {
@@ -78,6 +79,8 @@ hs_status launch_end(const LaunchToken &t) {
     return HS_OK;
 }
 
+void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
 static void prof_drain_locked() {
     for (auto &s : g_prof_pending) {
         float ms = 0.f;
@@ -90,6 +93,48 @@ static void prof_drain_locked() {
         g_event_pool.push_back({s.a, s.b});
     }
     g_prof_pending.clear();
+}
+
+// Device status word raised by kernels instead of trapping (bounded waits
+// that gave up, malformed offsets); one copy per device.
+static __device__ unsigned g_status;
+
+hs_status device_status(unsigned **out) {
+    static std::mutex mu;
+    static unsigned *addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(HS_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if ((e = cudaGetSymbolAddress(&p, g_status)) != cudaSuccess)
+            return fail_cuda(e, "cudaGetSymbolAddress(status)");
+        addr[dev] = static_cast<unsigned *>(p);
+    }
+    *out = addr[dev];
+    return HS_OK;
+}
+
+hs_status device_check(cudaStream_t st) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(e, "hs_device_check: stream synchronize");
+    unsigned *p = nullptr;
+    hs_status r = device_status(&p);
+    if (r != HS_OK) return r;
+    unsigned v = 0;
+    if ((e = cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail_cuda(e, "hs_device_check: read status");
+    if (v) {
+        const unsigned zero = 0;
+        if ((e = cudaMemcpy(p, &zero, sizeof zero, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail_cuda(e, "hs_device_check: clear status");
+        if (v & kStatusTimeout)
+            return fail(HS_ERR_TIMEOUT, "a kernel gave up on a bounded wait");
+        return fail(HS_ERR_INVALID_ARG, "a kernel found malformed segment offsets");
+    }
+    return HS_OK;
 }
 
 hs_status ensure_smem(const void *func, int bytes) {
@@ -226,6 +271,11 @@ hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, vo
     return HS_OK;
 }
 
+hs_status hs_device_check(hs_stream_t stream) {
+    clear_error();
+    return device_check((cudaStream_t)stream);
+}
+
 hs_status hs_set_option(const char *name, int64_t value) {
     clear_error();
     if (!name) return fail(HS_ERR_INVALID_ARG, "hs_set_option: NULL name");
@@ -233,7 +283,24 @@ hs_status hs_set_option(const char *name, int64_t value) {
         quick_set_max_levels(value);
         return HS_OK;
     }
+    if (std::strcmp(name, "merge_kernel") == 0) {
+        if (value != 0 && value != 1)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_kernel must be 0 or 1");
+        merge_set_kernel((int)value);
+        return HS_OK;
+    }
+    if (std::strcmp(name, "blocksort_threads") == 0) {
+        if (value != 512 && value != 1024)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_threads must be 512 or 1024");
+        merge_set_blocksort_threads((int)value);
+        return HS_OK;
+    }
     return fail(HS_ERR_INVALID_ARG, std::string("hs_set_option: unknown option ") + name);
+}
+
+size_t hs_keys_tile(hs_netset s) {
+    if (!netset_ok(s)) return 0;
+    return (size_t)keys_tile(leaf_size(s));
 }
 
 int hs_network_pairs(int m, int *pairs, int cap) {
