@@ -54,6 +54,9 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=20000)
     p.add_argument("--option", action="append", default=[],
                    help="library tuning option name=value (hs_set_option)")
     return p.parse_args()
@@ -442,6 +445,124 @@ def run_extras(hs, torch, dev, stream, args, rank, pristine):
                                 "workload": "2^27 (int32 key from 2^16 values, int32 index) "
                                             "stable merge sort, 6To8 leaves"}
     del pk, pv, wk, wv, wsb
+    if not args.no_batched:
+        out["batched_segsort"] = run_batched(hs, torch, dev, stream, args)
+    if not args.no_serve:
+        out["serve"] = run_serving(hs, torch, dev, args)
+    return out
+
+
+def run_batched(hs, torch, dev, stream, args):
+    """200,000 independent arrays, sizes log-uniform in [3, 65536], mixed
+    distributions: one persistent launch replayed from a CUDA graph with the
+    autotuned plan, against one hs_sort_i32 call per array on one stream."""
+    keys, off, _ = hs_inputs.segmented(200_000, hs_inputs.config_seed(3))
+    n = keys.size
+    pristine = torch.from_numpy(keys).to(dev)
+    del keys
+    work = torch.empty_like(pristine)
+    offs = torch.from_numpy(off).to(dev)
+    work.copy_(pristine)
+    plan, tune_ms = hs.hs_segsort_autotune(work, offs, stream=stream)
+    graph = hs.hs_segsort_capture(work, offs, plan)
+    launches0 = hs.hs_launch_count()
+    ms = time_sorts(torch, stream, max(3, args.steps // 4), 2, lambda: work.copy_(pristine),
+                    lambda: graph.launch(stream))
+    launches = hs.hs_launch_count() - launches0
+    hs.hs_device_check(stream)
+    batched = work.clone()
+    d = batched[1:] >= batched[:-1]
+    d[offs[1:-1] - 1] = True  # segment boundaries
+    assert bool(d.all().item()), "batched output not sorted per segment"
+    # Per-array plain launches: one hs_sort_i32 per segment, FIFO on one stream.
+    work.copy_(pristine)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    hs.hs_sort_i32_many(work, off, "merge", "6To8", stream=stream)
+    torch.cuda.synchronize(dev)
+    plain_s = time.perf_counter() - t0
+    assert torch.equal(work, batched), "per-array result differs from batched result"
+    graph.destroy()
+    del work, pristine, batched, offs, d
+    return {"value": n / (ms / 1e3), "unit": "keys/s", "ms_per_batch": ms,
+            "plain_value": n / plain_s, "plain_s": plain_s,
+            "speedup_vs_plain": plain_s / (ms / 1e3), "keys": int(n), "segments": 200_000,
+            "plan": plan.as_dict(), "autotune_best_ms": tune_ms,
+            "gpu_launches_per_batch": launches / (max(3, args.steps // 4) + 2),
+            "workload": "200,000 int32 arrays, sizes log-uniform in [3, 65536], "
+                        "1/3 random, 1/3 sorted, 1/3 nearly sorted; CUDA-graph replay of "
+                        "one persistent launch; plain = one hs_sort_i32 per array"}
+
+
+def run_serving(hs, torch, dev, args):
+    """Poisson arrivals of sort requests (sizes log-uniform in [8, 4194304],
+    mixed distributions) into the continuous-batching server under an 8 GiB
+    budget; p50/p99 latency at 0.5/0.8/0.95 of its measured capacity, against
+    serial plain launches (one hs_sort_i32 at a time, FIFO)."""
+    import numpy as np
+    nreq = args.serve_requests
+    seed = hs_inputs.config_seed(4)
+    sizes = hs_inputs.log_uniform_sizes(nreq, seed, 8, 4194304)
+    dists = hs_inputs.uniform_int(seed ^ 0x51, nreq, 0, 2)
+    pool_n = 1 << 23
+    pools = [torch.from_numpy(hs_inputs.keys(pool_n, d, seed + i)).to(dev)
+             for i, d in enumerate(hs_inputs.DISTS)]
+    starts = hs_inputs.uniform_int(seed ^ 0x52, nreq, 0, pool_n - 4194304)
+    off = np.zeros(nreq + 1, np.int64)
+    np.cumsum(sizes, out=off[1:])
+    total = int(off[-1])
+    arena = torch.empty(total, dtype=torch.int32, device=dev)
+    for i in range(nreq):
+        s0, n_i = int(starts[i]), int(sizes[i])
+        arena[int(off[i]):int(off[i]) + n_i].copy_(pools[int(dists[i])][s0:s0 + n_i])
+    del pools
+    pristine = arena.clone()
+    base = arena.data_ptr()
+    ptrs = (base + 4 * off[:-1]).astype(np.uint64)
+    srv = hs.Server(8 << 30)
+    out = {"requests": nreq, "keys": total, "budget_bytes": 8 << 30,
+           "workload": "Poisson arrivals, sizes log-uniform in [8, 4194304], mixed "
+                       "random/sorted/nearly sorted, 8 GiB budget"}
+    try:
+        srv.replay(np.zeros(min(nreq, 500)), ptrs[:500], sizes[:500])  # warm-up
+        arena.copy_(pristine)
+        torch.cuda.synchronize(dev)
+        lat, mk = srv.replay(np.zeros(nreq), ptrs, sizes)
+        cap_req_s = nreq / mk
+        out["capacity"] = {"keys_per_s": total / mk, "requests_per_s": cap_req_s,
+                           "makespan_s": mk}
+        for frac in (0.5, 0.8, 0.95):
+            arena.copy_(pristine)
+            torch.cuda.synchronize(dev)
+            arr = hs_inputs.poisson_arrivals(nreq, frac * cap_req_s, seed ^ int(frac * 100))
+            lat, mk = srv.replay(arr, ptrs, sizes)
+            out[f"load_{int(frac * 100)}"] = {
+                "rate_req_per_s": frac * cap_req_s, "p50_ms": float(np.percentile(lat, 50)) * 1e3,
+                "p99_ms": float(np.percentile(lat, 99)) * 1e3, "sustained_keys_per_s": total / mk}
+        out["server_stats"] = srv.stats()
+    finally:
+        srv.destroy()
+    # Serial plain launches: one request at a time (FIFO), service time each.
+    arena.copy_(pristine)
+    ws = torch.empty(hs.hs_sort_workspace_bytes(4194304), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)
+    service = np.zeros(nreq)
+    stream = torch.cuda.current_stream(dev)
+    for i in range(nreq):
+        t0 = time.perf_counter()
+        hs.hs_sort_i32(arena[int(off[i]):int(off[i + 1])], "merge", "6To8", ws=ws, stream=stream)
+        torch.cuda.synchronize(dev)
+        service[i] = time.perf_counter() - t0
+    out["serial_plain"] = {"keys_per_s": total / service.sum()}
+    arr = hs_inputs.poisson_arrivals(nreq, 0.8 * out["capacity"]["requests_per_s"], seed ^ 80)
+    finish, t = np.zeros(nreq), 0.0
+    for i in range(nreq):  # FIFO single-server queue on the measured service times
+        t = max(t, arr[i]) + service[i]
+        finish[i] = t
+    lat = finish - arr
+    out["serial_plain"]["at_load_80"] = {"p50_ms": float(np.percentile(lat, 50)) * 1e3,
+                                         "p99_ms": float(np.percentile(lat, 99)) * 1e3}
+    del arena, pristine, ws
     return out
 
 

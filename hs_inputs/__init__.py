@@ -26,16 +26,53 @@ arrays; it gives no generator parameters):
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
 
 import numpy as np
 
+_U64 = 0xFFFFFFFFFFFFFFFF
 GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 _CHUNK = 1 << 22
 
 SEED_BASE = 0x5EED0000
+
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libhsgen.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles gen.c (the fast form of these generators) with plain gcc."""
+    src = os.path.join(_HERE, "gen.c")
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src):
+        return _LIB_PATH
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, src])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _clib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        u64, i64, vp = ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p
+        L.hsg_u32.argtypes = [u64, u64, u64, vp]
+        L.hsg_sorted.argtypes = [u64, i64, vp]
+        L.hsg_nearly.argtypes = [u64, i64, vp]
+        L.hsg_segmented.argtypes = [u64, i64, vp, vp, vp]
+        for f in (L.hsg_u32, L.hsg_sorted, L.hsg_nearly, L.hsg_segmented):
+            f.restype = None
+        _lib = L
+    return _lib
 
 
 def config_seed(config_id: int, salt: int = 0) -> int:
@@ -78,10 +115,32 @@ def uniform_int(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
 
 
 def random_i32(n: int, seed: int) -> np.ndarray:
-    return _stream_u32(seed, n).view(np.int32)
+    out = np.empty(n, np.int32)
+    if n:
+        _clib().hsg_u32(seed & _U64, 0, n, out.ctypes.data)
+    return out
 
 
 def sorted_i32(n: int, seed: int) -> np.ndarray:
+    out = np.empty(n, np.int32)
+    if n:
+        _clib().hsg_sorted(seed & _U64, n, out.ctypes.data)
+    return out
+
+
+def nearly_sorted_i32(n: int, seed: int) -> np.ndarray:
+    out = np.empty(n, np.int32)
+    if n:
+        _clib().hsg_nearly(seed & _U64, n, out.ctypes.data)
+    return out
+
+
+def np_random_i32(n: int, seed: int) -> np.ndarray:
+    """numpy form of random_i32 (the definition the C form must match)."""
+    return _stream_u32(seed, n).view(np.int32)
+
+
+def np_sorted_i32(n: int, seed: int) -> np.ndarray:
     """Ascending keys spanning [INT32_MIN, INT32_MAX] with random gaps."""
     if n == 0:
         return np.empty(0, np.int32)
@@ -97,8 +156,8 @@ def sorted_i32(n: int, seed: int) -> np.ndarray:
     return out
 
 
-def nearly_sorted_i32(n: int, seed: int) -> np.ndarray:
-    a = sorted_i32(n, seed)
+def np_nearly_sorted_i32(n: int, seed: int) -> np.ndarray:
+    a = np_sorted_i32(n, seed)
     k = n // 100
     if k == 0:
         return a
@@ -123,7 +182,7 @@ def keys(n: int, dist: str, seed: int) -> np.ndarray:
 
 def pair_keys_16bit(n: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
     """Keys from 2^16 distinct int32 values and values = original index."""
-    u = (_stream_u32(seed, n) & np.uint32(0xFFFF)).astype(np.uint32)
+    u = (random_i32(n, seed).view(np.uint32) & np.uint32(0xFFFF)).astype(np.uint32)
     h = splitmix64(seed ^ 0x7061697273, 0, 2)
     mult = np.uint32((int(h[0]) & 0xFFFFFFFF) | 1)
     xor = np.uint32(int(h[1]) & 0xFFFFFFFF)
@@ -145,21 +204,60 @@ DISTS = ("random", "sorted", "nearly")
 
 def segmented(num_segs: int, seed: int, lo: int = 3, hi: int = 65536,
               sizes: np.ndarray | None = None):
+    """Concatenated segments with a per-segment distribution (C form of
+    np_segmented).  Returns (keys, offsets[num_segs+1], dist_ids)."""
+    sizes = segment_sizes(num_segs, seed, lo, hi) if sizes is None else np.asarray(sizes, np.int64)
+    off = np.zeros(sizes.size + 1, np.int64)
+    np.cumsum(sizes, out=off[1:])
+    dist_ids = np.ascontiguousarray(uniform_int(seed ^ 0x64697374, sizes.size, 0, 2), np.int64)
+    out = np.empty(int(off[-1]), np.int32)
+    if sizes.size:
+        _clib().hsg_segmented(seed & _U64, sizes.size, off.ctypes.data, dist_ids.ctypes.data,
+                              out.ctypes.data)
+    return out, off, dist_ids
+
+
+def np_segmented(num_segs: int, seed: int, lo: int = 3, hi: int = 65536,
+                 sizes: np.ndarray | None = None):
     """Concatenated segments with a per-segment distribution drawn uniformly
-    from (random, sorted, nearly).  Returns (keys, offsets[num_segs+1], dist_ids)."""
+    from (random, sorted, nearly).  Returns (keys, offsets[num_segs+1], dist_ids).
+
+    Random segments take their keys from one stream over the whole buffer.
+    Sorted and nearly sorted segments are running sums of random gaps (one
+    stream over their positions), each spread over the int32 range; nearly
+    sorted ones then get floor(0.01 * size) sequential swaps of uniform pairs
+    (one stream of draws, segment by segment)."""
     sizes = segment_sizes(num_segs, seed, lo, hi) if sizes is None else np.asarray(sizes, np.int64)
     num_segs = sizes.size
     off = np.zeros(num_segs + 1, np.int64)
     np.cumsum(sizes, out=off[1:])
     dist_ids = uniform_int(seed ^ 0x64697374, num_segs, 0, 2)
     out = np.empty(int(off[-1]), np.int32)
-    # One contiguous random draw for the whole buffer, then per-segment rewrites
-    # for sorted and nearly sorted segments (each seeded by its index).
     _stream_u32(seed ^ 0x6B657973, out.size, out.view(np.uint32))
-    for s in np.nonzero(dist_ids != 0)[0].tolist():
-        b, e = int(off[s]), int(off[s + 1])
-        sub_seed = (seed * 1000003 + s) & 0xFFFFFFFFFFFFFFFF
-        out[b:e] = keys(e - b, DISTS[int(dist_ids[s])], sub_seed)
+    sel = np.nonzero((dist_ids != 0) & (sizes > 0))[0]
+    if sel.size:
+        ssz = sizes[sel]
+        starts = off[sel]
+        # positions of all selected segments, segment by segment
+        rel = np.arange(int(ssz.sum()), dtype=np.int64) - np.repeat(np.cumsum(ssz) - ssz, ssz)
+        pos = np.repeat(starts, ssz) + rel
+        max_gap = np.repeat(np.maximum(1, (1 << 33) // ssz), ssz).astype(np.uint64)
+        gaps = (splitmix64(seed ^ 0x67617073, 0, pos.size) % max_gap).astype(np.int64)
+        run = np.cumsum(gaps)
+        first = np.cumsum(ssz) - ssz  # index of each segment's first position in `pos`
+        base = np.repeat(run[first] - gaps[first], ssz)
+        out[pos] = np.clip(run - base - (1 << 31), -(1 << 31), (1 << 31) - 1).astype(np.int32)
+        near = sel[dist_ids[sel] == 2]
+        k = sizes[near] // 100
+        if k.sum() > 0:
+            draws = splitmix64(seed ^ 0x6E656172, 0, 2 * int(k.sum()))
+            seg_of = np.repeat(np.arange(near.size), k)
+            span = sizes[near][seg_of].astype(np.uint64)
+            b = off[near][seg_of]
+            ii = (b + (draws[0::2] % span).astype(np.int64)).tolist()
+            jj = (b + (draws[1::2] % span).astype(np.int64)).tolist()
+            for i, j in zip(ii, jj):
+                out[i], out[j] = out[j], out[i]
     return out, off, dist_ids
 
 

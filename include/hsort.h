@@ -213,6 +213,42 @@ HS_API hs_status hs_segsort_autotune(int32_t *d_keys, size_t n_keys, const int64
 HS_API hs_status hs_tune_cache_save(const char *path);
 HS_API hs_status hs_tune_cache_load(const char *path);
 
+/* ---------------------------------------------------------------- serving */
+
+/* Continuous-batching sort server for one device (the device current at
+ * creation).  Requests are device arrays sorted in place with the merge path;
+ * a worker thread admits them in arrival order while the memory budget fits
+ * (a request counts its keys plus the workspace the server reserves for it),
+ * batches everything admitted into one launch per free stream slot (requests
+ * of up to 65,536 keys share one persistent batched launch; longer ones run
+ * the multi-CTA merge path in the same slot), and keeps up to four slots in
+ * flight, so newly admitted work overlaps with running work.  A request's
+ * result is the same as hs_sort_i32's on its own.
+ *   hs_server_create: budget_bytes >= 1 MiB; the server allocates a workspace
+ *     pool of budget_bytes once, plus four streams.
+ *   hs_server_submit: returns at once with a ticket; HS_ERR_OVER_BUDGET if the
+ *     request alone exceeds the budget; HS_ERR_UNSUPPORTED for HS_ALGO_QUICK.
+ *     The caller must not touch d_keys until hs_server_wait returns.
+ *   hs_server_wait: blocks until the request finished; *result is its status,
+ *     *latency_s the seconds from submit to completion.  Each ticket is waited
+ *     for once.
+ *   hs_server_replay: load generator: submits count requests at arrival_s[i]
+ *     seconds after the call (busy-waiting on the host clock), waits for all,
+ *     and returns each latency and the total makespan.
+ *   hs_server_destroy: finishes all submitted work, then frees everything. */
+typedef struct hs_server hs_server;
+HS_API hs_status hs_server_create(size_t budget_bytes, hs_server **out);
+HS_API hs_status hs_server_submit(hs_server *srv, int32_t *d_keys, size_t n, hs_algo a,
+                                  hs_netset s, uint64_t *ticket);
+HS_API hs_status hs_server_wait(hs_server *srv, uint64_t ticket, hs_status *result,
+                                double *latency_s);
+HS_API hs_status hs_server_stats(hs_server *srv, uint64_t *batches, uint64_t *batched_requests,
+                                 size_t *bytes_in_use);
+HS_API hs_status hs_server_replay(hs_server *srv, const double *arrival_s,
+                                  int32_t *const *d_keys, const size_t *n, size_t count,
+                                  hs_netset s, double *latency_s, double *makespan_s);
+HS_API void hs_server_destroy(hs_server *srv);
+
 /* ------------------------------------------------------- errors, counters */
 
 HS_API const char *hs_status_str(hs_status st);

@@ -30,6 +30,7 @@ __all__ = [
     "hs_sort_i32_noalloc", "NOALLOC_MAX_KEYS", "hs_device_check", "Plan", "make_plan",
     "hs_segsort_workspace_bytes", "hs_segsort_i32", "hs_sort_i32_many", "Graph",
     "hs_segsort_capture", "hs_segsort_autotune", "hs_tune_cache_save", "hs_tune_cache_load",
+    "Server",
 ]
 
 
@@ -211,6 +212,59 @@ def hs_tune_cache_save(path: str) -> None:
 
 def hs_tune_cache_load(path: str) -> None:
     check(lib().hs_tune_cache_load(path.encode()))
+
+
+class Server:
+    """Continuous-batching sort server (hs_server_*) on the current device."""
+
+    def __init__(self, budget_bytes: int):
+        h = ctypes.c_void_p()
+        check(lib().hs_server_create(int(budget_bytes), ctypes.byref(h)))
+        self.handle = h.value
+
+    def submit(self, keys: torch.Tensor, netset="6To8", algo="merge") -> int:
+        _check_i32(keys, "keys")
+        t = ctypes.c_uint64()
+        n = keys.numel()
+        check(lib().hs_server_submit(self.handle, keys.data_ptr() if n else None, n,
+                                     algo_id(algo), netset_mask(netset), ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket: int) -> tuple[int, float]:
+        st = ctypes.c_int()
+        lat = ctypes.c_double()
+        check(lib().hs_server_wait(self.handle, ticket, ctypes.byref(st), ctypes.byref(lat)))
+        return int(st.value), float(lat.value)
+
+    def stats(self) -> dict:
+        b, r, u = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_size_t()
+        check(lib().hs_server_stats(self.handle, ctypes.byref(b), ctypes.byref(r), ctypes.byref(u)))
+        return {"batches": b.value, "batched_requests": r.value, "bytes_in_use": u.value}
+
+    def replay(self, arrival_s, key_ptrs, sizes, netset="6To8"):
+        """Submits requests at the given offsets (s) from now; returns
+        (latencies_s, makespan_s)."""
+        import numpy as np
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        ptrs = np.ascontiguousarray(key_ptrs, dtype=np.uint64)
+        ns = np.ascontiguousarray(sizes, dtype=np.uint64)
+        lat = np.zeros(arr.size, np.float64)
+        mk = ctypes.c_double()
+        check(lib().hs_server_replay(self.handle, arr.ctypes.data, ptrs.ctypes.data, ns.ctypes.data,
+                                     arr.size, netset_mask(netset), lat.ctypes.data,
+                                     ctypes.byref(mk)))
+        return lat, float(mk.value)
+
+    def destroy(self) -> None:
+        if self.handle:
+            lib().hs_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 NOALLOC_MAX_KEYS = 4194304

@@ -40,6 +40,15 @@ SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_double)]),
     "hs_tune_cache_save": (_int, [ctypes.c_char_p]),
     "hs_tune_cache_load": (_int, [ctypes.c_char_p]),
+    "hs_server_create": (_int, [_sz, ctypes.POINTER(_vp)]),
+    "hs_server_submit": (_int, [_vp, _vp, _sz, _int, _u32, ctypes.POINTER(ctypes.c_uint64)]),
+    "hs_server_wait": (_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_int),
+                              ctypes.POINTER(ctypes.c_double)]),
+    "hs_server_stats": (_int, [_vp, ctypes.POINTER(ctypes.c_uint64),
+                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_sz)]),
+    "hs_server_replay": (_int, [_vp, _vp, _vp, _vp, _sz, _u32, _vp,
+                                ctypes.POINTER(ctypes.c_double)]),
+    "hs_server_destroy": (None, [_vp]),
     "hs_status_str": (ctypes.c_char_p, [_int]),
     "hs_last_error": (ctypes.c_char_p, []),
     "hs_version": (ctypes.c_char_p, []),

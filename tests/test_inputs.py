@@ -55,3 +55,19 @@ def test_poisson():
     gaps = np.diff(t)
     assert np.all(gaps >= 0)
     assert abs(gaps.mean() * 100.0 - 1) < 0.05
+
+
+def test_c_forms_match_numpy_definitions():
+    for n in [0, 1, 7, 99, 100, 1000, 12345]:
+        assert np.array_equal(g.random_i32(n, 3), g.np_random_i32(n, 3))
+        assert np.array_equal(g.sorted_i32(n, 4), g.np_sorted_i32(n, 4))
+        assert np.array_equal(g.nearly_sorted_i32(n, 5), g.np_nearly_sorted_i32(n, 5))
+    sizes = np.array([3, 0, 250, 1000, 7, 4096, 65536, 1, 333], np.int64)
+    for seed in [1, 2, 3]:
+        a = g.segmented(0, seed, sizes=sizes)
+        b = g.np_segmented(0, seed, sizes=sizes)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    a = g.segmented(400, 9)
+    b = g.np_segmented(400, 9)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
