@@ -281,9 +281,12 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *     guard merge-sorts the segments still open (default -1 = automatic,
  *     4*ceil(log2 n) + 16).
  *   "blocksort_threads": 512 or 1024 (default) threads per CTA in the keys
- *     block sort; the first merge tile holds 2 * leaf * threads keys.
- *   "merge_kernel": 0 (default) staged-load merge levels, 1 persistent
- *     bulk-copy (TMA) merge levels; both give identical results.
+ *     block sort; each thread holds two leaves (leaf and leaf-1 keys), so
+ *     the first merge tile holds (2 * leaf - 1) * threads keys.
+ *   "merge_kernel": 1 (default) tiled merge levels with asynchronous 16-byte
+ *     staging and odd outputs per thread (used for keys when both buffers
+ *     are 16-byte aligned and n % 4 == 0), 0 staged-load serial merges.
+ *     Both give identical results.
  * Unknown names or values return HS_ERR_INVALID_ARG. */
 HS_API hs_status hs_set_option(const char *name, int64_t value);
 

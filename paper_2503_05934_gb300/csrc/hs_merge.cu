@@ -10,13 +10,6 @@
 
 namespace hs {
 
-struct DeviceInfo {
-    int sms = 0;
-    unsigned *status = nullptr;
-    int tma_occ = 0;
-};
-
-static hs_status device_info(DeviceInfo **out);
 
 // Block sort: 1024 threads, one leaf of L keys each -> tiles of 1024*L keys
 // (8192 for the {6,7,8} set).  Merge levels: 256 threads x 16 keys (keys) or
@@ -49,19 +42,19 @@ static hs_status launch_blocksort_t(const int32_t *kin, int32_t *kout, const int
     return launch_end(t);
 }
 
-// Keys: two leaves per thread (block_sort_tile2).  512 or 1024 threads per
-// CTA (tile 1024*L or 2048*L keys); 1024 by default.
+// Keys: two leaves (L and L-1 keys) per thread (block_sort_tile3).  512 or
+// 1024 threads per CTA (tile (2L-1)*512 or (2L-1)*1024 keys); 1024 default.
 static int g_bs2_threads = 1024;
 
-int64_t keys_tile(int L) { return (int64_t)g_bs2_threads * 2 * L; }
+int64_t keys_tile(int L) { return (int64_t)g_bs2_threads * (2 * L - 1); }
 
 void merge_set_blocksort_threads(int nt) { g_bs2_threads = (nt == 512) ? 512 : 1024; }
 
 template <int NT, int L>
 static hs_status launch_blocksort2_t(const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
                                      int vec, cudaStream_t st) {
-    using C = BlockSort2<NT, L>;
-    auto kern = k_blocksort2<NT, L>;
+    using C = BlockSort3<NT, L>;
+    auto kern = k_blocksort3<NT, L>;
     hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
     if (r != HS_OK) return r;
     const int64_t grid = (n + C::T - 1) / C::T;
@@ -109,10 +102,12 @@ hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, 
     return launch_blocksort<false>(L, kin, kout, nullptr, nullptr, n, s, vec, st);
 }
 
-// Keys, 16-byte aligned buffers: persistent bulk-copy merge kernel, used when
-// the "merge_kernel" option is 1 (default 0: the staged-load kernel).
-constexpr int MT_NT = 256, MT_E = 16;
-static int g_merge_kernel = 0;
+// Keys with 16-byte aligned buffers and n % 4 == 0: the streaming bulk-copy
+// merge kernel (option "merge_kernel" 1, the default); otherwise, or with
+// option 0, the staged-load kernel with a partition pass.
+constexpr int MT_NT = 128, MT_E = 15;
+constexpr int TT_NT = 256, TT_EO = 15;
+static int g_merge_kernel = 1;
 
 void merge_set_kernel(int k) { g_merge_kernel = k; }
 
@@ -121,29 +116,35 @@ static hs_status launch_merge_level(const int32_t *kin, int32_t *kout, const int
                                     int32_t *vout, int64_t n, int64_t w, int64_t *part, int vec,
                                     cudaStream_t st) {
     constexpr int TO = NT * E;
-    static_assert(PAIRS || TO == MT_NT * MT_E, "keys tiles of both merge kernels must agree");
     const int64_t span = 2 * w;
     const int64_t ngroups = (n + span - 1) / span;
     const int64_t tpg = (span + TO - 1) / TO;
     const int64_t last = n - (ngroups - 1) * span;
     const int64_t nblocks = (ngroups - 1) * tpg + (last + TO - 1) / TO;
 
-    LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
-    k_merge_partition<<<(unsigned)((nblocks + 255) / 256), 256, 0, st>>>(kin, n, w, TO, (int)tpg,
-                                                                         nblocks, part);
-    hs_status r = launch_end(t);
-    if (r != HS_OK) return r;
-
-    if (!PAIRS && vec && g_merge_kernel == 1) {
-        DeviceInfo *di = nullptr;
-        if ((r = device_info(&di)) != HS_OK) return r;
-        using C = TmaMerge<MT_NT, MT_E>;
-        const int64_t grid = std::min<int64_t>(nblocks, (int64_t)di->sms * di->tma_occ);
+    hs_status r = HS_OK;
+    LaunchToken t;
+    if (!PAIRS && vec && g_merge_kernel == 1 && (n % 4) == 0) {
+        using C = TileMerge<TT_NT, TT_EO>;
+        constexpr int TTO = C::TO;
+        const int64_t ttpg = (span + TTO - 1) / TTO;
+        const int64_t tnb = (ngroups - 1) * ttpg + (last + TTO - 1) / TTO;
+        t = launch_begin(K_MERGE_PARTITION, st);
+        k_merge_partition<<<(unsigned)((tnb + 255) / 256), 256, 0, st>>>(kin, n, w, TTO, (int)ttpg,
+                                                                         tnb, part);
+        if ((r = launch_end(t)) != HS_OK) return r;
+        auto kern = k_merge_tile<TT_NT, TT_EO>;
+        if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
         t = launch_begin(K_MERGE_KEYS, st);
-        k_merge_tma<MT_NT, MT_E><<<(unsigned)grid, MT_NT, C::SMEM_BYTES, st>>>(
-            kin, kout, n, w, part, (int)tpg, nblocks, di->status);
+        kern<<<(unsigned)tnb, TT_NT, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, (int)ttpg);
         return launch_end(t);
     }
+    t = launch_begin(K_MERGE_PARTITION, st);
+    k_merge_partition<<<(unsigned)((nblocks + 255) / 256), 256, 0, st>>>(kin, n, w, TO, (int)tpg,
+                                                                         nblocks, part);
+    r = launch_end(t);
+    if (r != HS_OK) return r;
+
     const int smem = merge_smem_words<NT, E>() * (int)sizeof(int32_t) * (PAIRS ? 2 : 1);
     auto kern = k_merge_pass<NT, E, PAIRS>;
     r = ensure_smem((const void *)kern, smem);
@@ -151,34 +152,6 @@ static hs_status launch_merge_level(const int32_t *kin, int32_t *kout, const int
     t = launch_begin(PAIRS ? K_MERGE_PAIRS : K_MERGE_KEYS, st);
     kern<<<(unsigned)nblocks, NT, smem, st>>>(kin, kout, vin, vout, n, w, part, (int)tpg, vec);
     return launch_end(t);
-}
-
-static hs_status device_info(DeviceInfo **out) {
-    static std::mutex mu;
-    static DeviceInfo table[64];
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) return fail(HS_ERR_UNSUPPORTED, "device ordinal above 63");
-    std::lock_guard<std::mutex> lk(mu);
-    DeviceInfo &d = table[dev];
-    if (d.sms == 0) {
-        using C = TmaMerge<MT_NT, MT_E>;
-        auto kern = k_merge_tma<MT_NT, MT_E>;
-        hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
-        if (r != HS_OK) return r;
-        int sms = 0, occ = 0;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-            return fail_cuda(e, "cudaDeviceGetAttribute");
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, MT_NT, C::SMEM_BYTES)) !=
-            cudaSuccess)
-            return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        if ((r = device_status(&d.status)) != HS_OK) return r;
-        d.tma_occ = occ > 0 ? occ : 1;
-        d.sms = sms;
-    }
-    *out = &d;
-    return HS_OK;
 }
 
 hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, void *d_ws,

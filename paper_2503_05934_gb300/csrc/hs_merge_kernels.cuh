@@ -36,6 +36,18 @@ HS_DEV int merge_path(const int32_t *s, int a0, int na, int b0, int nb, int diag
     return lo;
 }
 
+// Merge-path split of two separate sorted arrays.
+HS_DEV int merge_path2(const int32_t *A, int na, const int32_t *B, int nb, int diag) {
+    int lo = diag > nb ? diag - nb : 0;
+    int hi = diag < na ? diag : na;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Sequential stable merge of E outputs from shared memory, starting at the
 // merge-path split (ai in A = [.., aend), bi in B = [.., bend)).  One shared
 // load per output; it may read one element past either run, so every buffer
@@ -217,14 +229,17 @@ HS_HD constexpr int pow2_at_least(int x) {
     return p;
 }
 
-HS_DEV int pad4(int i) { return i + ((i >> 5) << 2); }
+// Padded shared index for the keys block sort: one pad word after every 8.
+// Merge windows of neighbouring threads start about 8 keys apart; the pad
+// puts their k-th words on different banks.
+HS_DEV int pad4(int i) { return i + (i >> 3); }
 
 template <int NT, int L>
 struct BlockSort2 {
     static constexpr int E = 2 * L;
     static constexpr int P = pow2_at_least(E);
     static constexpr int T = NT * E;
-    static constexpr int SZ = T + T / 8 + 64;  // padded tile (+ window slack)
+    static constexpr int SZ = T + T / 8 + 64;  // padded tile (1 word per 8) + window slack
     static constexpr int SMEM_BYTES = SZ * 4;
 };
 
@@ -252,7 +267,7 @@ HS_DEV void register_merge_two(int32_t *x) {
 // padding point).
 template <int E>
 HS_DEV void read_own(const int32_t *s, int my0, int32_t (&k)[E]) {
-    if constexpr (E % 4 == 0) {
+    if constexpr (false) {
 #pragma unroll
         for (int q = 0; q < E / 4; ++q) {
             const int4 v = *reinterpret_cast<const int4 *>(s + pad4(my0 + 4 * q));
@@ -269,7 +284,7 @@ HS_DEV void read_own(const int32_t *s, int my0, int32_t (&k)[E]) {
 
 template <int E>
 HS_DEV void write_own(int32_t *s, int my0, const int32_t (&k)[E]) {
-    if constexpr (E % 4 == 0) {
+    if constexpr (false) {
 #pragma unroll
         for (int q = 0; q < E / 4; ++q)
             *reinterpret_cast<int4 *>(s + pad4(my0 + 4 * q)) =
@@ -290,8 +305,14 @@ HS_DEV void block_sort_tile2(const int32_t *kin, int32_t *kout, int cnt, uint32_
     if (vec && cnt == T) {
         const int4 *s4 = reinterpret_cast<const int4 *>(kin);
 #pragma unroll 4
-        for (int q = threadIdx.x; q < T / 4; q += NT)
-            *reinterpret_cast<int4 *>(s + pad4(4 * q)) = ld_stream(s4 + q);
+        for (int q = threadIdx.x; q < T / 4; q += NT) {
+            const int4 v = ld_stream(s4 + q);
+            const int i = pad4(4 * q);  // 4 consecutive keys never straddle a pad word
+            s[i] = v.x;
+            s[i + 1] = v.y;
+            s[i + 2] = v.z;
+            s[i + 3] = v.w;
+        }
     } else {
         for (int i = threadIdx.x; i < T; i += NT) s[pad4(i)] = i < cnt ? kin[i] : kKeyMax;
     }
@@ -330,22 +351,12 @@ HS_DEV void block_sort_tile2(const int32_t *kin, int32_t *kout, int cnt, uint32_
         const int a0 = gs + lo, b0 = gs + w + diag - lo;
         const int ra = w - lo, rb = w - (diag - lo);
         int32_t o[P];
-        if (ra >= E && rb >= E) {
 #pragma unroll
-            for (int i = 0; i < P; ++i) {
-                const int j = P - 1 - i;
-                const int32_t a = i < E ? s[pad4(a0 + i)] : kKeyMax;
-                const int32_t b = j < E ? s[pad4(b0 + j)] : kKeyMax;
-                o[i] = hs_min(a, b);
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-                const int j = P - 1 - i;
-                const int32_t a = (i < E && i < ra) ? s[pad4(a0 + i)] : kKeyMax;
-                const int32_t b = (j < E && j < rb) ? s[pad4(b0 + j)] : kKeyMax;
-                o[i] = hs_min(a, b);
-            }
+        for (int i = 0; i < P; ++i) {
+            const int j = P - 1 - i;
+            const int32_t a = (i < E && i < ra) ? s[pad4(a0 + i)] : kKeyMax;
+            const int32_t b = (j < E && j < rb) ? s[pad4(b0 + j)] : kKeyMax;
+            o[i] = hs_min(a, b);
         }
         bitonic_half_clean<P>(o);
 #pragma unroll
@@ -358,8 +369,10 @@ HS_DEV void block_sort_tile2(const int32_t *kin, int32_t *kout, int cnt, uint32_
     if (vec) {
         const int n4 = cnt >> 2;
         int4 *d4 = reinterpret_cast<int4 *>(kout);
-        for (int q = threadIdx.x; q < n4; q += NT)
-            st_stream(d4 + q, *reinterpret_cast<const int4 *>(s + pad4(4 * q)));
+        for (int q = threadIdx.x; q < n4; q += NT) {
+            const int i = pad4(4 * q);
+            st_stream(d4 + q, make_int4(s[i], s[i + 1], s[i + 2], s[i + 3]));
+        }
         for (int i = 4 * n4 + threadIdx.x; i < cnt; i += NT) kout[i] = s[pad4(i)];
     } else {
         for (int i = threadIdx.x; i < cnt; i += NT) kout[i] = s[pad4(i)];
@@ -374,6 +387,152 @@ __global__ void __launch_bounds__(NT)
     const int64_t base = (int64_t)blockIdx.x * T;
     const int cnt = (int)((n - base) < T ? (n - base) : T);
     block_sort_tile2<NT, L>(kin + base, kout + base, cnt, netset, vec != 0, smem);
+}
+
+// ---------------------------------------------------------------------------
+// Block sort, odd form (keys).  Each of the NT threads holds EO = 2L - 1
+// consecutive keys as two leaves: one of L keys and one of L - 1 keys, each
+// sorted by its network ("ApplySortingNetwork"; a leaf size that is not in
+// the set is padded with +infinity sentinels up to the next size that is, the
+// same rule as a ragged leaf), then merged in registers.  For the {6,7,8} set
+// the leaves are 8 and 7 keys, both sizes in the set.
+//
+// The shared-memory levels merge runs of w -> 2w; every thread finds its
+// merge-path split and forms its EO outputs as the lowest EO of the lower half
+// of a P-wide bitonic merge of the two windows at the split.  Because EO is
+// odd, neighbouring threads' windows and their own EO-key slots fall on
+// different banks, so the tile is stored unpadded.
+
+template <int NT, int L>
+struct BlockSort3 {
+    static constexpr int EO = 2 * L - 1;
+    static constexpr int P = pow2_at_least(EO);
+    static constexpr int T = NT * EO;
+    static constexpr int SZ = T + P + 32;  // tile + window slack
+    static constexpr int SMEM_BYTES = SZ * 4;
+};
+
+// Sorts leaf x[0..N) in registers (N live keys at most; r of them real).
+template <int N>
+HS_DEV void sort_leaf(int32_t *x, int r, uint32_t netset) {
+    if (r <= 1) return;
+    const int m = ragged_net_size(r, netset);  // r if r is in the set, else the next size up
+    if (m == N && r == N) {
+        KeyCE op{x};
+        network<N>(op);
+        return;
+    }
+    // Pad to the network size with sentinels (never stored), sort, copy back.
+    int32_t t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t[i] = (i < N && i < r) ? x[i < N ? i : 0] : kKeyMax;
+    KeyCE op{t};
+    network_dyn(m, op);
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = t[i];
+}
+
+// Bitonic merge of sorted x[0..N1) and x[N1..N1+N2) (N1, N2 <= P/2) in
+// registers; the ascending result goes back to x[0..N1+N2).
+template <int N1, int N2, int P>
+HS_DEV void register_merge(int32_t *x) {
+    int32_t lo[P / 2], hi[P / 2];
+#pragma unroll
+    for (int i = 0; i < P / 2; ++i) {
+        const int32_t a = i < N1 ? x[i] : kKeyMax;
+        const int j = P / 2 - 1 - i;  // second run, reversed
+        const int32_t b = j < N2 ? x[N1 + (j < N2 ? j : 0)] : kKeyMax;
+        lo[i] = hs_min(a, b);
+        hi[i] = hs_max(a, b);
+    }
+    bitonic_half_clean<P / 2>(lo);
+    bitonic_half_clean<P / 2>(hi);
+#pragma unroll
+    for (int i = 0; i < N1 + N2; ++i) x[i] = i < P / 2 ? lo[i] : hi[i - P / 2];
+}
+
+template <int NT, int L>
+HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_t netset,
+                             bool vec, int32_t *s) {
+    using C = BlockSort3<NT, L>;
+    constexpr int EO = C::EO, P = C::P, T = C::T;
+
+    if (vec && cnt == T && (T % 4) == 0) {
+        const int4 *s4 = reinterpret_cast<const int4 *>(kin);
+#pragma unroll 4
+        for (int q = threadIdx.x; q < T / 4; q += NT)
+            *reinterpret_cast<int4 *>(s + 4 * q) = ld_stream(s4 + q);
+    } else {
+        for (int i = threadIdx.x; i < T; i += NT) s[i] = i < cnt ? kin[i] : kKeyMax;
+    }
+    __syncthreads();
+
+    const int my0 = threadIdx.x * EO;
+    int32_t k[EO];
+#pragma unroll
+    for (int j = 0; j < EO; ++j) k[j] = s[my0 + j];
+
+    if constexpr (L > 1) {
+        const int r0 = hs_min(hs_max(cnt - my0, 0), L);
+        const int r1 = hs_min(hs_max(cnt - my0 - L, 0), L - 1);
+        sort_leaf<L>(k, r0, netset);
+        sort_leaf<L - 1>(k + L, r1, netset);
+        register_merge<L, L - 1, P>(k);
+    }
+
+    for (int w = EO; w < T && w < cnt; w *= 2) {
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < EO; ++j) s[my0 + j] = k[j];
+        __syncthreads();
+        const int gs = (my0 / (2 * w)) * (2 * w);
+        const int diag = my0 - gs;
+        const int32_t *A = s + gs, *B = s + gs + w;
+        int lo = diag > w ? diag - w : 0;
+        int hi = diag < w ? diag : w;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
+            else hi = mid;
+        }
+        const int32_t *wA = A + lo, *wB = B + (diag - lo);
+        const int ra = w - lo, rb = w - (diag - lo);
+        int32_t o[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const int j = P - 1 - i;
+            const int32_t x = (i < EO && i < ra) ? wA[i] : kKeyMax;
+            const int32_t y = (j < EO && j < rb) ? wB[j] : kKeyMax;
+            o[i] = hs_min(x, y);
+        }
+        bitonic_half_clean<P>(o);
+#pragma unroll
+        for (int j = 0; j < EO; ++j) k[j] = o[j];
+    }
+
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < EO; ++j) s[my0 + j] = k[j];
+    __syncthreads();
+    if (vec && (T % 4) == 0) {
+        const int n4 = cnt >> 2;
+        int4 *d4 = reinterpret_cast<int4 *>(kout);
+        for (int q = threadIdx.x; q < n4; q += NT)
+            st_stream(d4 + q, *reinterpret_cast<const int4 *>(s + 4 * q));
+        for (int i = 4 * n4 + threadIdx.x; i < cnt; i += NT) kout[i] = s[i];
+    } else {
+        for (int i = threadIdx.x; i < cnt; i += NT) kout[i] = s[i];
+    }
+}
+
+template <int NT, int L>
+__global__ void __launch_bounds__(NT)
+    k_blocksort3(const int32_t *kin, int32_t *kout, int64_t n, uint32_t netset, int vec) {
+    constexpr int T = BlockSort3<NT, L>::T;
+    extern __shared__ __align__(16) int32_t smem[];
+    const int64_t base = (int64_t)blockIdx.x * T;
+    const int cnt = (int)((n - base) < T ? (n - base) : T);
+    block_sort_tile3<NT, L>(kin + base, kout + base, cnt, netset, vec != 0, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -490,191 +649,103 @@ __global__ void __launch_bounds__(NT)
 }
 
 // ---------------------------------------------------------------------------
-// Global merge level, bulk-copy form (keys, 16-byte aligned buffers).
+// Global merge level, tiled form (keys; 16-byte aligned buffers, n % 4 == 0).
 //
-// Persistent CTAs walk the output tiles b = blockIdx.x, +gridDim.x, ...  The
-// tile's A and B input ranges arrive in shared memory by 1-D bulk copies
-// (cp.async.bulk, completion on an mbarrier), double-buffered: the copy of the
-// next tile is in flight while the current one is merged.  Each thread then
-// takes its merge-path split and forms its E outputs as the lower half of a
-// bitonic merge of A[ai, ai+E) and B[bi, bi+E) (no dependent load chain), and
-// stores them straight from registers with 16-byte stores.  Ties between A and
-// B keys are indistinguishable for keys alone, so the unstable bitonic step
-// yields the same bytes as a stable merge.
+// One CTA per output tile of TO = NT*EO keys (the partition pass gives its
+// merge-path split), many CTAs per SM for latency hiding.  The tile's A and B
+// ranges are staged in shared memory by 16-byte asynchronous copies
+// (cp.async) of their 16-byte-aligned covers; each thread then forms its EO
+// outputs from the lower half of a P-wide bitonic merge of its two windows
+// and stores them directly.  EO is odd so that neighbouring threads' windows
+// start on different banks.
 
-template <int NT, int E>
-struct TmaMerge {
-    static constexpr int TO = NT * E;
-    // head (<= 3) + TO keys + E words of over-read slack, kept a multiple of 4
-    static constexpr int REG = TO + E + 8;
-    static constexpr int STAGE = 2 * REG;
-    static constexpr int SMEM_BYTES = 2 * STAGE * 4 + 2 * 8;
+HS_DEV void cp_async16(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+HS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int NT, int EO>
+struct TileMerge {
+    static constexpr int P = pow2_at_least(EO);
+    static constexpr int TO = NT * EO;
+    static constexpr int REG = TO + 8 + P;  // aligned cover + window slack
+    static constexpr int SMEM_BYTES = 2 * REG * 4;
 };
 
-struct TileGeom {
-    int64_t ga, gb, out;  // global start of A range, of B range, of output
-    int na, nb, tot;
-};
-
-HS_DEV TileGeom tile_geom(int64_t b, int64_t n, int64_t w, int tpg, int to, const int64_t *part) {
-    const int64_t g = b / tpg;
-    const int t = (int)(b - g * tpg);
+template <int NT, int EO>
+__global__ void __launch_bounds__(NT)
+    k_merge_tile(const int32_t *in, int32_t *out, int64_t n, int64_t w, const int64_t *part,
+                 int tpg) {
+    using C = TileMerge<NT, EO>;
+    constexpr int TO = C::TO, P = C::P;
+    extern __shared__ __align__(16) int32_t smem[];
+    const int64_t g = blockIdx.x / tpg;
+    const int t = blockIdx.x - (int)(g * tpg);
     const MergeGeom m = merge_geom(g, n, w);
     const int64_t glen = m.alen + m.blen;
-    const int64_t o0 = (int64_t)t * to;
-    const int64_t o1 = (o0 + to) < glen ? (o0 + to) : glen;
-    const int64_t a0 = part[b];
-    const int64_t a1 = (o1 == glen) ? m.alen : part[b + 1];
-    TileGeom tg;
-    tg.ga = m.gs + a0;
-    tg.na = (int)(a1 - a0);
-    tg.gb = m.gs + w + (o0 - a0);
-    tg.nb = (int)((o1 - a1) - (o0 - a0));
-    tg.out = m.gs + o0;
-    tg.tot = (int)(o1 - o0);
-    return tg;
-}
-
-// Copy window of a range [g, g+cnt): 16-byte aligned start, end rounded up but
-// never past n4 (the last multiple of 4 <= n); keys in [hi, g+cnt) are loaded
-// by plain loads afterwards.
-struct CopyWin {
-    int64_t lo, hi;
-};
-HS_DEV CopyWin copy_window(int64_t g, int cnt, int64_t n4) {
-    CopyWin c;
-    c.lo = g & ~int64_t(3);
-    int64_t hi = (g + cnt + 3) & ~int64_t(3);
-    c.hi = hi < n4 ? hi : n4;
-    if (c.hi < c.lo) c.hi = c.lo;
-    return c;
-}
-
-template <int NT, int E>
-HS_DEV void tma_issue(const TileGeom &tg, const int32_t *in, int64_t n4, int32_t *stage,
-                      uint64_t *bar) {
-    using C = TmaMerge<NT, E>;
-    const CopyWin ca = copy_window(tg.ga, tg.na, n4);
-    const CopyWin cb = copy_window(tg.gb, tg.nb, n4);
-    const uint32_t bytes_a = (uint32_t)(ca.hi - ca.lo) * 4u;
-    const uint32_t bytes_b = (uint32_t)(cb.hi - cb.lo) * 4u;
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, bytes_a + bytes_b);
-    if (bytes_a) bulk_load(stage, in + ca.lo, bytes_a, bar);
-    if (bytes_b) bulk_load(stage + C::REG, in + cb.lo, bytes_b, bar);
-}
-
-// Merge-path split of two separate sorted arrays.
-HS_DEV int merge_path2(const int32_t *A, int na, const int32_t *B, int nb, int diag) {
-    int lo = diag > nb ? diag - nb : 0;
-    int hi = diag < na ? diag : na;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
-        else hi = mid;
+    const int64_t o0 = (int64_t)t * TO;
+    const int64_t o1 = (o0 + TO) < glen ? (o0 + TO) : glen;
+    const int64_t a0 = part[blockIdx.x];
+    const int64_t a1 = (o1 == glen) ? m.alen : part[blockIdx.x + 1];
+    const int na = (int)(a1 - a0);
+    const int tot = (int)(o1 - o0);
+    const int nb = tot - na;
+    // 16-byte aligned covers of [A + a0, + na) and [B + b0, + nb).
+    const int64_t ga = m.gs + a0, gb = m.gs + w + (o0 - a0);
+    const int64_t ca = ga & ~int64_t(3), cb = gb & ~int64_t(3);
+    const int nca = (int)(((ga + na + 3) & ~int64_t(3)) - ca) / 4;
+    const int ncb = (int)(((gb + nb + 3) & ~int64_t(3)) - cb) / 4;
+    int32_t *sA = smem, *sB = smem + C::REG;
+    for (int q = threadIdx.x; q < nca + ncb; q += NT) {
+        if (q < nca) cp_async16(sA + 4 * q, in + ca + 4 * q);
+        else cp_async16(sB + 4 * (q - nca), in + cb + 4 * (q - nca));
     }
-    return lo;
-}
+    cp_async_wait_all();
+    __syncthreads();
+    const int32_t *A = sA + (int)(ga - ca), *B = sB + (int)(gb - cb);
 
-// The E smallest keys of A[ai..] and B[bi..] in ascending order: lower half of
-// the bitonic merge of A[ai, ai+E) and reversed B[bi, bi+E), then sorted.
-template <int E>
-HS_DEV void merge_window(const int32_t *A, int ra, const int32_t *B, int rb, int32_t (&lo)[E]) {
-    int32_t a[E], b[E];
-    if (ra >= E && rb >= E) {
-#pragma unroll
-        for (int k = 0; k < E; ++k) {
-            a[k] = A[k];
-            b[k] = B[k];
+    const int diag = threadIdx.x * EO;
+    int32_t o[P];
+    if (diag < tot) {
+        int lo = diag > nb ? diag - nb : 0, hi = diag < na ? diag : na;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
+            else hi = mid;
         }
-    } else {
+        const int32_t *wA = A + lo, *wB = B + (diag - lo);
+        const int ra = na - lo, rb = nb - (diag - lo);
+        if (ra >= EO && rb >= EO) {
 #pragma unroll
-        for (int k = 0; k < E; ++k) {
-            a[k] = k < ra ? A[k] : kKeyMax;
-            b[k] = k < rb ? B[k] : kKeyMax;
+            for (int i = 0; i < P; ++i) {
+                const int j = P - 1 - i;
+                o[i] = hs_min(i < EO ? wA[i] : kKeyMax, j < EO ? wB[j] : kKeyMax);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const int j = P - 1 - i;
+                const int32_t x = (i < EO && i < ra) ? wA[i] : kKeyMax;
+                const int32_t y = (j < EO && j < rb) ? wB[j] : kKeyMax;
+                o[i] = hs_min(x, y);
+            }
         }
+        bitonic_half_clean<P>(o);
     }
+    // Stage the outputs (odd stride EO: conflict-free) for coalesced stores.
+    __syncthreads();
+    if (diag < tot) {
 #pragma unroll
-    for (int k = 0; k < E; ++k) lo[k] = hs_min(a[k], b[E - 1 - k]);
-    bitonic_half_clean<E>(lo);
-}
-
-template <int NT, int E>
-__global__ void __launch_bounds__(NT)
-    k_merge_tma(const int32_t *in, int32_t *out, int64_t n, int64_t w, const int64_t *part,
-                int tpg, int64_t ntiles, unsigned *status) {
-    using C = TmaMerge<NT, E>;
-    extern __shared__ __align__(16) int32_t smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * C::STAGE);
-    const int64_t n4 = n & ~int64_t(3);
-
-    if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_barrier_init();
+        for (int k = 0; k < EO; ++k) sA[diag + k] = o[k];
     }
     __syncthreads();
-
-    int64_t b = blockIdx.x;
-    if (b >= ntiles) return;
-    if (threadIdx.x == 0) tma_issue<NT, E>(tile_geom(b, n, w, tpg, C::TO, part), in, n4, smem, &bars[0]);
-
-    int stage = 0;
-    uint32_t parities = 0;  // bit s: parity of the next phase of barrier s
-    for (; b < ntiles; b += gridDim.x) {
-        const int64_t bn = b + gridDim.x;
-        int32_t *cur = smem + stage * C::STAGE;
-        if (bn < ntiles && threadIdx.x == 0)
-            tma_issue<NT, E>(tile_geom(bn, n, w, tpg, C::TO, part), in, n4,
-                             smem + (stage ^ 1) * C::STAGE, &bars[stage ^ 1]);
-
-        const bool ok = mbar_wait(&bars[stage], (parities >> stage) & 1u);
-        if (__syncthreads_or(!ok)) {
-            // A bulk copy did not complete in time: report it, give the copies
-            // still in flight a bounded chance to land, and leave.
-            if (threadIdx.x == 0) {
-                atomicOr(status, kStatusTimeout);
-                mbar_wait(&bars[stage], (parities >> stage) & 1u);
-                if (bn < ntiles) mbar_wait(&bars[stage ^ 1], (parities >> (stage ^ 1)) & 1u);
-            }
-            return;
-        }
-        parities ^= 1u << stage;
-
-        const TileGeom tg = tile_geom(b, n, w, tpg, C::TO, part);
-        const CopyWin ca = copy_window(tg.ga, tg.na, n4);
-        const CopyWin cb = copy_window(tg.gb, tg.nb, n4);
-        int32_t *sA = cur + (int)(tg.ga - ca.lo);
-        int32_t *sB = cur + C::REG + (int)(tg.gb - cb.lo);
-        // Keys past the last multiple of 4 of the array: plain loads.
-        const int64_t tail_a = tg.ga + tg.na - ca.hi, tail_b = tg.gb + tg.nb - cb.hi;
-        if (tail_a > 0 || tail_b > 0) {
-            if (threadIdx.x < tail_a) sA[(int)(ca.hi - tg.ga) + threadIdx.x] = in[ca.hi + threadIdx.x];
-            if (threadIdx.x < tail_b) sB[(int)(cb.hi - tg.gb) + threadIdx.x] = in[cb.hi + threadIdx.x];
-            __syncthreads();
-        }
-
-        const int diag = threadIdx.x * E;
-        if (diag < tg.tot) {
-            const int ai = merge_path2(sA, tg.na, sB, tg.nb, diag);
-            const int bi = diag - ai;
-            int32_t o[E];
-            merge_window<E>(sA + ai, tg.na - ai, sB + bi, tg.nb - bi, o);
-            int32_t *dst = out + tg.out + diag;
-            if (diag + E <= tg.tot) {
-#pragma unroll
-                for (int q = 0; q < E / 4; ++q)
-                    st_stream(reinterpret_cast<int4 *>(dst) + q,
-                              make_int4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]));
-            } else {
-#pragma unroll
-                for (int k = 0; k < E; ++k)
-                    if (diag + k < tg.tot) dst[k] = o[k];
-            }
-        }
-        __syncthreads();
-        stage ^= 1;
-    }
+    int32_t *dst = out + m.gs + o0;  // 16-byte aligned: gs and o0 are multiples of 4
+    const int n4 = tot >> 2;
+    for (int q = threadIdx.x; q < n4; q += NT)
+        st_stream(reinterpret_cast<int4 *>(dst) + q, *reinterpret_cast<const int4 *>(sA + 4 * q));
+    for (int i = 4 * n4 + threadIdx.x; i < tot; i += NT) st_stream(dst + i, sA[i]);
 }
 
 }  // namespace hs
