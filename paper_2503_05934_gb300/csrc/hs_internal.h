@@ -64,6 +64,7 @@ hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, vo
 int64_t keys_tile(int L);
 void merge_set_blocksort_threads(int nt);
 void merge_set_kernel(int k);
+void merge_set_tile(int v);
 
 // Block sort of [0, n) in tiles of keys_tile(L) keys (the merge path's first pass;
 // the whole sort when n fits one tile).

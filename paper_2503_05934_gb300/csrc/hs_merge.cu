@@ -106,7 +106,31 @@ hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, 
 // merge kernel (option "merge_kernel" 1, the default); otherwise, or with
 // option 0, the staged-load kernel with a partition pass.
 constexpr int MT_NT = 128, MT_E = 15;
-constexpr int TT_NT = 256, TT_EO = 15;
+static int g_merge_tile = 2;
+
+void merge_set_tile(int v) { g_merge_tile = v; }
+
+// Partition pass + one tiled merge launch for one level (keys).
+template <auto KERN, class C>
+static hs_status launch_tile(const int32_t *kin, int32_t *kout, int64_t n, int64_t w,
+                             int64_t *part, cudaStream_t st) {
+    constexpr int TTO = C::TO;
+    const int64_t span = 2 * w;
+    const int64_t ngroups = (n + span - 1) / span;
+    const int64_t last = n - (ngroups - 1) * span;
+    const int64_t ttpg = (span + TTO - 1) / TTO;
+    const int64_t tnb = (ngroups - 1) * ttpg + (last + TTO - 1) / TTO;
+    LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
+    k_merge_partition<<<(unsigned)((tnb + 255) / 256), 256, 0, st>>>(kin, n, w, TTO, (int)ttpg, tnb,
+                                                                     part);
+    hs_status r = launch_end(t);
+    if (r != HS_OK) return r;
+    if ((r = ensure_smem((const void *)KERN, C::SMEM_BYTES)) != HS_OK) return r;
+    constexpr int NTH = C::TO / C::EOUT;
+    t = launch_begin(K_MERGE_KEYS, st);
+    KERN<<<(unsigned)tnb, NTH, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, (int)ttpg);
+    return launch_end(t);
+}
 static int g_merge_kernel = 1;
 
 void merge_set_kernel(int k) { g_merge_kernel = k; }
@@ -125,19 +149,15 @@ static hs_status launch_merge_level(const int32_t *kin, int32_t *kout, const int
     hs_status r = HS_OK;
     LaunchToken t;
     if (!PAIRS && vec && g_merge_kernel == 1 && (n % 4) == 0) {
-        using C = TileMerge<TT_NT, TT_EO>;
-        constexpr int TTO = C::TO;
-        const int64_t ttpg = (span + TTO - 1) / TTO;
-        const int64_t tnb = (ngroups - 1) * ttpg + (last + TTO - 1) / TTO;
-        t = launch_begin(K_MERGE_PARTITION, st);
-        k_merge_partition<<<(unsigned)((tnb + 255) / 256), 256, 0, st>>>(kin, n, w, TTO, (int)ttpg,
-                                                                         tnb, part);
-        if ((r = launch_end(t)) != HS_OK) return r;
-        auto kern = k_merge_tile<TT_NT, TT_EO>;
-        if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
-        t = launch_begin(K_MERGE_KEYS, st);
-        kern<<<(unsigned)tnb, TT_NT, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, (int)ttpg);
-        return launch_end(t);
+        switch (g_merge_tile) {
+            case 0: return launch_tile<k_merge_tile<256, 15>, TileMerge<256, 15>>(kin, kout, n, w, part, st);
+            case 1: return launch_tile<k_merge_tile2<64, 31>, TileMerge2<64, 31>>(kin, kout, n, w, part, st);
+            case 2: return launch_tile<k_merge_tile2<128, 31>, TileMerge2<128, 31>>(kin, kout, n, w, part, st);
+            case 3: return launch_tile<k_merge_tile2<64, 63>, TileMerge2<64, 63>>(kin, kout, n, w, part, st);
+            case 4: return launch_tile<k_merge_tile2<128, 23>, TileMerge2<128, 23>>(kin, kout, n, w, part, st);
+            case 5: return launch_tile<k_merge_tile2<96, 31>, TileMerge2<96, 31>>(kin, kout, n, w, part, st);
+            default: return launch_tile<k_merge_tile2<192, 31>, TileMerge2<192, 31>>(kin, kout, n, w, part, st);
+        }
     }
     t = launch_begin(K_MERGE_PARTITION, st);
     k_merge_partition<<<(unsigned)((nblocks + 255) / 256), 256, 0, st>>>(kin, n, w, TO, (int)tpg,

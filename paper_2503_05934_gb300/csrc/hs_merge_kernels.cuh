@@ -18,6 +18,24 @@
 
 namespace hs {
 
+// Sorts a bitonic sequence x[0..E) ascending (half-cleaners of decreasing
+// distance, Batcher 1968).
+template <int E>
+HS_DEV void bitonic_half_clean(int32_t (&x)[E]) {
+#pragma unroll
+    for (int d = E / 2; d > 0; d >>= 1) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            if ((i & d) == 0) {
+                int32_t lo = hs_min(x[i], x[i + d]);
+                int32_t hi = hs_max(x[i], x[i + d]);
+                x[i] = lo;
+                x[i + d] = hi;
+            }
+        }
+    }
+}
+
 // Merge-path split (Odeh, Green, Mwassi, Shmueli, Birk, "Merge Path -
 // Parallel Merging Made Simple", IPDPSW 2012): the number of elements of run
 // A among the first `diag` outputs of the stable merge of A and B.
@@ -34,6 +52,26 @@ HS_DEV int merge_path(const int32_t *s, int a0, int na, int b0, int nb, int diag
         else hi = mid;
     }
     return lo;
+}
+
+// The cnt (<= EO) outputs of one thread as a sorted run: its merge-path split
+// (ai, bi) and end split (ai + na) are known, so it reads exactly its na keys
+// of A (ascending) and cnt - na keys of B (descending), with +infinity padding
+// between them, which is one bitonic sequence of P keys; a P-wide bitonic
+// merge sorts it.  Only ties between equal keys can land in either order,
+// which keys alone cannot show.
+template <int EO, int P>
+HS_DEV void exact_window_merge(const int32_t *A, int ai, const int32_t *B, int bi, int na,
+                               int cnt, int32_t (&x)[P]) {
+    const int nb = cnt - na;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        int32_t v = kKeyMax;
+        if (i < na) v = A[ai + i];
+        else if (i >= P - nb) v = B[bi + (P - 1 - i)];
+        x[i] = v;
+    }
+    bitonic_half_clean<P>(x);
 }
 
 // Merge-path split of two separate sorted arrays.
@@ -196,21 +234,6 @@ __global__ void __launch_bounds__(NT)
                                   PAIRS ? vout + base : nullptr, cnt, netset, vec != 0, smem);
 }
 
-template <int E>
-HS_DEV void bitonic_half_clean(int32_t (&x)[E]) {
-#pragma unroll
-    for (int d = E / 2; d > 0; d >>= 1) {
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-            if ((i & d) == 0) {
-                int32_t lo = hs_min(x[i], x[i + d]);
-                int32_t hi = hs_max(x[i], x[i + d]);
-                x[i] = lo;
-                x[i + d] = hi;
-            }
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Block sort, two leaves per thread (keys).  Each of the NT threads holds
@@ -495,17 +518,23 @@ HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_
             if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
             else hi = mid;
         }
-        const int32_t *wA = A + lo, *wB = B + (diag - lo);
-        const int ra = w - lo, rb = w - (diag - lo);
-        int32_t o[P];
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-            const int j = P - 1 - i;
-            const int32_t x = (i < EO && i < ra) ? wA[i] : kKeyMax;
-            const int32_t y = (j < EO && j < rb) ? wB[j] : kKeyMax;
-            o[i] = hs_min(x, y);
+        // End split: the next lane's start inside the same group, all of A at
+        // the group's end, or one more search in the warp's last lane.
+        int end = __shfl_down_sync(0xffffffffu, lo, 1);
+        const int dend = diag + EO;  // 2w is a multiple of EO
+        if (dend == 2 * w) {
+            end = w;
+        } else if ((threadIdx.x & 31) == 31) {
+            int l2 = dend > w ? dend - w : 0, h2 = dend < w ? dend : w;
+            while (l2 < h2) {
+                const int mid = (l2 + h2) >> 1;
+                if (A[mid] <= B[dend - 1 - mid]) l2 = mid + 1;
+                else h2 = mid;
+            }
+            end = l2;
         }
-        bitonic_half_clean<P>(o);
+        int32_t o[P];
+        exact_window_merge<EO, P>(A, lo, B, diag - lo, end - lo, EO, o);
 #pragma unroll
         for (int j = 0; j < EO; ++j) k[j] = o[j];
     }
@@ -668,6 +697,7 @@ HS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"
 
 template <int NT, int EO>
 struct TileMerge {
+    static constexpr int EOUT = EO;
     static constexpr int P = pow2_at_least(EO);
     static constexpr int TO = NT * EO;
     static constexpr int REG = TO + 8 + P;  // aligned cover + window slack
@@ -747,5 +777,90 @@ __global__ void __launch_bounds__(NT)
         st_stream(reinterpret_cast<int4 *>(dst) + q, *reinterpret_cast<const int4 *>(sA + 4 * q));
     for (int i = 4 * n4 + threadIdx.x; i < tot; i += NT) st_stream(dst + i, sA[i]);
 }
+
+// ---------------------------------------------------------------------------
+// Global merge level, tiled exact-window form (keys; 16-byte aligned buffers,
+// n % 4 == 0).  Like k_merge_tile, but each thread merges exactly its own EO
+// keys: its end split comes from the next lane (a shuffle), or from one extra
+// search in the warp's last lane, so the windows read each key once.
+template <int NT, int EO>
+struct TileMerge2 {
+    static constexpr int EOUT = EO;
+    static constexpr int P = pow2_at_least(EO);
+    static constexpr int TO = NT * EO;
+    static constexpr int REG = TO + 8 + 8;  // 16-byte aligned cover + slack
+    static constexpr int SMEM_BYTES = 2 * REG * 4;
+};
+
+template <int NT, int EO>
+__global__ void __launch_bounds__(NT)
+    k_merge_tile2(const int32_t *in, int32_t *out, int64_t n, int64_t w, const int64_t *part,
+                  int tpg) {
+    using C = TileMerge2<NT, EO>;
+    constexpr int TO = C::TO, P = C::P;
+    extern __shared__ __align__(16) int32_t smem[];
+    const int64_t g = blockIdx.x / tpg;
+    const int t = blockIdx.x - (int)(g * tpg);
+    const MergeGeom m = merge_geom(g, n, w);
+    const int64_t glen = m.alen + m.blen;
+    const int64_t o0 = (int64_t)t * TO;
+    const int64_t o1 = (o0 + TO) < glen ? (o0 + TO) : glen;
+    const int64_t a0 = part[blockIdx.x];
+    const int64_t a1 = (o1 == glen) ? m.alen : part[blockIdx.x + 1];
+    const int na = (int)(a1 - a0);
+    const int tot = (int)(o1 - o0);
+    const int nb = tot - na;
+    const int64_t ga = m.gs + a0, gb = m.gs + w + (o0 - a0);
+    const int64_t ca = ga & ~int64_t(3), cb = gb & ~int64_t(3);
+    const int nca = (int)(((ga + na + 3) & ~int64_t(3)) - ca) / 4;
+    const int ncb = (int)(((gb + nb + 3) & ~int64_t(3)) - cb) / 4;
+    int32_t *sA = smem, *sB = smem + C::REG;
+    for (int q = threadIdx.x; q < nca + ncb; q += NT) {
+        if (q < nca) cp_async16(sA + 4 * q, in + ca + 4 * q);
+        else cp_async16(sB + 4 * (q - nca), in + cb + 4 * (q - nca));
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int32_t *A = sA + (int)(ga - ca), *B = sB + (int)(gb - cb);
+
+    const int diag = threadIdx.x * EO;
+    const int lane = threadIdx.x & 31;
+    const int dcl = diag < tot ? diag : tot;
+    int lo = dcl > nb ? dcl - nb : 0, hi = dcl < na ? dcl : na;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] <= B[dcl - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    // End split: the next lane's start, or (last lane) one more search.
+    int end = __shfl_down_sync(0xffffffffu, lo, 1);
+    const int dend = (diag + EO) < tot ? (diag + EO) : tot;
+    if (lane == 31 || dend == tot) {
+        int l2 = dend > nb ? dend - nb : 0, h2 = dend < na ? dend : na;
+        if (dend == tot) l2 = h2 = na;
+        while (l2 < h2) {
+            const int mid = (l2 + h2) >> 1;
+            if (A[mid] <= B[dend - 1 - mid]) l2 = mid + 1;
+            else h2 = mid;
+        }
+        end = l2;
+    }
+    int32_t x[P];
+    const int cnt = dend - dcl;
+    if (cnt > 0) exact_window_merge<EO, P>(A, lo, B, dcl - lo, end - lo, cnt, x);
+    __syncthreads();
+    if (cnt > 0) {
+#pragma unroll
+        for (int k = 0; k < EO; ++k)
+            if (k < cnt) sA[diag + k] = x[k];
+    }
+    __syncthreads();
+    int32_t *dst = out + m.gs + o0;  // 16-byte aligned: gs and o0 are multiples of 4
+    const int n4 = tot >> 2;
+    for (int q = threadIdx.x; q < n4; q += NT)
+        st_stream(reinterpret_cast<int4 *>(dst) + q, *reinterpret_cast<const int4 *>(sA + 4 * q));
+    for (int i = 4 * n4 + threadIdx.x; i < tot; i += NT) st_stream(dst + i, sA[i]);
+}
+
 
 }  // namespace hs
