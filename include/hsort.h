@@ -280,7 +280,7 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *   "quick_max_levels": partition levels the quick path runs before its depth
  *     guard merge-sorts the segments still open (default -1 = automatic,
  *     4*ceil(log2 n) + 16).
- *   "blocksort_threads": 512 or 1024 (default) threads per CTA in the keys
+ *   "blocksort_threads": 512 (default) or 1024 threads per CTA in the keys
  *     block sort; each thread holds two leaves (leaf and leaf-1 keys), so
  *     the first merge tile holds (2 * leaf - 1) * threads keys.
  *   "merge_kernel": 1 (default) tiled merge levels with asynchronous 16-byte

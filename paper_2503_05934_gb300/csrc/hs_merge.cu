@@ -43,8 +43,8 @@ static hs_status launch_blocksort_t(const int32_t *kin, int32_t *kout, const int
 }
 
 // Keys: two leaves (L and L-1 keys) per thread (block_sort_tile3).  512 or
-// 1024 threads per CTA (tile (2L-1)*512 or (2L-1)*1024 keys); 1024 default.
-static int g_bs2_threads = 1024;
+// 1024 threads per CTA (tile (2L-1)*512 or (2L-1)*1024 keys); 512 default.
+static int g_bs2_threads = 512;
 
 int64_t keys_tile(int L) { return (int64_t)g_bs2_threads * (2 * L - 1); }
 
@@ -105,7 +105,6 @@ hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, 
 // Keys with 16-byte aligned buffers and n % 4 == 0: the streaming bulk-copy
 // merge kernel (option "merge_kernel" 1, the default); otherwise, or with
 // option 0, the staged-load kernel with a partition pass.
-constexpr int MT_NT = 128, MT_E = 15;
 static int g_merge_tile = 2;
 
 void merge_set_tile(int v) { g_merge_tile = v; }

@@ -63,13 +63,13 @@ HS_DEV int merge_path(const int32_t *s, int a0, int na, int b0, int nb, int diag
 template <int EO, int P>
 HS_DEV void exact_window_merge(const int32_t *A, int ai, const int32_t *B, int bi, int na,
                                int cnt, int32_t (&x)[P]) {
-    const int nb = cnt - na;
+    const int tb = P - (cnt - na);  // first slot of the descending B part
+    const int32_t *pa = A + ai, *pb = B + bi + (P - 1);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-        int32_t v = kKeyMax;
-        if (i < na) v = A[ai + i];
-        else if (i >= P - nb) v = B[bi + (P - 1 - i)];
-        x[i] = v;
+        // One load per slot: A ascending, B descending, +infinity in between.
+        const int32_t v = (i < na) ? pa[i] : pb[-i];
+        x[i] = (i < na || i >= tb) ? v : kKeyMax;
     }
     bitonic_half_clean<P>(x);
 }
@@ -431,7 +431,7 @@ struct BlockSort3 {
     static constexpr int EO = 2 * L - 1;
     static constexpr int P = pow2_at_least(EO);
     static constexpr int T = NT * EO;
-    static constexpr int SZ = T + P + 32;  // tile + window slack
+    static constexpr int SZ = T + P + 32 + NT / 32 + 1;  // tile + window slack + warp splits
     static constexpr int SMEM_BYTES = SZ * 4;
 };
 
@@ -479,6 +479,7 @@ HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_
                              bool vec, int32_t *s) {
     using C = BlockSort3<NT, L>;
     constexpr int EO = C::EO, P = C::P, T = C::T;
+    int *wsplit = s + C::T + C::P + 32;  // one split per warp
 
     if (vec && cnt == T && (T % 4) == 0) {
         const int4 *s4 = reinterpret_cast<const int4 *>(kin);
@@ -519,20 +520,16 @@ HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_
             else hi = mid;
         }
         // End split: the next lane's start inside the same group, all of A at
-        // the group's end, or one more search in the warp's last lane.
+        // the group's end, or (the warp's last lane) the next warp's first
+        // lane's start, passed through shared memory.
         int end = __shfl_down_sync(0xffffffffu, lo, 1);
         const int dend = diag + EO;  // 2w is a multiple of EO
-        if (dend == 2 * w) {
-            end = w;
-        } else if ((threadIdx.x & 31) == 31) {
-            int l2 = dend > w ? dend - w : 0, h2 = dend < w ? dend : w;
-            while (l2 < h2) {
-                const int mid = (l2 + h2) >> 1;
-                if (A[mid] <= B[dend - 1 - mid]) l2 = mid + 1;
-                else h2 = mid;
-            }
-            end = l2;
+        if (2 * w > 32 * EO) {  // groups span warps: exchange warp-boundary splits
+            if ((threadIdx.x & 31) == 0) wsplit[threadIdx.x >> 5] = lo;
+            __syncthreads();
+            if ((threadIdx.x & 31) == 31 && dend != 2 * w) end = wsplit[(threadIdx.x >> 5) + 1];
         }
+        if (dend == 2 * w) end = w;
         int32_t o[P];
         exact_window_merge<EO, P>(A, lo, B, diag - lo, end - lo, EO, o);
 #pragma unroll
@@ -832,19 +829,17 @@ __global__ void __launch_bounds__(NT)
         if (A[mid] <= B[dcl - 1 - mid]) lo = mid + 1;
         else hi = mid;
     }
-    // End split: the next lane's start, or (last lane) one more search.
+    // End split: the next lane's start, or (the warp's last lane) the next
+    // warp's first lane's start through shared memory; the tile end takes
+    // all of A.
+    __shared__ int wsplit[NT / 32 + 1];
     int end = __shfl_down_sync(0xffffffffu, lo, 1);
+    if (lane == 0) wsplit[threadIdx.x >> 5] = lo;
+    if (threadIdx.x == 0) wsplit[NT / 32] = na;
+    __syncthreads();
     const int dend = (diag + EO) < tot ? (diag + EO) : tot;
-    if (lane == 31 || dend == tot) {
-        int l2 = dend > nb ? dend - nb : 0, h2 = dend < na ? dend : na;
-        if (dend == tot) l2 = h2 = na;
-        while (l2 < h2) {
-            const int mid = (l2 + h2) >> 1;
-            if (A[mid] <= B[dend - 1 - mid]) l2 = mid + 1;
-            else h2 = mid;
-        }
-        end = l2;
-    }
+    if (lane == 31) end = wsplit[(threadIdx.x >> 5) + 1];
+    if (dend == tot) end = na;
     int32_t x[P];
     const int cnt = dend - dcl;
     if (cnt > 0) exact_window_merge<EO, P>(A, lo, B, dcl - lo, end - lo, cnt, x);

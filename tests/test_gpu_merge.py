@@ -154,8 +154,12 @@ def test_workspace_reuse_and_launch_count(hs):
         torch.cuda.synchronize()
         assert np.array_equal(t.cpu().numpy(), np.sort(a))
     # 1 block sort + 2 launches (partition, merge) per global level; tile
-    # (2*8-1) * 1024 = 15360 keys, 2^20 / 15360 -> 7 levels
-    assert hs.hs_launch_count() - before == 3 * (1 + 2 * 7)
+    # (2*8-1) * 512 = 7680 keys, 2^20 / 7680 -> 8 levels
+    tile = int(hs.lib().hs_keys_tile(hs.netset_mask("6To8")))
+    levels = 0
+    while tile << levels < n:
+        levels += 1
+    assert hs.hs_launch_count() - before == 3 * (1 + 2 * levels)
 
 
 def test_tail_not_multiple_of_four(hs):
@@ -187,8 +191,8 @@ def test_tuning_options_keep_results(hs, threads, kernel):
                 a = g.random_i32(n, n + threads + kernel)
                 assert np.array_equal(gpu_sort(hs, a, "merge", netset), oracle.merge_sort(a, netset))
     finally:
-        hs.hs_set_option("blocksort_threads", 1024)
-        hs.hs_set_option("merge_kernel", 0)
+        hs.hs_set_option("blocksort_threads", 512)
+        hs.hs_set_option("merge_kernel", 1)
 
 
 def test_profiling_counters(hs):
@@ -203,7 +207,11 @@ def test_profiling_counters(hs):
         n_mk, ms_mk = hs.hs_prof_read("merge_keys")
     finally:
         hs.hs_prof_enable(False)
-    assert n_bs == 1 and n_mk == 5 and ms_bs > 0 and ms_mk > 0  # 2^18 / 15360 -> 5 levels
+    tile = int(hs.lib().hs_keys_tile(hs.netset_mask("6To8")))
+    levels = 0
+    while tile << levels < (1 << 18):
+        levels += 1
+    assert n_bs == 1 and n_mk == levels and ms_bs > 0 and ms_mk > 0
 
 
 def test_full_size_keys_2p28(hs):
