@@ -280,9 +280,11 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *   "quick_max_levels": partition levels the quick path runs before its depth
  *     guard merge-sorts the segments still open (default -1 = automatic,
  *     4*ceil(log2 n) + 16).
- *   "blocksort_threads": 512 (default) or 1024 threads per CTA in the keys
- *     block sort; each thread holds two leaves (leaf and leaf-1 keys), so
- *     the first merge tile holds (2 * leaf - 1) * threads keys.
+ *   "blocksort_shape": keys block-sort shape, 0: 512 threads x 2 leaves,
+ *     1: 1024 x 2, 2 (default): 256 x 4, 3: 512 x 4.  A thread holds its
+ *     leaves as leaf, ..., leaf, leaf-1 keys, so the first merge tile holds
+ *     (leaves * leaf - 1) * threads keys.
+ *   "blocksort_threads": 512 or 1024: shape 0 or 1.
  *   "merge_kernel": 1 (default) tiled merge levels with asynchronous 16-byte
  *     staging and odd outputs per thread (used for keys when both buffers
  *     are 16-byte aligned and n % 4 == 0), 0 staged-load serial merges.

@@ -63,6 +63,7 @@ hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, vo
 // Tile of the keys block sort for leaf size L, and its thread-count option.
 int64_t keys_tile(int L);
 void merge_set_blocksort_threads(int nt);
+void merge_set_blocksort_shape(int v);
 void merge_set_kernel(int k);
 void merge_set_tile(int v);
 

@@ -42,19 +42,24 @@ static hs_status launch_blocksort_t(const int32_t *kin, int32_t *kout, const int
     return launch_end(t);
 }
 
-// Keys: two leaves (L and L-1 keys) per thread (block_sort_tile3).  512 or
-// 1024 threads per CTA (tile (2L-1)*512 or (2L-1)*1024 keys); 512 default.
-static int g_bs2_threads = 512;
+// Keys: block_sort_tile3 with two leaves (L, L-1) or four leaves (L, L, L,
+// L-1) per thread.  Shapes (option "blocksort_shape"):
+//   0: 512 threads x 2 leaves   1: 1024 x 2   2: 256 x 4 (default)   3: 512 x 4
+static int g_bs_shape = 2;
 
-int64_t keys_tile(int L) { return (int64_t)g_bs2_threads * (2 * L - 1); }
+static int bs_threads() { return (g_bs_shape == 1) ? 1024 : (g_bs_shape == 2) ? 256 : 512; }
+static int bs_leaves() { return g_bs_shape >= 2 ? 4 : 2; }
 
-void merge_set_blocksort_threads(int nt) { g_bs2_threads = (nt == 512) ? 512 : 1024; }
+int64_t keys_tile(int L) { return (int64_t)bs_threads() * (bs_leaves() * L - 1); }
 
-template <int NT, int L>
+void merge_set_blocksort_threads(int nt) { g_bs_shape = (nt == 1024) ? 1 : 0; }
+void merge_set_blocksort_shape(int v) { g_bs_shape = v; }
+
+template <int NT, int L, int LEAVES>
 static hs_status launch_blocksort2_t(const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
                                      int vec, cudaStream_t st) {
-    using C = BlockSort3<NT, L>;
-    auto kern = k_blocksort3<NT, L>;
+    using C = BlockSort3<NT, L, LEAVES>;
+    auto kern = k_blocksort3<NT, L, LEAVES>;
     hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
     if (r != HS_OK) return r;
     const int64_t grid = (n + C::T - 1) / C::T;
@@ -63,17 +68,17 @@ static hs_status launch_blocksort2_t(const int32_t *kin, int32_t *kout, int64_t 
     return launch_end(t);
 }
 
-template <int NT>
+template <int NT, int LEAVES>
 static hs_status launch_blocksort2_nt(int L, const int32_t *kin, int32_t *kout, int64_t n,
                                       hs_netset s, int vec, cudaStream_t st) {
     switch (L) {
-        case 1: return launch_blocksort2_t<NT, 1>(kin, kout, n, s, vec, st);
-        case 3: return launch_blocksort2_t<NT, 3>(kin, kout, n, s, vec, st);
-        case 4: return launch_blocksort2_t<NT, 4>(kin, kout, n, s, vec, st);
-        case 5: return launch_blocksort2_t<NT, 5>(kin, kout, n, s, vec, st);
-        case 6: return launch_blocksort2_t<NT, 6>(kin, kout, n, s, vec, st);
-        case 7: return launch_blocksort2_t<NT, 7>(kin, kout, n, s, vec, st);
-        case 8: return launch_blocksort2_t<NT, 8>(kin, kout, n, s, vec, st);
+        case 1: return launch_blocksort2_t<NT, 1, LEAVES>(kin, kout, n, s, vec, st);
+        case 3: return launch_blocksort2_t<NT, 3, LEAVES>(kin, kout, n, s, vec, st);
+        case 4: return launch_blocksort2_t<NT, 4, LEAVES>(kin, kout, n, s, vec, st);
+        case 5: return launch_blocksort2_t<NT, 5, LEAVES>(kin, kout, n, s, vec, st);
+        case 6: return launch_blocksort2_t<NT, 6, LEAVES>(kin, kout, n, s, vec, st);
+        case 7: return launch_blocksort2_t<NT, 7, LEAVES>(kin, kout, n, s, vec, st);
+        case 8: return launch_blocksort2_t<NT, 8, LEAVES>(kin, kout, n, s, vec, st);
     }
     return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
 }
@@ -82,8 +87,12 @@ template <bool PAIRS>
 static hs_status launch_blocksort(int L, const int32_t *kin, int32_t *kout, const int32_t *vin,
                                   int32_t *vout, int64_t n, hs_netset s, int vec, cudaStream_t st) {
     if constexpr (!PAIRS) {
-        return g_bs2_threads == 512 ? launch_blocksort2_nt<512>(L, kin, kout, n, s, vec, st)
-                                    : launch_blocksort2_nt<1024>(L, kin, kout, n, s, vec, st);
+        switch (g_bs_shape) {
+            case 1: return launch_blocksort2_nt<1024, 2>(L, kin, kout, n, s, vec, st);
+            case 2: return launch_blocksort2_nt<256, 4>(L, kin, kout, n, s, vec, st);
+            case 3: return launch_blocksort2_nt<512, 4>(L, kin, kout, n, s, vec, st);
+            default: return launch_blocksort2_nt<512, 2>(L, kin, kout, n, s, vec, st);
+        }
     }
     switch (L) {
         case 1: return launch_blocksort_t<1, PAIRS>(kin, kout, vin, vout, n, s, vec, st);

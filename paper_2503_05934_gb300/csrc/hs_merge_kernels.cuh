@@ -426,9 +426,10 @@ __global__ void __launch_bounds__(NT)
 // odd, neighbouring threads' windows and their own EO-key slots fall on
 // different banks, so the tile is stored unpadded.
 
-template <int NT, int L>
+template <int NT, int L, int LEAVES = 2>
 struct BlockSort3 {
-    static constexpr int EO = 2 * L - 1;
+    static_assert(LEAVES == 2 || LEAVES == 4, "two or four leaves per thread");
+    static constexpr int EO = LEAVES * L - 1;
     static constexpr int P = pow2_at_least(EO);
     static constexpr int T = NT * EO;
     static constexpr int SZ = T + P + 32 + NT / 32 + 1;  // tile + window slack + warp splits
@@ -474,10 +475,10 @@ HS_DEV void register_merge(int32_t *x) {
     for (int i = 0; i < N1 + N2; ++i) x[i] = i < P / 2 ? lo[i] : hi[i - P / 2];
 }
 
-template <int NT, int L>
+template <int NT, int L, int LEAVES = 2>
 HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_t netset,
                              bool vec, int32_t *s) {
-    using C = BlockSort3<NT, L>;
+    using C = BlockSort3<NT, L, LEAVES>;
     constexpr int EO = C::EO, P = C::P, T = C::T;
     int *wsplit = s + C::T + C::P + 32;  // one split per warp
 
@@ -496,12 +497,23 @@ HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_
 #pragma unroll
     for (int j = 0; j < EO; ++j) k[j] = s[my0 + j];
 
-    if constexpr (L > 1) {
+    if constexpr (LEAVES == 2 && L > 1) {
         const int r0 = hs_min(hs_max(cnt - my0, 0), L);
         const int r1 = hs_min(hs_max(cnt - my0 - L, 0), L - 1);
         sort_leaf<L>(k, r0, netset);
         sort_leaf<L - 1>(k + L, r1, netset);
         register_merge<L, L - 1, P>(k);
+    } else if constexpr (LEAVES == 4) {
+        // Leaves of L, L, L and L - 1 keys (for L = 1: single keys, merged).
+        if constexpr (L > 1) {
+#pragma unroll
+            for (int h = 0; h < 3; ++h)
+                sort_leaf<L>(k + h * L, hs_min(hs_max(cnt - my0 - h * L, 0), L), netset);
+            sort_leaf<L - 1>(k + 3 * L, hs_min(hs_max(cnt - my0 - 3 * L, 0), L - 1), netset);
+        }
+        register_merge<L, L, P / 2>(k);
+        register_merge<L, L - 1, P / 2>(k + 2 * L);
+        register_merge<2 * L, 2 * L - 1, P>(k);
     }
 
     for (int w = EO; w < T && w < cnt; w *= 2) {
@@ -551,14 +563,14 @@ HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_
     }
 }
 
-template <int NT, int L>
+template <int NT, int L, int LEAVES = 2>
 __global__ void __launch_bounds__(NT)
     k_blocksort3(const int32_t *kin, int32_t *kout, int64_t n, uint32_t netset, int vec) {
-    constexpr int T = BlockSort3<NT, L>::T;
+    constexpr int T = BlockSort3<NT, L, LEAVES>::T;
     extern __shared__ __align__(16) int32_t smem[];
     const int64_t base = (int64_t)blockIdx.x * T;
     const int cnt = (int)((n - base) < T ? (n - base) : T);
-    block_sort_tile3<NT, L>(kin + base, kout + base, cnt, netset, vec != 0, smem);
+    block_sort_tile3<NT, L, LEAVES>(kin + base, kout + base, cnt, netset, vec != 0, smem);
 }
 
 // ---------------------------------------------------------------------------

@@ -295,6 +295,12 @@ hs_status hs_set_option(const char *name, int64_t value) {
         merge_set_tile((int)value);
         return HS_OK;
     }
+    if (std::strcmp(name, "blocksort_shape") == 0) {
+        if (value < 0 || value > 3)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_shape must be 0..3");
+        merge_set_blocksort_shape((int)value);
+        return HS_OK;
+    }
     if (std::strcmp(name, "blocksort_threads") == 0) {
         if (value != 512 && value != 1024)
             return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_threads must be 512 or 1024");

@@ -165,8 +165,8 @@ def test_workspace_reuse_and_launch_count(hs):
 def test_tail_not_multiple_of_four(hs):
     """Aligned buffers whose length is not a multiple of 4: the bulk-copy merge
     loads the last keys with plain loads."""
-    for n in [8192 * 2 + 1, 8192 * 2 + 2, 8192 * 2 + 3, 8192 * 5 + 3, 1_000_001, 1_000_002,
-              (1 << 22) + 3]:
+    for n in [8192 * 2 + 1, 8192 * 2 + 2, 8192 * 2 + 3, 8192 * 5 + 3, 7936 * 3 + 1, 7936 * 4 + 2,
+              1_000_001, 1_000_002, (1 << 22) + 3]:
         a = g.random_i32(n, 5000 + n)
         assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), n
 
@@ -179,11 +179,11 @@ def test_many_duplicates_and_runs(hs):
         assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), mod
 
 
-@pytest.mark.parametrize("threads", [512, 1024])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
 @pytest.mark.parametrize("kernel", [0, 1])
-def test_tuning_options_keep_results(hs, threads, kernel):
-    """Block-sort CTA size and merge-level kernel change speed, not bytes."""
-    hs.hs_set_option("blocksort_threads", threads)
+def test_tuning_options_keep_results(hs, shape, kernel):
+    """Block-sort shape and merge-level kernel change speed, not bytes."""
+    hs.hs_set_option("blocksort_shape", shape)
     hs.hs_set_option("merge_kernel", kernel)
     try:
         for netset in ["6To8", "3To5", "none", "Odd"]:
@@ -191,7 +191,7 @@ def test_tuning_options_keep_results(hs, threads, kernel):
                 a = g.random_i32(n, n + threads + kernel)
                 assert np.array_equal(gpu_sort(hs, a, "merge", netset), oracle.merge_sort(a, netset))
     finally:
-        hs.hs_set_option("blocksort_threads", 512)
+        hs.hs_set_option("blocksort_shape", 2)
         hs.hs_set_option("merge_kernel", 1)
 
 
