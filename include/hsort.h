@@ -149,7 +149,8 @@ HS_API hs_status hs_sort_i32_noalloc(int32_t *d_keys, size_t n, hs_netset s, hs_
  * timing candidates on the caller's data. */
 typedef struct {
     hs_netset netset;      /* leaf networks (Table 3 set; leaf = largest size) */
-    int32_t block_threads; /* 512 or 1024; one tile holds 2*leaf*block_threads keys */
+    int32_t block_threads; /* 256 (four leaves per thread) or 512 (two leaves per
+                              thread); a tile holds (leaves*leaf - 1)*block_threads keys */
     int32_t ctas_per_sm;   /* persistent CTAs per SM, 1..8; 0 = as many as fit */
     int32_t reserved;      /* must be 0 */
 } hs_plan;

@@ -121,7 +121,7 @@ def _i64_dev(t: torch.Tensor, name: str) -> None:
         raise ValueError(f"{name} must be a contiguous int64 CUDA tensor")
 
 
-def make_plan(netset="6To8", block_threads=512, ctas_per_sm=0) -> Plan:
+def make_plan(netset="6To8", block_threads=256, ctas_per_sm=0) -> Plan:
     return Plan(netset_mask(netset), int(block_threads), int(ctas_per_sm), 0)
 
 

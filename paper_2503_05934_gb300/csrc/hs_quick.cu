@@ -30,7 +30,8 @@ namespace hs {
 constexpr int QS_NT = 256;
 constexpr int QS_IPT = 32;
 constexpr int QS_C = QS_NT * QS_IPT;  // keys per partition chunk
-constexpr int QS_BS_NT = 1024;        // small-segment sort: tile = 1024 * leaf
+constexpr int QS_BS_NT = 256;  // small-segment sort: 256 threads x four leaves
+static int64_t qs_tile(int L) { return (int64_t)QS_BS_NT * (4 * L - 1); }
 
 struct QSeg {
     int64_t begin, end, chunk0;
@@ -274,11 +275,11 @@ template <int L>
 __global__ void __launch_bounds__(QS_BS_NT)
     k_qs_small(const QSmall *small, const int32_t *X, const int32_t *Y, int32_t *Xw,
                uint32_t netset) {
-    extern __shared__ int32_t smem[];
+    extern __shared__ __align__(16) int32_t smem[];
     const QSmall s = small[blockIdx.x];
     const int32_t *src = s.buf ? Y : X;
-    block_sort_tile<QS_BS_NT, L, false>(src + s.begin, Xw + s.begin, nullptr, nullptr,
-                                        (int)(s.end - s.begin), netset, false, smem);
+    block_sort_tile3<QS_BS_NT, L, 4>(src + s.begin, Xw + s.begin, (int)(s.end - s.begin), netset,
+                                     false, smem);
 }
 
 // ---------------------------------------------------------------- host side
@@ -324,7 +325,7 @@ void quick_set_max_levels(int64_t v) { qs_option_max_levels = v; }
 template <int L>
 static hs_status launch_small_t(const QSmall *small, int64_t nsmall, const int32_t *X,
                                 const int32_t *Y, int32_t *Xw, hs_netset s, cudaStream_t st) {
-    const int smem = blocksort_smem_words<QS_BS_NT, L>() * (int)sizeof(int32_t);
+    const int smem = BlockSort3<QS_BS_NT, L, 4>::SMEM_BYTES;
     auto kern = k_qs_small<L>;
     hs_status r = ensure_smem((const void *)kern, smem);
     if (r != HS_OK) return r;
@@ -375,9 +376,9 @@ hs_status quick_sort(int32_t *d_keys, size_t n_, hs_netset s, void *d_ws, size_t
                      cudaStream_t st) {
     const int64_t n = (int64_t)n_;
     const int L = leaf_size(s);
-    const int64_t tile = (int64_t)QS_BS_NT * L;
+    const int64_t tile = qs_tile(L);
     const int vec = aligned(d_keys, 16) ? 1 : 0;
-    if (n <= tile) return blocksort_launch(L, d_keys, d_keys, n, s, vec, st);
+    if (n <= keys_tile(L)) return blocksort_launch(L, d_keys, d_keys, n, s, vec, st);
 
     const QLayout q = qs_layout(n_);
     if (!d_ws || ws_bytes < q.total)

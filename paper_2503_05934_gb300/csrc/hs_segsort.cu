@@ -46,11 +46,11 @@ HS_DEV void window_merge(const int32_t *A, int ra, const int32_t *B, int rb, int
 // merged into runs of 2w in dst.  Output chunks of T keys; their merge-path
 // splits are searched in parallel (one thread per chunk boundary), then each
 // chunk is staged in shared memory and merged with per-thread windows.
-template <int NT, int L>
+template <int NT, int L, int LV>
 HS_DEV void cta_merge_level(const int32_t *src, int32_t *dst, int64_t n, int64_t w, int32_t *s,
                             int64_t *split) {
-    using C = BlockSort2<NT, L>;
-    constexpr int T = C::T, E = C::E, P = C::P;
+    using C = BlockSort3<NT, L, LV>;
+    constexpr int T = C::T, E = C::EO, P = C::P;
     const int64_t span = 2 * w;
     const int64_t ngroups = (n + span - 1) / span;
     const int64_t tpg = (span + T - 1) / T;
@@ -121,14 +121,14 @@ HS_DEV void cta_merge_level(const int32_t *src, int32_t *dst, int64_t n, int64_t
     }
 }
 
-template <int NT, int L>
+template <int NT, int L, int LV>
 HS_DEV void sort_segment(const SegDesc &d, uint32_t netset, int32_t *s, int64_t *split) {
-    using C = BlockSort2<NT, L>;
+    using C = BlockSort3<NT, L, LV>;
     constexpr int T = C::T;
     const int64_t n = d.n;
     if (n <= 1) return;
     if (n <= T) {
-        block_sort_tile2<NT, L>(d.keys, d.keys, (int)n, netset, aligned16(d.keys), s);
+        block_sort_tile3<NT, L, LV>(d.keys, d.keys, (int)n, netset, aligned16(d.keys), s);
         return;
     }
     int levels = 0;
@@ -139,18 +139,18 @@ HS_DEV void sort_segment(const SegDesc &d, uint32_t netset, int32_t *s, int64_t 
     const bool vec = aligned16(d.keys) && aligned16(cur);
     for (int64_t base = 0; base < n; base += T) {
         const int cnt = (int)std::min<int64_t>(T, n - base);
-        block_sort_tile2<NT, L>(d.keys + base, cur + base, cnt, netset, vec, s);
+        block_sort_tile3<NT, L, LV>(d.keys + base, cur + base, cnt, netset, vec, s);
         __syncthreads();
     }
     for (int64_t w = T; w < n; w *= 2) {
-        cta_merge_level<NT, L>(cur, alt, n, w, s, split);
+        cta_merge_level<NT, L, LV>(cur, alt, n, w, s, split);
         int32_t *tmp = cur;
         cur = alt;
         alt = tmp;
     }
 }
 
-template <int NT, int L>
+template <int NT, int L, int LV>
 __global__ void __launch_bounds__(NT)
     k_seg_sort(const SegDesc *descs, int64_t ndesc, unsigned long long *head, uint32_t netset) {
     extern __shared__ __align__(16) int32_t smem[];
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(NT)
         const unsigned long long item = s_item;
         if (item >= (unsigned long long)ndesc) break;
         const SegDesc d = descs[item];
-        sort_segment<NT, L>(d, netset, smem, s_split);
+        sort_segment<NT, L, LV>(d, netset, smem, s_split);
         __syncthreads();
     }
 }
@@ -194,10 +194,10 @@ struct SegKernelInfo {
     int max_occ;
 };
 
-template <int NT, int L>
+template <int NT, int L, int LV>
 static hs_status seg_kernel_info(SegKernelInfo *out) {
-    using C = BlockSort2<NT, L>;
-    auto kern = k_seg_sort<NT, L>;
+    using C = BlockSort3<NT, L, LV>;
+    auto kern = k_seg_sort<NT, L, LV>;
     hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
     if (r != HS_OK) return r;
     int occ = 0;
@@ -209,24 +209,26 @@ static hs_status seg_kernel_info(SegKernelInfo *out) {
     return HS_OK;
 }
 
-template <int NT>
+template <int NT, int LV>
 static hs_status seg_kernel_info_nt(int L, SegKernelInfo *out) {
     switch (L) {
-        case 1: return seg_kernel_info<NT, 1>(out);
-        case 3: return seg_kernel_info<NT, 3>(out);
-        case 4: return seg_kernel_info<NT, 4>(out);
-        case 5: return seg_kernel_info<NT, 5>(out);
-        case 6: return seg_kernel_info<NT, 6>(out);
-        case 7: return seg_kernel_info<NT, 7>(out);
-        case 8: return seg_kernel_info<NT, 8>(out);
+        case 1: return seg_kernel_info<NT, 1, LV>(out);
+        case 3: return seg_kernel_info<NT, 3, LV>(out);
+        case 4: return seg_kernel_info<NT, 4, LV>(out);
+        case 5: return seg_kernel_info<NT, 5, LV>(out);
+        case 6: return seg_kernel_info<NT, 6, LV>(out);
+        case 7: return seg_kernel_info<NT, 7, LV>(out);
+        case 8: return seg_kernel_info<NT, 8, LV>(out);
     }
     return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
 }
 
+// CTA shapes of the batched kernel: 256 threads hold four leaves each, 512
+// threads two leaves each.
 static hs_status seg_kernel(int nt, int L, SegKernelInfo *out) {
-    if (nt == 512) return seg_kernel_info_nt<512>(L, out);
-    if (nt == 1024) return seg_kernel_info_nt<1024>(L, out);
-    return fail(HS_ERR_INVALID_ARG, "plan block_threads must be 512 or 1024");
+    if (nt == 256) return seg_kernel_info_nt<256, 4>(L, out);
+    if (nt == 512) return seg_kernel_info_nt<512, 2>(L, out);
+    return fail(HS_ERR_INVALID_ARG, "plan block_threads must be 256 or 512");
 }
 
 static int sm_count() {
@@ -242,15 +244,15 @@ static int sm_count() {
 hs_plan default_seg_plan(hs_netset s) {
     hs_plan p{};
     p.netset = s;
-    p.block_threads = 512;
+    p.block_threads = 256;
     p.ctas_per_sm = 0;  // as many as fit
     return p;
 }
 
 hs_status check_plan(const hs_plan &p) {
     if (!netset_ok(p.netset)) return fail(HS_ERR_INVALID_ARG, "plan netset has bits outside sizes 3..8");
-    if (p.block_threads != 512 && p.block_threads != 1024)
-        return fail(HS_ERR_INVALID_ARG, "plan block_threads must be 512 or 1024");
+    if (p.block_threads != 256 && p.block_threads != 512)
+        return fail(HS_ERR_INVALID_ARG, "plan block_threads must be 256 or 512");
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 8)
         return fail(HS_ERR_INVALID_ARG, "plan ctas_per_sm must be 0..8");
     return HS_OK;

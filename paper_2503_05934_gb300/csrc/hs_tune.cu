@@ -2,7 +2,7 @@
 //
 // The autotuner times candidate plans on the caller's own segments: leaf
 // network set (leaf size 8, 7, 5 or 4: {6,7,8}, {3,5,7}, {3,4,5}, {3,4}),
-// CTA size (512 or 1024 threads, i.e. the block-sort tile) and persistent
+// CTA shape (256 threads x four leaves or 512 threads x two leaves) and persistent
 // CTAs per SM.  Every plan produces the same bytes; only the time differs.
 // Winners are cached in-process by device name and size buckets and can be
 // saved to / loaded from a small JSON file.
@@ -125,7 +125,7 @@ hs_status autotune(int32_t *d_keys, size_t n_keys, const int64_t *d_offsets, siz
         return fail_cuda(e, "autotune: events");
     }
     const hs_netset sets[] = {HS_NETS_6TO8, HS_NETS_ODD, HS_NETS_3TO5, HS_NETS_3TO4};
-    const int threads[] = {512, 1024};
+    const int threads[] = {256, 512};
     const int ctas[] = {0, 1, 2};
     float best_t = 1e30f;
     hs_plan best_p = default_seg_plan(HS_NETS_6TO8);

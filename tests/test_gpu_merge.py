@@ -188,7 +188,7 @@ def test_tuning_options_keep_results(hs, shape, kernel):
     try:
         for netset in ["6To8", "3To5", "none", "Odd"]:
             for n in [1, 7, 8191, 16385, 100_003, 1 << 20]:
-                a = g.random_i32(n, n + threads + kernel)
+                a = g.random_i32(n, n + 10 * shape + kernel)
                 assert np.array_equal(gpu_sort(hs, a, "merge", netset), oracle.merge_sort(a, netset))
     finally:
         hs.hs_set_option("blocksort_shape", 2)

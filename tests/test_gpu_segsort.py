@@ -57,11 +57,12 @@ def test_log_uniform_mix_against_oracle(hs):
 
 
 @pytest.mark.parametrize("netset", ["6To8", "Odd", "3To5", "3To4", "none"])
-@pytest.mark.parametrize("threads", [512, 1024])
+@pytest.mark.parametrize("threads", [256, 512])
 @pytest.mark.parametrize("ctas", [0, 1, 2])
 def test_every_plan_gives_the_same_bytes(hs, netset, threads, ctas):
-    sizes = np.array([0, 1, 2, 3, 9, 100, 1023, 1024, 1025, 8191, 8192, 8193, 16383, 16384,
-                      16385, 40_000, 65_536, 5, 7, 12_345], np.int64)
+    sizes = np.array([0, 1, 2, 3, 9, 100, 1023, 1024, 1025, 7679, 7680, 7681, 7935, 7936, 7937,
+                      8191, 8192, 8193, 15_360, 15_873, 16383, 16384, 16385, 40_000, 65_536, 5, 7,
+                      12_345], np.int64)
     keys, off, _ = g.segmented(0, 77, sizes=sizes)
     want = oracle.segsort(keys, off, "merge", "6To8")
     plan = hs.make_plan(netset, threads, ctas)
@@ -80,7 +81,7 @@ def test_large_segments_and_many_merge_chunks(hs):
 def test_unaligned_segment_starts(hs):
     sizes = np.array([1, 2, 3, 5, 8190, 16387, 33_001, 4, 70_000], np.int64)
     keys, off, _ = g.segmented(0, 12, sizes=sizes)
-    for plan in [hs.make_plan("6To8", 512), hs.make_plan("6To8", 1024), hs.make_plan("Odd", 512)]:
+    for plan in [hs.make_plan("6To8", 256), hs.make_plan("6To8", 512), hs.make_plan("Odd", 256)]:
         assert np.array_equal(gpu_segsort(hs, keys, off, plan=plan),
                               oracle.segsort(keys, off, "merge", "6To8"))
 
@@ -91,7 +92,7 @@ def test_graph_replay(hs):
     want = oracle.segsort(keys, off, "merge", "6To8")
     tk, to = _dev(hs, keys, off)
     pristine = tk.clone()
-    graph = hs.hs_segsort_capture(tk, to, hs.make_plan("6To8", 512))
+    graph = hs.hs_segsort_capture(tk, to, hs.make_plan("6To8", 256))
     for _ in range(3):
         tk.copy_(pristine)
         graph.launch()
@@ -112,7 +113,7 @@ def test_autotune_restores_keys_and_caches(hs, tmp_path):
     keys, off, _ = g.segmented(1500, 8)
     tk, to = _dev(hs, keys, off)
     plan, ms = hs.hs_segsort_autotune(tk, to)
-    assert ms > 0 and plan.block_threads in (512, 1024)
+    assert ms > 0 and plan.block_threads in (256, 512)
     assert np.array_equal(tk.cpu().numpy(), keys)  # input untouched
     again, ms2 = hs.hs_segsort_autotune(tk, to)  # cache hit: same plan, no timing
     assert again.as_dict() == plan.as_dict() and ms2 == ms
