@@ -64,11 +64,13 @@ template <int EO, int P>
 HS_DEV void exact_window_merge(const int32_t *A, int ai, const int32_t *B, int bi, int na,
                                int cnt, int32_t (&x)[P]) {
     const int tb = P - (cnt - na);  // first slot of the descending B part
-    const int32_t *pa = A + ai, *pb = B + bi + (P - 1);
+    const int32_t *pa = A + ai, *pb = B + bi;
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-        // One load per slot: A ascending, B descending, +infinity in between.
-        const int32_t v = (i < na) ? pa[i] : pb[-i];
+        // One load per slot, always inside the thread's own keys: A ascending,
+        // B descending, +infinity in between (those slots load B[bi] and
+        // discard it).
+        const int32_t v = (i < na) ? pa[i] : pb[(i >= tb) ? (P - 1 - i) : 0];
         x[i] = (i < na || i >= tb) ? v : kKeyMax;
     }
     bitonic_half_clean<P>(x);
@@ -797,8 +799,10 @@ struct TileMerge2 {
     static constexpr int EOUT = EO;
     static constexpr int P = pow2_at_least(EO);
     static constexpr int TO = NT * EO;
-    static constexpr int REG = TO + 8 + 8;  // 16-byte aligned cover + slack
-    static constexpr int SMEM_BYTES = 2 * REG * 4;
+    // A's and B's 16-byte aligned covers back to back: na + nb = TO keys plus
+    // at most 3 extra keys at each end of each cover.
+    static constexpr int REG = TO + 16;
+    static constexpr int SMEM_BYTES = REG * 4;
 };
 
 template <int NT, int EO>
@@ -823,7 +827,7 @@ __global__ void __launch_bounds__(NT)
     const int64_t ca = ga & ~int64_t(3), cb = gb & ~int64_t(3);
     const int nca = (int)(((ga + na + 3) & ~int64_t(3)) - ca) / 4;
     const int ncb = (int)(((gb + nb + 3) & ~int64_t(3)) - cb) / 4;
-    int32_t *sA = smem, *sB = smem + C::REG;
+    int32_t *sA = smem, *sB = smem + 4 * nca;  // B's cover right after A's
     for (int q = threadIdx.x; q < nca + ncb; q += NT) {
         if (q < nca) cp_async16(sA + 4 * q, in + ca + 4 * q);
         else cp_async16(sB + 4 * (q - nca), in + cb + 4 * (q - nca));
