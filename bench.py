@@ -35,7 +35,8 @@ METRIC = "int32 keys/s & %HBM roofline; batched vs plain keys/s; serve p50/p99"
 UNIT = "keys/s"
 FALLBACK_HBM_GBS = 6800.0
 SPEC_HBM_GBS = 8000.0
-KERNEL_SOURCES = ["paper_2503_05934_gb300/csrc/hs_merge_kernels.cuh",
+KERNEL_SOURCES = ["paper_2503_05934_gb300/csrc/hs_merge_tile.cuh",
+                  "paper_2503_05934_gb300/csrc/hs_merge_prims.cuh",
                   "paper_2503_05934_gb300/csrc/hs_merge.cu",
                   "paper_2503_05934_gb300/csrc/hs_common.cuh",
                   "paper_2503_05934_gb300/csrc/hs_networks.cuh"]
@@ -315,7 +316,7 @@ def run_ours(args):
         "algorithmic_bytes_per_launch": alg_bytes,
         "launch_ms": avg_mk_s * 1e3 if avg_mk_s else None,
     }
-    tile = int(hs.lib().hs_keys_tile(hs.netset_mask(args.netset)))
+    tile = int(hs.lib().hs_keys_tile(hs.netset_mask(args.netset), n))
     passes = sort_passes(n, tile) if tile else None
     p_ref = sort_passes(n, 8192)
     ms_step = total_ms / args.steps
@@ -411,39 +412,62 @@ def time_sorts(torch, stream, reps, warmup, restore, sort):
 def run_extras(hs, torch, dev, stream, args, rank, pristine):
     out = {}
     n_keys = pristine.numel()
-    # Quick path (Algorithm 2) on the same 2^28 uniform keys.
+    peak, peak_kind = measured_peak()
+    reps = max(3, args.steps // 4)
+    # Both paths on the three distributions of the paper's experiments
+    # (uniform, sorted, nearly sorted) at the headline size; the merge path
+    # on uniform keys is the headline line itself.
+    tile = int(hs.lib().hs_keys_tile(hs.netset_mask(args.netset), n_keys))
+    p_counted = min(sort_passes(n_keys, tile), sort_passes(n_keys, 8192)) if tile else None
     work = torch.empty_like(pristine)
+    wsm = torch.empty(hs.hs_sort_workspace_bytes(n_keys), dtype=torch.uint8, device=dev)
     wsq = torch.empty(hs.hs_sort_workspace_bytes(n_keys, False, "quick"), dtype=torch.uint8,
                       device=dev)
-    ms = time_sorts(torch, stream, max(3, args.steps // 4), 2, lambda: work.copy_(pristine),
-                    lambda: hs.hs_sort_i32(work, "quick", args.netset, ws=wsq, stream=stream))
-    assert bool((work[1:] >= work[:-1]).all().item()), "quick sort output not sorted"
-    out["quick_2p28_uniform"] = {"value": n_keys / (ms / 1e3), "unit": "keys/s", "ms_per_sort": ms,
-                                 "workload": "2^28 uniform int32, median-of-three 3-way "
-                                             "partitions, 6To8 leaves"}
-    del work, wsq
+    seed = hs_inputs.config_seed(2, salt=2 + (rank << 8))
+    for dist in ["uniform", "sorted", "nearly"]:
+        src = pristine if dist == "uniform" else torch.from_numpy(
+            hs_inputs.keys(n_keys, dist, seed)).to(dev)
+        for algo in (["quick"] if dist == "uniform" else ["merge", "quick"]):
+            ws = wsm if algo == "merge" else wsq
+            ms = time_sorts(torch, stream, reps, 2, lambda: work.copy_(src),
+                            lambda: hs.hs_sort_i32(work, algo, args.netset, ws=ws, stream=stream))
+            assert bool((work[1:] >= work[:-1]).all().item()), f"{algo} {dist} output not sorted"
+            entry = {"value": n_keys / (ms / 1e3), "unit": "keys/s", "ms_per_sort": ms,
+                     "workload": f"2^{args.log2n} {dist} int32, "
+                                 + ("hybrid merge sort" if algo == "merge" else
+                                    "median-of-three 3-way partitions")
+                                 + f", {args.netset} leaves"}
+            if algo == "merge" and p_counted:
+                entry["frac_of_measured"] = p_counted * 8 * n_keys / (ms / 1e3) / (peak * 1e9)
+            out[f"{algo}_2p{args.log2n}_{dist}"] = entry
+        del src
+    del work, wsm, wsq
     # Stable pairs: 2^27 keys from 2^16 distinct values, value = index.
     n = 1 << (args.log2n - 1)
     k, v = hs_inputs.pair_keys_16bit(n, hs_inputs.config_seed(2, salt=1 + (rank << 8)))
     pk, pv = torch.from_numpy(k).to(dev), torch.from_numpy(v).to(dev)
     wk, wv = torch.empty_like(pk), torch.empty_like(pv)
     wsb = torch.empty(hs.hs_sort_workspace_bytes(n, True), dtype=torch.uint8, device=dev)
-    times = []
-    for i in range(args.warmup + max(3, args.steps // 2)):
+
+    def restore_pairs():
         wk.copy_(pk)
         wv.copy_(pv)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        hs.hs_sort_pairs_i32(wk, wv, "merge", args.netset, ws=wsb, stream=stream)
-        e1.record(stream)
-        if i >= args.warmup:
-            times.append((e0, e1))
-    torch.cuda.synchronize(dev)
-    ms = sum(a.elapsed_time(b) for a, b in times) / len(times)
-    out["pairs_stable_2p27"] = {"value": n / (ms / 1e3), "unit": "pairs/s", "ms_per_sort": ms,
-                                "workload": "2^27 (int32 key from 2^16 values, int32 index) "
-                                            "stable merge sort, 6To8 leaves"}
+
+    ms = time_sorts(torch, stream, max(3, args.steps // 2), args.warmup, restore_pairs,
+                    lambda: hs.hs_sort_pairs_i32(wk, wv, "merge", args.netset, ws=wsb,
+                                                 stream=stream))
+    ok = bool((wk[1:] >= wk[:-1]).all().item())
+    same = wk[1:] == wk[:-1]
+    ok = ok and bool(((wv[1:] > wv[:-1]) | ~same).all().item())  # value = index: stable
+    assert ok, "pair sort output not sorted or not stable"
+    ptile = int(hs.lib().hs_pairs_tile(hs.netset_mask(args.netset)))
+    pp = min(sort_passes(n, ptile), sort_passes(n, 8192)) if ptile else None
+    out[f"pairs_stable_2p{args.log2n - 1}"] = {
+        "value": n / (ms / 1e3), "unit": "pairs/s", "ms_per_sort": ms,
+        "passes": sort_passes(n, ptile) if ptile else None, "passes_ref": sort_passes(n, 8192),
+        "frac_of_measured": pp * 16 * n / (ms / 1e3) / (peak * 1e9) if pp else None,
+        "workload": f"2^{args.log2n - 1} (int32 key from 2^16 values, int32 index) "
+                    f"stable merge sort, {args.netset} leaves"}
     del pk, pv, wk, wv, wsb
     if not args.no_batched:
         out["batched_segsort"] = run_batched(hs, torch, dev, stream, args)

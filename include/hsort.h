@@ -271,10 +271,11 @@ HS_API void hs_prof_reset(void);
 HS_API hs_status hs_prof_read(const char *kernel, uint64_t *launches, double *total_ms);
 
 /* Waits for `stream`, then reads and clears the current device's kernel
- * status word.  Kernels never trap: a bounded wait inside a kernel (an
- * mbarrier on a bulk copy) that gives up raises this word and the kernel
- * returns early.  Returns HS_ERR_TIMEOUT if that happened since the last
- * check, HS_ERR_CUDA on a CUDA error, else HS_OK.  Synchronous. */
+ * status word.  Kernels never trap: a kernel that meets invalid device-side
+ * input (segment offsets that decrease or run past the key count) raises
+ * this word and skips that work.  Returns HS_ERR_INVALID_ARG for such input,
+ * HS_ERR_TIMEOUT if a bounded device-side wait gave up, HS_ERR_CUDA on a
+ * CUDA error, else HS_OK.  Synchronous. */
 HS_API hs_status hs_device_check(hs_stream_t stream);
 
 /* Process-wide tuning knobs (set them while no sort is in flight).
@@ -282,21 +283,33 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *     guard merge-sorts the segments still open (default -1 = automatic,
  *     4*ceil(log2 n) + 16).
  *   "blocksort_shape": keys block-sort shape, 0: 512 threads x 2 leaves,
- *     1: 1024 x 2, 2 (default): 256 x 4, 3: 512 x 4.  A thread holds its
+ *     1: 1024 x 2, 2: 256 x 4, 3: 512 x 4, 4: 288 x 4, -1 (default): per
+ *     array, 4 when its larger tile saves a global level over 2, else 2.  A thread holds its
  *     leaves as leaf, ..., leaf, leaf-1 keys, so the first merge tile holds
  *     (leaves * leaf - 1) * threads keys.
  *   "blocksort_threads": 512 or 1024: shape 0 or 1.
  *   "merge_kernel": 1 (default) tiled merge levels with asynchronous 16-byte
  *     staging and odd outputs per thread (used for keys when both buffers
  *     are 16-byte aligned and n % 4 == 0), 0 staged-load serial merges.
- *     Both give identical results.
+ *   "merge_tile": shape of the tiled keys level: 2 (default) 128 threads x
+ *     31 keys with exact per-thread windows, 0 256 x 15 with two windows,
+ *     1 64 x 31, 3 64 x 63, 4 128 x 23, 5 96 x 31, 6 192 x 31.
+ *   "pairs_blocksort": pair block-sort shape, 0 (default) 256 threads x 4
+ *     leaves, 1: 512 x 2, 2: 512 x 4, 3: 288 x 4.
+ *   "pairs_merge": 1 (default) tiled pair levels (16-byte aligned keys and
+ *     values, n % 4 == 0), 0 staged-load serial merges.
+ *     Every option gives identical results.
  * Unknown names or values return HS_ERR_INVALID_ARG. */
 HS_API hs_status hs_set_option(const char *name, int64_t value);
 
-/* Keys per block-sort tile of the merge path for network set s under the
- * current options (the global merge levels above it number
+/* Keys per block-sort tile of the merge path for an n-key array and network
+ * set s under the current options (the global merge levels above it number
  * ceil(log2(n / tile))); 0 for an invalid set. */
-HS_API size_t hs_keys_tile(hs_netset s);
+HS_API size_t hs_keys_tile(hs_netset s, size_t n);
+
+/* Pairs per block-sort tile of the stable pair sort for network set s under
+ * the current options; 0 for an invalid set. */
+HS_API size_t hs_pairs_tile(hs_netset s);
 
 /* --------------------------------------------------------- host checking */
 

@@ -1,0 +1,300 @@
+// Block sort: the first pass of Algorithm 1 on the GPU.  One CTA sorts one
+// tile of the array: every thread sorts its leaves in registers with the
+// fixed networks ("ApplySortingNetwork" on subarrays of 3..8 keys), merges
+// them in registers, and log2(NT) merge-path levels in shared memory merge
+// the threads' runs into one sorted tile (the bottom levels of "Merge").
+//
+//  * keys (block_sort_tile3): int32 keys.
+//  * pairs (block_sort_pairs_tile): 64-bit sort words (key, position in the
+//    tile), so every network and merge orders equal keys by input position,
+//    which makes the result the stable order; the values stay in shared
+//    memory and are gathered once, by position, at the end.
+#pragma once
+
+#include "hs_merge_prims.cuh"
+#include "hs_networks.cuh"
+
+namespace hs {
+
+// Compare-exchange on one register array of sort words (keys or pair words).
+template <class K>
+struct WordCE {
+    K *k;
+    template <int i, int j>
+    HS_HD void ce() {
+        K a = k[i], b = k[j];
+        k[i] = hs_min(a, b);
+        k[j] = hs_max(a, b);
+    }
+};
+
+// Sorts leaf x[0..N) in registers (N live slots; r of them real).  A leaf of
+// r keys uses the size-r network when the set has one, else the next size up
+// with the missing keys padded by +infinity sentinels (never stored).
+template <int N, class K>
+HS_DEV void sort_leaf(K *x, int r, uint32_t netset) {
+    if (r <= 1) return;
+    const int m = ragged_net_size(r, netset);
+    if (m == N && r == N) {
+        WordCE<K> op{x};
+        network<N>(op);
+        return;
+    }
+    K t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t[i] = (i < N && i < r) ? x[i < N ? i : 0] : word_max<K>();
+    WordCE<K> op{t};
+    network_dyn(m, op);
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = t[i];
+}
+
+// Bitonic merge of sorted x[0..N1) and x[N1..N1+N2) (N1, N2 <= P/2) in
+// registers; the ascending result goes back to x[0..N1+N2).
+template <int N1, int N2, int P, class K>
+HS_DEV void register_merge(K *x) {
+    K lo[P / 2], hi[P / 2];
+#pragma unroll
+    for (int i = 0; i < P / 2; ++i) {
+        const K a = i < N1 ? x[i] : word_max<K>();
+        const int j = P / 2 - 1 - i;  // second run, reversed
+        const K b = j < N2 ? x[N1 + (j < N2 ? j : 0)] : word_max<K>();
+        lo[i] = hs_min(a, b);
+        hi[i] = hs_max(a, b);
+    }
+    bitonic_half_clean<P / 2>(lo);
+    bitonic_half_clean<P / 2>(hi);
+#pragma unroll
+    for (int i = 0; i < N1 + N2; ++i) x[i] = i < P / 2 ? lo[i] : hi[i - P / 2];
+}
+
+// A thread's leaves: two (L, L - 1 keys) or four (L, L, L, L - 1 keys), each
+// sorted by its network, then merged in registers into one run of EO keys.
+// A leaf size that is not in the set is padded up to the next size that is,
+// the same rule as a ragged leaf; for the {6,7,8} set the leaves are 8 and 7
+// keys, both in the set.  avail = live keys from the thread's first slot.
+template <int L, int LEAVES, int P, class K>
+HS_DEV void sort_thread_leaves(K *k, int avail, uint32_t netset) {
+    if constexpr (LEAVES == 2) {
+        if constexpr (L > 1) {
+            sort_leaf<L>(k, hs_min(hs_max(avail, 0), L), netset);
+            sort_leaf<L - 1>(k + L, hs_min(hs_max(avail - L, 0), L - 1), netset);
+            register_merge<L, L - 1, P>(k);
+        }
+    } else {
+        if constexpr (L > 1) {
+#pragma unroll
+            for (int h = 0; h < 3; ++h)
+                sort_leaf<L>(k + h * L, hs_min(hs_max(avail - h * L, 0), L), netset);
+            sort_leaf<L - 1>(k + 3 * L, hs_min(hs_max(avail - 3 * L, 0), L - 1), netset);
+        }
+        register_merge<L, L, P / 2>(k);
+        register_merge<L, L - 1, P / 2>(k + 2 * L);
+        register_merge<2 * L, 2 * L - 1, P>(k);
+    }
+}
+
+// The shared-memory merge levels: runs of w -> 2w over the tile s[0..T).
+// Every thread finds its merge-path split and forms its EO outputs as the
+// exact-window merge of its own keys; its end split is the next lane's start
+// (a shuffle), or for a warp's last lane the next warp's first lane's start,
+// passed through wsplit.  Because EO is odd, neighbouring threads' windows
+// and their own EO-key slots fall on different banks, so the tile is stored
+// unpadded.  NT need not be a power of two: the last group of a level may
+// hold a short B run or none (then its keys stay as they are).  On return k
+// holds the thread's EO keys of the sorted tile.
+template <int NT, int EO, int P, class K>
+HS_DEV void block_merge_levels(K *s, int *wsplit, K (&k)[EO], int cnt) {
+    constexpr int T = NT * EO;
+    const int my0 = threadIdx.x * EO;
+    for (int w = EO; w < T && w < cnt; w *= 2) {
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < EO; ++j) s[my0 + j] = k[j];
+        __syncthreads();
+        const int gs = (my0 / (2 * w)) * (2 * w);
+        const int diag = my0 - gs;
+        const int alen = hs_min(w, T - gs);
+        const int blen = hs_max(hs_min(w, T - gs - w), 0);
+        // With no B run (a short last group) B points at A, so the unused
+        // window slots still read inside the tile.
+        const K *A = s + gs, *B = s + (blen > 0 ? gs + w : gs);
+        int lo = diag > blen ? diag - blen : 0;
+        int hi = diag < alen ? diag : alen;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
+            else hi = mid;
+        }
+        int end = __shfl_down_sync(0xffffffffu, lo, 1);
+        const int dend = diag + EO;  // runs and groups are multiples of EO
+        const bool last = dend == alen + blen;
+        if (2 * w > 32 * EO) {  // groups span warps: exchange warp-boundary splits
+            if ((threadIdx.x & 31) == 0) wsplit[threadIdx.x >> 5] = lo;
+            __syncthreads();
+            if ((threadIdx.x & 31) == 31 && !last) end = wsplit[(threadIdx.x >> 5) + 1];
+        }
+        if (last) end = alen;
+        K o[P];
+        exact_window_merge<EO, P>(A, lo, B, diag - lo, end - lo, EO, o);
+#pragma unroll
+        for (int j = 0; j < EO; ++j) k[j] = o[j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Keys.  NT threads x EO = LEAVES*L - 1 keys per tile.
+
+template <int NT, int L, int LEAVES = 2>
+struct BlockSort3 {
+    static_assert(LEAVES == 2 || LEAVES == 4, "two or four leaves per thread");
+    static constexpr int EO = LEAVES * L - 1;
+    static constexpr int P = pow2_at_least(EO);
+    static constexpr int T = NT * EO;
+    static constexpr int SZ = T + P + 32 + NT / 32 + 1;  // tile + window slack + warp splits
+    static constexpr int SMEM_BYTES = SZ * 4;
+};
+
+template <int NT, int L, int LEAVES = 2>
+HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_t netset,
+                             bool vec, int32_t *s) {
+    using C = BlockSort3<NT, L, LEAVES>;
+    constexpr int EO = C::EO, P = C::P, T = C::T;
+    int *wsplit = s + C::T + C::P + 32;  // one split per warp
+
+    if (vec && cnt == T && (T % 4) == 0) {
+        const int4 *s4 = reinterpret_cast<const int4 *>(kin);
+#pragma unroll 4
+        for (int q = threadIdx.x; q < T / 4; q += NT)
+            *reinterpret_cast<int4 *>(s + 4 * q) = ld_stream(s4 + q);
+    } else {
+        for (int i = threadIdx.x; i < T; i += NT) s[i] = i < cnt ? kin[i] : kKeyMax;
+    }
+    __syncthreads();
+
+    const int my0 = threadIdx.x * EO;
+    int32_t k[EO];
+#pragma unroll
+    for (int j = 0; j < EO; ++j) k[j] = s[my0 + j];
+    sort_thread_leaves<L, LEAVES, P>(k, cnt - my0, netset);
+    block_merge_levels<NT, EO, P>(s, wsplit, k, cnt);
+
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < EO; ++j) s[my0 + j] = k[j];
+    __syncthreads();
+    if (vec && (T % 4) == 0) {
+        const int n4 = cnt >> 2;
+        int4 *d4 = reinterpret_cast<int4 *>(kout);
+        for (int q = threadIdx.x; q < n4; q += NT)
+            st_stream(d4 + q, *reinterpret_cast<const int4 *>(s + 4 * q));
+        for (int i = 4 * n4 + threadIdx.x; i < cnt; i += NT) kout[i] = s[i];
+    } else {
+        for (int i = threadIdx.x; i < cnt; i += NT) kout[i] = s[i];
+    }
+}
+
+// Tile t covers keys [t*T, (t+1)*T); the last tile may be short.  kin/kout
+// may alias: each CTA reads its whole tile into shared memory before writing.
+template <int NT, int L, int LEAVES = 2>
+__global__ void __launch_bounds__(NT)
+    k_blocksort3(const int32_t *kin, int32_t *kout, int64_t n, uint32_t netset, int vec) {
+    constexpr int T = BlockSort3<NT, L, LEAVES>::T;
+    extern __shared__ __align__(16) int32_t smem[];
+    const int64_t base = (int64_t)blockIdx.x * T;
+    const int cnt = (int)((n - base) < T ? (n - base) : T);
+    block_sort_tile3<NT, L, LEAVES>(kin + base, kout + base, cnt, netset, vec != 0, smem);
+}
+
+// ---------------------------------------------------------------------------
+// Pairs.  Shared layout: W = sort words [T + P + 32] (int64; during the load
+// and the final store its first 2T int32 slots hold keys, then output keys
+// and output values), V = input values [T] (int32), then the warp splits.
+
+template <int NT, int L, int LEAVES = 2>
+struct BlockSortPairs {
+    static_assert(LEAVES == 2 || LEAVES == 4, "two or four leaves per thread");
+    static constexpr int EO = LEAVES * L - 1;
+    static constexpr int P = pow2_at_least(EO);
+    static constexpr int T = NT * EO;
+    static constexpr int W_WORDS = T + P + 32;
+    static constexpr int SMEM_BYTES = W_WORDS * 8 + T * 4 + (NT / 32 + 1) * 4;
+};
+
+template <int NT, int L, int LEAVES = 2>
+HS_DEV void block_sort_pairs_tile(const int32_t *kin, int32_t *kout, const int32_t *vin,
+                                  int32_t *vout, int cnt, uint32_t netset, bool vec,
+                                  int64_t *sw) {
+    using C = BlockSortPairs<NT, L, LEAVES>;
+    constexpr int EO = C::EO, P = C::P, T = C::T;
+    int32_t *s32 = reinterpret_cast<int32_t *>(sw);  // 2 * W_WORDS int32 slots
+    int32_t *sv = reinterpret_cast<int32_t *>(sw + C::W_WORDS);
+    int *wsplit = sv + T;
+
+    if (vec && cnt == T && (T % 4) == 0) {
+        const int4 *k4 = reinterpret_cast<const int4 *>(kin);
+        const int4 *v4 = reinterpret_cast<const int4 *>(vin);
+#pragma unroll 4
+        for (int q = threadIdx.x; q < T / 4; q += NT) {
+            *reinterpret_cast<int4 *>(s32 + 4 * q) = ld_stream(k4 + q);
+            *reinterpret_cast<int4 *>(sv + 4 * q) = ld_stream(v4 + q);
+        }
+    } else {
+        for (int i = threadIdx.x; i < cnt; i += NT) {
+            s32[i] = kin[i];
+            sv[i] = vin[i];
+        }
+    }
+    __syncthreads();
+
+    const int my0 = threadIdx.x * EO;
+    int64_t k[EO];
+#pragma unroll
+    for (int j = 0; j < EO; ++j)
+        k[j] = (my0 + j < cnt) ? pack_word(s32[my0 + j], (uint32_t)(my0 + j)) : word_max<int64_t>();
+    sort_thread_leaves<L, LEAVES, P>(k, cnt - my0, netset);
+    block_merge_levels<NT, EO, P>(sw, wsplit, k, cnt);
+
+    // Output keys to s32[0, T), values (gathered by position) to s32[T, 2T).
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < EO; ++j) {
+        if (my0 + j < cnt) {
+            s32[my0 + j] = word_key(k[j]);
+            s32[T + my0 + j] = sv[word_tag(k[j])];
+        }
+    }
+    __syncthreads();
+    if (vec && (T % 4) == 0) {
+        const int n4 = cnt >> 2;
+        int4 *dk = reinterpret_cast<int4 *>(kout);
+        int4 *dv = reinterpret_cast<int4 *>(vout);
+        for (int q = threadIdx.x; q < n4; q += NT) {
+            st_stream(dk + q, *reinterpret_cast<const int4 *>(s32 + 4 * q));
+            st_stream(dv + q, *reinterpret_cast<const int4 *>(s32 + T + 4 * q));
+        }
+        for (int i = 4 * n4 + threadIdx.x; i < cnt; i += NT) {
+            kout[i] = s32[i];
+            vout[i] = s32[T + i];
+        }
+    } else {
+        for (int i = threadIdx.x; i < cnt; i += NT) {
+            kout[i] = s32[i];
+            vout[i] = s32[T + i];
+        }
+    }
+}
+
+template <int NT, int L, int LEAVES = 2>
+__global__ void __launch_bounds__(NT)
+    k_blocksort_pairs(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
+                      int64_t n, uint32_t netset, int vec) {
+    constexpr int T = BlockSortPairs<NT, L, LEAVES>::T;
+    extern __shared__ __align__(16) int64_t smem64[];
+    const int64_t base = (int64_t)blockIdx.x * T;
+    const int cnt = (int)((n - base) < T ? (n - base) : T);
+    block_sort_pairs_tile<NT, L, LEAVES>(kin + base, kout + base, vin + base, vout + base, cnt,
+                                         netset, vec != 0, smem64);
+}
+
+}  // namespace hs

@@ -55,13 +55,20 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // device (the attribute is per function and device).
 hs_status ensure_smem(const void *func, int bytes);
 
-// Merge path internals exposed to the other translation units.
+// Merge path internals exposed to the other translation units.  merge_sort
+// sorts keys, or stable pairs when d_vals is non-null (pairs_sort).
 size_t merge_workspace_bytes(size_t n, int with_values);
 hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, void *d_ws,
                      size_t ws_bytes, cudaStream_t st);
+hs_status pairs_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, void *d_ws,
+                     size_t ws_bytes, cudaStream_t st);
+int64_t pairs_tile(int L);
+void pairs_set_blocksort(int v);
+void pairs_set_merge(int v);
 
-// Tile of the keys block sort for leaf size L, and its thread-count option.
-int64_t keys_tile(int L);
+// Tile of the keys block sort of an n-key array for leaf size L, and its
+// shape options.
+int64_t keys_tile(int L, int64_t n);
 void merge_set_blocksort_threads(int nt);
 void merge_set_blocksort_shape(int v);
 void merge_set_kernel(int k);

@@ -1,0 +1,255 @@
+// Stable key/value merge sort (Algorithm 1 on (key, value) pairs): block sort
+// on (key, position) words, then global merge levels that keep equal keys in
+// input order.  Keys and values live in separate int32 arrays; each level
+// reads and writes both once.
+#include <algorithm>
+
+#include "hs_internal.h"
+#include "hs_blocksort.cuh"
+
+namespace hs {
+
+// ---------------------------------------------------------------------------
+// Tiled pairs level (16-byte aligned key and value buffers, n % 4 == 0).  One
+// CTA per output tile of TO = NT*EO pairs: the tile's A and B key and value
+// ranges are staged by 16-byte asynchronous copies of their aligned covers;
+// each thread finds its merge-path split, takes its end split from the next
+// lane, and merges exactly its own outputs serially (stable: A's element on
+// ties), picking each value by the same decision; the outputs then leave
+// through shared memory as 16-byte streaming stores.
+template <int NT, int EO>
+struct TileMergePairs {
+    static constexpr int EOUT = EO;
+    static constexpr int TO = NT * EO;
+    static constexpr int REG = TO + 16;  // A and B covers back to back
+    static constexpr int SMEM_BYTES = 2 * REG * 4;  // keys, values
+};
+
+template <int NT, int EO>
+__global__ void __launch_bounds__(NT)
+    k_merge_tile_pairs(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
+                       int64_t n, int64_t w, const int64_t *part, int tpg) {
+    using C = TileMergePairs<NT, EO>;
+    constexpr int TO = C::TO;
+    extern __shared__ __align__(16) int32_t smem[];
+    int32_t *sK = smem, *sV = smem + C::REG;
+    const int64_t g = blockIdx.x / tpg;
+    const int t = blockIdx.x - (int)(g * tpg);
+    const MergeGeom m = merge_geom(g, n, w);
+    const int64_t glen = m.alen + m.blen;
+    const int64_t o0 = (int64_t)t * TO;
+    const int64_t o1 = (o0 + TO) < glen ? (o0 + TO) : glen;
+    const int64_t a0 = part[blockIdx.x];
+    const int64_t a1 = (o1 == glen) ? m.alen : part[blockIdx.x + 1];
+    const int na = (int)(a1 - a0);
+    const int tot = (int)(o1 - o0);
+    const int nb = tot - na;
+    const int64_t ga = m.gs + a0, gb = m.gs + w + (o0 - a0);
+    const int64_t ca = ga & ~int64_t(3), cb = gb & ~int64_t(3);
+    const int nca = (int)(((ga + na + 3) & ~int64_t(3)) - ca) / 4;
+    const int ncb = (int)(((gb + nb + 3) & ~int64_t(3)) - cb) / 4;
+    for (int q = threadIdx.x; q < nca + ncb; q += NT) {
+        const int64_t src = q < nca ? ca + 4 * q : cb + 4 * (q - nca);
+        cp_async16(sK + 4 * q, kin + src);
+        cp_async16(sV + 4 * q, vin + src);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int offA = (int)(ga - ca), offB = 4 * nca + (int)(gb - cb);
+    const int32_t *A = sK + offA, *B = sK + offB;
+    const int32_t *VA = sV + offA, *VB = sV + offB;
+
+    const int diag = threadIdx.x * EO;
+    const int lane = threadIdx.x & 31;
+    const int dcl = diag < tot ? diag : tot;
+    int lo = dcl > nb ? dcl - nb : 0, hi = dcl < na ? dcl : na;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] <= B[dcl - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    __shared__ int wsplit[NT / 32 + 1];
+    int end = __shfl_down_sync(0xffffffffu, lo, 1);
+    if (lane == 0) wsplit[threadIdx.x >> 5] = lo;
+    if (threadIdx.x == 0) wsplit[NT / 32] = na;
+    __syncthreads();
+    const int dend = (diag + EO) < tot ? (diag + EO) : tot;
+    if (lane == 31) end = wsplit[(threadIdx.x >> 5) + 1];
+    if (dend == tot) end = na;
+    const int cnt = dend - dcl;
+
+    // Serial stable merge of A[lo, end) and B[dcl - lo, dcl - lo + cnt - (end - lo)).
+    // A read at ia == end or ib == eb lands inside the covers (each run is
+    // followed by at least one staged word), and its key is never taken.
+    int32_t ok[EO], ov[EO];
+    {
+        int ia = lo, ib = dcl - lo;
+        const int eb = ib + cnt - (end - lo);
+        int32_t ka = A[ia], kb = B[ib];
+#pragma unroll
+        for (int k = 0; k < EO; ++k) {
+            const bool take_b = (ib < eb) && ((ia >= end) || (kb < ka));
+            ok[k] = take_b ? kb : ka;
+            ov[k] = take_b ? VB[ib] : VA[ia];
+            ib += take_b;
+            ia += !take_b;
+            const int32_t nx = take_b ? B[ib] : A[ia];
+            kb = take_b ? nx : kb;
+            ka = take_b ? ka : nx;
+        }
+    }
+    __syncthreads();
+    if (cnt > 0) {
+#pragma unroll
+        for (int k = 0; k < EO; ++k) {
+            if (k < cnt) {
+                sK[diag + k] = ok[k];
+                sV[diag + k] = ov[k];
+            }
+        }
+    }
+    __syncthreads();
+    int32_t *dk = kout + m.gs + o0, *dv = vout + m.gs + o0;  // 16-byte aligned
+    const int n4 = tot >> 2;
+    for (int q = threadIdx.x; q < n4; q += NT) {
+        st_stream(reinterpret_cast<int4 *>(dk) + q, *reinterpret_cast<const int4 *>(sK + 4 * q));
+        st_stream(reinterpret_cast<int4 *>(dv) + q, *reinterpret_cast<const int4 *>(sV + 4 * q));
+    }
+    for (int i = 4 * n4 + threadIdx.x; i < tot; i += NT) {
+        st_stream(dk + i, sK[i]);
+        st_stream(dv + i, sV[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Planner.
+
+// Block sort shape (option "pairs_blocksort"): 0 = 256 threads x 4 leaves
+// (the default; tiles of 256*(4L - 1) pairs), 1 = 512 x 2 leaves, 2 = 512 x 4
+// leaves (one CTA per SM), 3 = 288 x 4 leaves (tiles of at least 8192 pairs
+// for the {6,7,8} set).
+static int g_pairs_bs = 0;
+// Merge level (option "pairs_merge"): 1 = tiled (the default when aligned),
+// 0 = the generic serial-merge pass.
+static int g_pairs_merge = 1;
+
+void pairs_set_blocksort(int v) { g_pairs_bs = v; }
+void pairs_set_merge(int v) { g_pairs_merge = v; }
+
+int64_t pairs_tile(int L) {
+    switch (g_pairs_bs) {
+        case 1: return 512 * (2 * L - 1);
+        case 2: return 512 * (4 * L - 1);
+        case 3: return 288 * (4 * L - 1);
+        default: return 256 * (4 * L - 1);
+    }
+}
+
+template <int NT, int L, int LEAVES>
+static hs_status launch_pairs_blocksort_t(const int32_t *kin, int32_t *kout, const int32_t *vin,
+                                          int32_t *vout, int64_t n, hs_netset s, int vec,
+                                          cudaStream_t st) {
+    using C = BlockSortPairs<NT, L, LEAVES>;
+    auto kern = k_blocksort_pairs<NT, L, LEAVES>;
+    hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
+    if (r != HS_OK) return r;
+    const int64_t grid = (n + C::T - 1) / C::T;
+    LaunchToken t = launch_begin(K_BLOCKSORT_PAIRS, st);
+    kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, s, vec);
+    return launch_end(t);
+}
+
+template <int NT, int LEAVES>
+static hs_status launch_pairs_blocksort_nt(int L, const int32_t *kin, int32_t *kout,
+                                           const int32_t *vin, int32_t *vout, int64_t n,
+                                           hs_netset s, int vec, cudaStream_t st) {
+    switch (L) {
+        case 1: return launch_pairs_blocksort_t<NT, 1, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
+        case 3: return launch_pairs_blocksort_t<NT, 3, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
+        case 4: return launch_pairs_blocksort_t<NT, 4, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
+        case 5: return launch_pairs_blocksort_t<NT, 5, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
+        case 6: return launch_pairs_blocksort_t<NT, 6, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
+        case 7: return launch_pairs_blocksort_t<NT, 7, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
+        case 8: return launch_pairs_blocksort_t<NT, 8, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
+    }
+    return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
+}
+
+constexpr int PM_NT = 128, PM_EO = 31;  // tiled level
+constexpr int PG_NT = 256, PG_E = 8;    // generic level
+
+static hs_status launch_pairs_level(const int32_t *kin, int32_t *kout, const int32_t *vin,
+                                    int32_t *vout, int64_t n, int64_t w, int64_t *part, int vec,
+                                    cudaStream_t st) {
+    const bool tiled = vec && g_pairs_merge == 1 && (n % 4) == 0;
+    const int64_t to = tiled ? TileMergePairs<PM_NT, PM_EO>::TO : PG_NT * PG_E;
+    const LevelTiles lt = level_tiles(n, w, to);
+    LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
+    k_merge_partition<<<(unsigned)((lt.nblocks + 255) / 256), 256, 0, st>>>(
+        kin, n, w, (int)to, (int)lt.tpg, lt.nblocks, part);
+    hs_status r = launch_end(t);
+    if (r != HS_OK) return r;
+    if (tiled) {
+        using C = TileMergePairs<PM_NT, PM_EO>;
+        auto kern = k_merge_tile_pairs<PM_NT, PM_EO>;
+        if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
+        t = launch_begin(K_MERGE_PAIRS, st);
+        kern<<<(unsigned)lt.nblocks, PM_NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, w, part,
+                                                                 (int)lt.tpg);
+        return launch_end(t);
+    }
+    const int smem = merge_smem_words<PG_NT, PG_E>() * (int)sizeof(int32_t) * 2;
+    auto kern = k_merge_pass<PG_NT, PG_E, true>;
+    if ((r = ensure_smem((const void *)kern, smem)) != HS_OK) return r;
+    t = launch_begin(K_MERGE_PAIRS, st);
+    kern<<<(unsigned)lt.nblocks, PG_NT, smem, st>>>(kin, kout, vin, vout, n, w, part, (int)lt.tpg,
+                                                     vec);
+    return launch_end(t);
+}
+
+hs_status pairs_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, void *d_ws,
+                     size_t ws_bytes, cudaStream_t st) {
+    const int64_t n = (int64_t)n_;
+    const int L = leaf_size(s);
+    const int64_t T = pairs_tile(L);
+    int passes = 0;
+    for (int64_t w = T; w < n; w *= 2) ++passes;
+
+    int32_t *kbuf = nullptr, *vbuf = nullptr;
+    int64_t *part = nullptr;
+    if (passes > 0) {
+        if (!d_ws || ws_bytes < merge_workspace_bytes(n_, 1))
+            return fail(HS_ERR_INVALID_ARG, "pair sort: workspace smaller than hs_sort_workspace_bytes");
+        if (!aligned(d_ws, 16)) return fail(HS_ERR_INVALID_ARG, "pair sort: workspace not 16-byte aligned");
+        char *p = static_cast<char *>(d_ws);
+        const size_t kb = align_up(n_ * sizeof(int32_t), 256);
+        kbuf = reinterpret_cast<int32_t *>(p);
+        vbuf = reinterpret_cast<int32_t *>(p + kb);
+        part = reinterpret_cast<int64_t *>(p + 2 * kb);
+    }
+    const int vec = aligned(d_keys, 16) && aligned(d_vals, 16) ? 1 : 0;
+
+    // With an even number of global levels the block sort writes in place, so
+    // the last level lands in the caller's arrays.
+    int32_t *kcur = (passes % 2 == 0) ? d_keys : kbuf;
+    int32_t *vcur = (passes % 2 == 0) ? d_vals : vbuf;
+    int32_t *kalt = (kcur == d_keys) ? kbuf : d_keys;
+    int32_t *valt = (vcur == d_vals) ? vbuf : d_vals;
+
+    hs_status r;
+    switch (g_pairs_bs) {
+        case 1: r = launch_pairs_blocksort_nt<512, 2>(L, d_keys, kcur, d_vals, vcur, n, s, vec, st); break;
+        case 2: r = launch_pairs_blocksort_nt<512, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, st); break;
+        case 3: r = launch_pairs_blocksort_nt<288, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, st); break;
+        default: r = launch_pairs_blocksort_nt<256, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, st);
+    }
+    if (r != HS_OK) return r;
+    for (int64_t w = T; w < n; w *= 2) {
+        if ((r = launch_pairs_level(kcur, kalt, vcur, valt, n, w, part, vec, st)) != HS_OK) return r;
+        std::swap(kcur, kalt);
+        std::swap(vcur, valt);
+    }
+    return HS_OK;
+}
+
+}  // namespace hs

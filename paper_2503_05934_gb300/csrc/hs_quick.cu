@@ -23,7 +23,7 @@
 #include <vector>
 
 #include "hs_internal.h"
-#include "hs_merge_kernels.cuh"
+#include "hs_blocksort.cuh"
 
 namespace hs {
 
@@ -378,7 +378,7 @@ hs_status quick_sort(int32_t *d_keys, size_t n_, hs_netset s, void *d_ws, size_t
     const int L = leaf_size(s);
     const int64_t tile = qs_tile(L);
     const int vec = aligned(d_keys, 16) ? 1 : 0;
-    if (n <= keys_tile(L)) return blocksort_launch(L, d_keys, d_keys, n, s, vec, st);
+    if (n <= keys_tile(L, n)) return blocksort_launch(L, d_keys, d_keys, n, s, vec, st);
 
     const QLayout q = qs_layout(n_);
     if (!d_ws || ws_bytes < q.total)

@@ -296,8 +296,8 @@ hs_status hs_set_option(const char *name, int64_t value) {
         return HS_OK;
     }
     if (std::strcmp(name, "blocksort_shape") == 0) {
-        if (value < 0 || value > 3)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_shape must be 0..3");
+        if (value < -1 || value > 4)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_shape must be -1..4");
         merge_set_blocksort_shape((int)value);
         return HS_OK;
     }
@@ -307,12 +307,29 @@ hs_status hs_set_option(const char *name, int64_t value) {
         merge_set_blocksort_threads((int)value);
         return HS_OK;
     }
+    if (std::strcmp(name, "pairs_blocksort") == 0) {
+        if (value < 0 || value > 3)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: pairs_blocksort must be 0..3");
+        pairs_set_blocksort((int)value);
+        return HS_OK;
+    }
+    if (std::strcmp(name, "pairs_merge") == 0) {
+        if (value != 0 && value != 1)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: pairs_merge must be 0 or 1");
+        pairs_set_merge((int)value);
+        return HS_OK;
+    }
     return fail(HS_ERR_INVALID_ARG, std::string("hs_set_option: unknown option ") + name);
 }
 
-size_t hs_keys_tile(hs_netset s) {
+size_t hs_keys_tile(hs_netset s, size_t n) {
     if (!netset_ok(s)) return 0;
-    return (size_t)keys_tile(leaf_size(s));
+    return (size_t)keys_tile(leaf_size(s), (int64_t)n);
+}
+
+size_t hs_pairs_tile(hs_netset s) {
+    if (!netset_ok(s)) return 0;
+    return (size_t)pairs_tile(leaf_size(s));
 }
 
 int hs_network_pairs(int m, int *pairs, int cap) {

@@ -1,7 +1,7 @@
 // Batched form: many independent arrays sorted by one persistent launch.
 //
 // Every array ("segment") is sorted by a single CTA, as Algorithm 1 would sort
-// it: network leaves and shared-memory merge levels (block_sort_tile2) for a
+// it: network leaves and shared-memory merge levels (block_sort_tile3) for a
 // segment of at most one tile; for a longer segment, tile-sized pieces first,
 // then CTA-local merge levels through the segment's scratch area, which stays
 // in L2 at the sizes this form targets (up to 64K keys).  Persistent CTAs take
@@ -19,7 +19,7 @@
 #include <vector>
 
 #include "hs_internal.h"
-#include "hs_merge_kernels.cuh"
+#include "hs_blocksort.cuh"
 #include "hs_segsort.h"
 
 namespace hs {

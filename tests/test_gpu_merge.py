@@ -134,6 +134,49 @@ def test_pairs_unaligned(hs):
     assert np.array_equal(ko, ek) and np.array_equal(vo, ev)
 
 
+@pytest.mark.parametrize("bs", [0, 1, 2, 3])
+@pytest.mark.parametrize("merge", [0, 1])
+def test_pairs_options_keep_results(hs, bs, merge):
+    """Every pair block-sort shape and merge-level kernel gives the oracle's
+    stable order: sizes around the tiles (7936 / 7680 / 15872 / 8928 pairs
+    per block-sort tile, 3968 per merge tile), n % 4 != 0, an unaligned
+    start, few distinct keys (long equal runs across tiles) and arbitrary
+    values."""
+    hs.hs_set_option("pairs_blocksort", bs)
+    hs.hs_set_option("pairs_merge", merge)
+    try:
+        rng = np.random.default_rng(40 + 2 * bs + merge)
+        for n in [2, 7, 31, 3967, 3968, 3969, 7679, 7680, 7681, 7935, 7936, 7937, 8927, 8928,
+                  8929, 15_871, 15_872, 15_873, 61_441, 250_003, 1 << 20]:
+            for kinds in ["few", "wide"]:
+                if kinds == "few":
+                    k = rng.integers(0, 5, n).astype(np.int32)
+                else:
+                    k = rng.integers(-(1 << 31), 1 << 31, n, dtype=np.int64).astype(np.int32)
+                v = rng.integers(-(1 << 31), 1 << 31, n, dtype=np.int64).astype(np.int32)
+                ek, ev = oracle.merge_sort_pairs(k, v, "6To8")
+                for off in ([0, 3] if n < 100_000 else [0]):
+                    ko, vo = gpu_sort_pairs(hs, k, v, "6To8", offset=off)
+                    assert np.array_equal(ko, ek), (n, kinds, off)
+                    assert np.array_equal(vo, ev), (n, kinds, off)
+    finally:
+        hs.hs_set_option("pairs_blocksort", 0)
+        hs.hs_set_option("pairs_merge", 1)
+
+
+@pytest.mark.parametrize("netset", ["none", "3To5", "Odd", "3To4", "6To8", "3", "PowerOf2"])
+def test_pairs_all_netsets_small_words(hs, netset):
+    """Every word over {0, 1, 2} of length 1..8, concatenated (ties
+    everywhere), sorted as stable pairs under every leaf size."""
+    import itertools
+    segs = [np.array(t, np.int32) for m in range(1, 9) for t in itertools.product(range(3), repeat=m)]
+    k = np.concatenate(segs)
+    v = np.arange(k.size, dtype=np.int32)[::-1].copy()
+    ko, vo = gpu_sort_pairs(hs, k, v, netset)
+    ek, ev = oracle.merge_sort_pairs(k, v, "6To8")
+    assert np.array_equal(ko, ek) and np.array_equal(vo, ev)
+
+
 def test_host_buffer_entry(hs):
     import torch
     a = g.random_i32(1_000_000, 31)
@@ -153,9 +196,9 @@ def test_workspace_reuse_and_launch_count(hs):
         hs.hs_sort_i32(t, "merge", "6To8", ws=ws)
         torch.cuda.synchronize()
         assert np.array_equal(t.cpu().numpy(), np.sort(a))
-    # 1 block sort + 2 launches (partition, merge) per global level; tile
-    # (2*8-1) * 512 = 7680 keys, 2^20 / 7680 -> 8 levels
-    tile = int(hs.lib().hs_keys_tile(hs.netset_mask("6To8")))
+    # 1 block sort + 2 launches (partition, merge) per global level over the
+    # block-sort tile the library reports for this n
+    tile = int(hs.lib().hs_keys_tile(hs.netset_mask("6To8"), n))
     levels = 0
     while tile << levels < n:
         levels += 1
@@ -179,7 +222,7 @@ def test_many_duplicates_and_runs(hs):
         assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), mod
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [-1, 0, 1, 2, 3, 4])
 @pytest.mark.parametrize("kernel", [0, 1])
 def test_tuning_options_keep_results(hs, shape, kernel):
     """Block-sort shape and merge-level kernel change speed, not bytes."""
@@ -187,11 +230,11 @@ def test_tuning_options_keep_results(hs, shape, kernel):
     hs.hs_set_option("merge_kernel", kernel)
     try:
         for netset in ["6To8", "3To5", "none", "Odd"]:
-            for n in [1, 7, 8191, 16385, 100_003, 1 << 20]:
-                a = g.random_i32(n, n + 10 * shape + kernel)
+            for n in [1, 7, 8191, 8928, 8929, 16385, 100_003, 1 << 20]:
+                a = g.random_i32(n, n + 10 * (shape + 1) + kernel)
                 assert np.array_equal(gpu_sort(hs, a, "merge", netset), oracle.merge_sort(a, netset))
     finally:
-        hs.hs_set_option("blocksort_shape", 2)
+        hs.hs_set_option("blocksort_shape", -1)
         hs.hs_set_option("merge_kernel", 1)
 
 
@@ -207,7 +250,7 @@ def test_profiling_counters(hs):
         n_mk, ms_mk = hs.hs_prof_read("merge_keys")
     finally:
         hs.hs_prof_enable(False)
-    tile = int(hs.lib().hs_keys_tile(hs.netset_mask("6To8")))
+    tile = int(hs.lib().hs_keys_tile(hs.netset_mask("6To8"), 1 << 18))
     levels = 0
     while tile << levels < (1 << 18):
         levels += 1
