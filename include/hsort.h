@@ -291,9 +291,12 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *   "merge_kernel": 1 (default) tiled merge levels with asynchronous 16-byte
  *     staging and odd outputs per thread (used for keys when both buffers
  *     are 16-byte aligned and n % 4 == 0), 0 staged-load serial merges.
- *   "merge_tile": shape of the tiled keys level: 2 (default) 128 threads x
+ *   "merge_tile": shape of the tiled keys level: 5 (default) 96 threads x
  *     31 keys with exact per-thread windows, 0 256 x 15 with two windows,
- *     1 64 x 31, 3 64 x 63, 4 128 x 23, 5 96 x 31, 6 192 x 31.
+ *     1 64 x 31, 2 128 x 31, 3 64 x 63, 4 128 x 23, 6 192 x 31, 7 256 x 31.
+ *   "merge_samples": 1 (default) the tiled keys levels' partition searches
+ *     start on every 32nd key of the level's input, written by the pass
+ *     before; 0 plain searches in the keys.
  *   "pairs_blocksort": pair block-sort shape, 0 (default) 256 threads x 4
  *     leaves, 1: 512 x 2, 2: 512 x 4, 3: 288 x 4.
  *   "pairs_merge": 1 (default) tiled pair levels (16-byte aligned keys and

@@ -155,9 +155,11 @@ struct BlockSort3 {
     static constexpr int SMEM_BYTES = SZ * 4;
 };
 
+// With samp, also writes the tile's samples (every kSampleStride-th key,
+// samp[(base + q) / S] for q % S == 0; base % S == 0).
 template <int NT, int L, int LEAVES = 2>
 HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_t netset,
-                             bool vec, int32_t *s) {
+                             bool vec, int32_t *s, int32_t *samp = nullptr, int64_t base = 0) {
     using C = BlockSort3<NT, L, LEAVES>;
     constexpr int EO = C::EO, P = C::P, T = C::T;
     int *wsplit = s + C::T + C::P + 32;  // one split per warp
@@ -184,26 +186,33 @@ HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_
     for (int j = 0; j < EO; ++j) s[my0 + j] = k[j];
     __syncthreads();
     if (vec && (T % 4) == 0) {
-        const int n4 = cnt >> 2;
-        int4 *d4 = reinterpret_cast<int4 *>(kout);
-        for (int q = threadIdx.x; q < n4; q += NT)
-            st_stream(d4 + q, *reinterpret_cast<const int4 *>(s + 4 * q));
-        for (int i = 4 * n4 + threadIdx.x; i < cnt; i += NT) kout[i] = s[i];
+        store_tile_out<NT>(kout, s, cnt, samp, base);
     } else {
-        for (int i = threadIdx.x; i < cnt; i += NT) kout[i] = s[i];
+        int32_t *sp = samp ? samp + base / kSampleStride : nullptr;
+        for (int i = threadIdx.x; i < cnt; i += NT) {
+            kout[i] = s[i];
+            if (sp && i % kSampleStride == 0) sp[i / kSampleStride] = s[i];
+        }
     }
 }
 
 // Tile t covers keys [t*T, (t+1)*T); the last tile may be short.  kin/kout
 // may alias: each CTA reads its whole tile into shared memory before writing.
+// Resident CTAs per SM the register budget must allow (about as many as the
+// shared tiles fit): 5 of up to 288 threads, 3 of 512.
+constexpr int blocksort_min_ctas(int nt) { return nt <= 288 ? 5 : nt <= 512 ? 3 : 1; }
+
 template <int NT, int L, int LEAVES = 2>
-__global__ void __launch_bounds__(NT)
-    k_blocksort3(const int32_t *kin, int32_t *kout, int64_t n, uint32_t netset, int vec) {
+__global__ void __launch_bounds__(NT, blocksort_min_ctas(NT))
+    k_blocksort3(const int32_t *kin, int32_t *kout, int64_t n, uint32_t netset, int vec,
+                 int32_t *samp) {
     constexpr int T = BlockSort3<NT, L, LEAVES>::T;
+    static_assert(T % kSampleStride == 0, "tiles start on sample positions");
     extern __shared__ __align__(16) int32_t smem[];
     const int64_t base = (int64_t)blockIdx.x * T;
     const int cnt = (int)((n - base) < T ? (n - base) : T);
-    block_sort_tile3<NT, L, LEAVES>(kin + base, kout + base, cnt, netset, vec != 0, smem);
+    block_sort_tile3<NT, L, LEAVES>(kin + base, kout + base, cnt, netset, vec != 0, smem, samp,
+                                    base);
 }
 
 // ---------------------------------------------------------------------------

@@ -57,6 +57,19 @@ hs_status ensure_smem(const void *func, int bytes);
 
 // Merge path internals exposed to the other translation units.  merge_sort
 // sorts keys, or stable pairs when d_vals is non-null (pairs_sort).
+//
+// Workspace layout (each part 256-byte aligned): the keys ping-pong copy,
+// the values copy (pairs), the merge partition indices (n/1024 + 8 int64:
+// more than the output tiles of any level, whose tiles hold at least 1984
+// keys), and the keys' samples (every 32nd key, n/32 + 8 int32).
+constexpr size_t ws_align(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t merge_ws_keys_bytes(size_t n) { return ws_align(n * sizeof(int32_t)); }
+constexpr size_t merge_ws_part_bytes(size_t n) { return ws_align((n / 1024 + 8) * sizeof(int64_t)); }
+constexpr size_t merge_ws_samp_bytes(size_t n) { return ws_align((n / 32 + 8) * sizeof(int32_t)); }
+constexpr size_t merge_workspace_size(size_t n, int with_values) {
+    return merge_ws_keys_bytes(n) * (with_values ? 2 : 1) + merge_ws_part_bytes(n) +
+           merge_ws_samp_bytes(n);
+}
 size_t merge_workspace_bytes(size_t n, int with_values);
 hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, void *d_ws,
                      size_t ws_bytes, cudaStream_t st);
@@ -73,11 +86,12 @@ void merge_set_blocksort_threads(int nt);
 void merge_set_blocksort_shape(int v);
 void merge_set_kernel(int k);
 void merge_set_tile(int v);
+void merge_set_samples(int v);
 
 // Block sort of [0, n) in tiles of keys_tile(L) keys (the merge path's first pass;
 // the whole sort when n fits one tile).
 hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
-                           int vec, cudaStream_t st);
+                           int vec, cudaStream_t st, int32_t *samp = nullptr);
 
 // Device address of the current device's status word (kernels OR status bits
 // into it), and the check that waits for `st`, then reads and clears it.

@@ -10,14 +10,7 @@
 
 namespace hs {
 
-// Output tiles per pass are at most n/TO + n/(2T) + 1 <= n/1024 + 2 for the
-// smallest TO (2048) and tile (1024); one more entry closes the last tile.
-static size_t partition_entries(size_t n) { return n / 1024 + 8; }
-
-size_t merge_workspace_bytes(size_t n, int with_values) {
-    size_t kb = align_up(n * sizeof(int32_t), 256);
-    return kb + (with_values ? kb : 0) + align_up(partition_entries(n) * sizeof(int64_t), 256);
-}
+size_t merge_workspace_bytes(size_t n, int with_values) { return merge_workspace_size(n, with_values); }
 
 // Keys block sort: block_sort_tile3 with two leaves (L, L-1) or four leaves
 // (L, L, L, L-1) per thread.  Shapes (option "blocksort_shape"):
@@ -56,40 +49,40 @@ void merge_set_blocksort_shape(int v) { g_bs_shape = v; }
 
 template <int NT, int L, int LEAVES>
 static hs_status launch_blocksort_t(const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
-                                    int vec, cudaStream_t st) {
+                                    int vec, int32_t *samp, cudaStream_t st) {
     using C = BlockSort3<NT, L, LEAVES>;
     auto kern = k_blocksort3<NT, L, LEAVES>;
     hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
     if (r != HS_OK) return r;
     const int64_t grid = (n + C::T - 1) / C::T;
     LaunchToken t = launch_begin(K_BLOCKSORT_KEYS, st);
-    kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, vec);
+    kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, vec, samp);
     return launch_end(t);
 }
 
 template <int NT, int LEAVES>
 static hs_status launch_blocksort_nt(int L, const int32_t *kin, int32_t *kout, int64_t n,
-                                     hs_netset s, int vec, cudaStream_t st) {
+                                     hs_netset s, int vec, int32_t *samp, cudaStream_t st) {
     switch (L) {
-        case 1: return launch_blocksort_t<NT, 1, LEAVES>(kin, kout, n, s, vec, st);
-        case 3: return launch_blocksort_t<NT, 3, LEAVES>(kin, kout, n, s, vec, st);
-        case 4: return launch_blocksort_t<NT, 4, LEAVES>(kin, kout, n, s, vec, st);
-        case 5: return launch_blocksort_t<NT, 5, LEAVES>(kin, kout, n, s, vec, st);
-        case 6: return launch_blocksort_t<NT, 6, LEAVES>(kin, kout, n, s, vec, st);
-        case 7: return launch_blocksort_t<NT, 7, LEAVES>(kin, kout, n, s, vec, st);
-        case 8: return launch_blocksort_t<NT, 8, LEAVES>(kin, kout, n, s, vec, st);
+        case 1: return launch_blocksort_t<NT, 1, LEAVES>(kin, kout, n, s, vec, samp, st);
+        case 3: return launch_blocksort_t<NT, 3, LEAVES>(kin, kout, n, s, vec, samp, st);
+        case 4: return launch_blocksort_t<NT, 4, LEAVES>(kin, kout, n, s, vec, samp, st);
+        case 5: return launch_blocksort_t<NT, 5, LEAVES>(kin, kout, n, s, vec, samp, st);
+        case 6: return launch_blocksort_t<NT, 6, LEAVES>(kin, kout, n, s, vec, samp, st);
+        case 7: return launch_blocksort_t<NT, 7, LEAVES>(kin, kout, n, s, vec, samp, st);
+        case 8: return launch_blocksort_t<NT, 8, LEAVES>(kin, kout, n, s, vec, samp, st);
     }
     return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
 }
 
 hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
-                           int vec, cudaStream_t st) {
+                           int vec, cudaStream_t st, int32_t *samp) {
     switch (shape_for(n, L)) {
-        case 1: return launch_blocksort_nt<1024, 2>(L, kin, kout, n, s, vec, st);
-        case 2: return launch_blocksort_nt<256, 4>(L, kin, kout, n, s, vec, st);
-        case 3: return launch_blocksort_nt<512, 4>(L, kin, kout, n, s, vec, st);
-        case 4: return launch_blocksort_nt<288, 4>(L, kin, kout, n, s, vec, st);
-        default: return launch_blocksort_nt<512, 2>(L, kin, kout, n, s, vec, st);
+        case 1: return launch_blocksort_nt<1024, 2>(L, kin, kout, n, s, vec, samp, st);
+        case 2: return launch_blocksort_nt<256, 4>(L, kin, kout, n, s, vec, samp, st);
+        case 3: return launch_blocksort_nt<512, 4>(L, kin, kout, n, s, vec, samp, st);
+        case 4: return launch_blocksort_nt<288, 4>(L, kin, kout, n, s, vec, samp, st);
+        default: return launch_blocksort_nt<512, 2>(L, kin, kout, n, s, vec, samp, st);
     }
 }
 
@@ -97,17 +90,23 @@ hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, 
 // 16-byte aligned buffers with n % 4 == 0, in the shape of option
 // "merge_tile"; otherwise, or with option 0, the generic serial-merge pass.
 static int g_merge_kernel = 1;
-static int g_merge_tile = 2;
+static int g_merge_tile = 5;
+// Sampled partition searches (option "merge_samples", 1 by default): every
+// pass also writes each 32nd key of its output for the next partition.
+static int g_merge_samples = 1;
 
 void merge_set_kernel(int k) { g_merge_kernel = k; }
 void merge_set_tile(int v) { g_merge_tile = v; }
+void merge_set_samples(int v) { g_merge_samples = v; }
 
 constexpr int MG_NT = 256, MG_E = 16;  // generic keys level
 
+static bool tiled_levels(int64_t n, int vec) { return vec && g_merge_kernel == 1 && (n % 4) == 0; }
+
 static hs_status launch_keys_level(const int32_t *kin, int32_t *kout, int64_t n, int64_t w,
-                                   int64_t *part, int vec, cudaStream_t st) {
-    if (vec && g_merge_kernel == 1 && (n % 4) == 0)
-        return launch_keys_tile_level(g_merge_tile, kin, kout, n, w, part, st);
+                                   int64_t *part, int32_t *samp, int vec, cudaStream_t st) {
+    if (tiled_levels(n, vec))
+        return launch_keys_tile_level(g_merge_tile, kin, kout, n, w, part, samp, st);
     const LevelTiles lt = level_tiles(n, w, MG_NT * MG_E);
     LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
     k_merge_partition<<<(unsigned)((lt.nblocks + 255) / 256), 256, 0, st>>>(
@@ -132,26 +131,29 @@ hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, v
     int passes = 0;
     for (int64_t w = T; w < n; w *= 2) ++passes;
 
-    int32_t *kbuf = nullptr;
+    int32_t *kbuf = nullptr, *samp = nullptr;
     int64_t *part = nullptr;
+    const int vec = aligned(d_keys, 16) ? 1 : 0;
     if (passes > 0) {
         if (!d_ws || ws_bytes < merge_workspace_bytes(n_, 0))
             return fail(HS_ERR_INVALID_ARG, "merge sort: workspace smaller than hs_sort_workspace_bytes");
         if (!aligned(d_ws, 16)) return fail(HS_ERR_INVALID_ARG, "merge sort: workspace not 16-byte aligned");
         char *p = static_cast<char *>(d_ws);
         kbuf = reinterpret_cast<int32_t *>(p);
-        part = reinterpret_cast<int64_t *>(p + align_up(n_ * sizeof(int32_t), 256));
+        part = reinterpret_cast<int64_t *>(p + merge_ws_keys_bytes(n_));
+        // Samples feed the tiled levels' partition searches.
+        if (tiled_levels(n, vec) && g_merge_samples)
+            samp = reinterpret_cast<int32_t *>(p + merge_ws_keys_bytes(n_) + merge_ws_part_bytes(n_));
     }
-    const int vec = aligned(d_keys, 16) ? 1 : 0;
 
     // Land the last level in the caller's array: with an even number of
     // global levels the block sort writes in place.
     int32_t *kcur = (passes % 2 == 0) ? d_keys : kbuf;
     int32_t *kalt = (kcur == d_keys) ? kbuf : d_keys;
-    hs_status r = blocksort_launch(L, d_keys, kcur, n, s, vec, st);
+    hs_status r = blocksort_launch(L, d_keys, kcur, n, s, vec, st, samp);
     if (r != HS_OK) return r;
     for (int64_t w = T; w < n; w *= 2) {
-        if ((r = launch_keys_level(kcur, kalt, n, w, part, vec, st)) != HS_OK) return r;
+        if ((r = launch_keys_level(kcur, kalt, n, w, part, samp, vec, st)) != HS_OK) return r;
         std::swap(kcur, kalt);
     }
     return HS_OK;

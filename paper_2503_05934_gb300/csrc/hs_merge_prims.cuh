@@ -89,17 +89,19 @@ HS_DEV int merge_path2(const K *A, int na, const K *B, int nb, int diag) {
 // between them, which is one bitonic sequence of P keys; a P-wide bitonic
 // merge sorts it.  Only ties between equal keys can land in either order,
 // which keys alone cannot show.  Works on keys or on unique sort words.
+//
+// Every slot issues one load at a constant offset from A + ai or from
+// B + bi + P - 1, and the +infinity slots discard theirs: those loads reach
+// up to P - 1 words past the thread's last B key, so every buffer read this
+// way keeps P words of slack after its B runs.
 template <int EO, int P, class K>
 HS_DEV void exact_window_merge(const K *A, int ai, const K *B, int bi, int na, int cnt,
                                K (&x)[P]) {
     const int tb = P - (cnt - na);  // first slot of the descending B part
-    const K *pa = A + ai, *pb = B + bi;
+    const K *pa = A + ai, *pb = B + bi + (P - 1);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-        // One load per slot, always inside the thread's own keys: A ascending,
-        // B descending, +infinity in between (those slots load B[bi] and
-        // discard it).
-        const K v = (i < na) ? pa[i] : pb[(i >= tb) ? (P - 1 - i) : 0];
+        const K v = (i < na) ? pa[i] : pb[-i];
         x[i] = (i < na || i >= tb) ? v : word_max<K>();
     }
     bitonic_half_clean<P>(x);
@@ -206,6 +208,85 @@ static __global__ void k_merge_partition(const int32_t *in, int64_t n, int64_t w
         else hi = mid;
     }
     part[b] = lo;
+}
+
+// Sampled form for arrays whose runs start at multiples of kSampleStride:
+// samp[j] = in[j * kSampleStride] (written by the kernel that produced `in`,
+// and small enough to stay in L2).  Two interleaved binary searches over the
+// samples narrow [lo, hi] from both sides with conclusions that hold for the
+// unsampled keys too; the exact search then finishes in the array.  At a
+// candidate split i = m*S (S = kSampleStride), with j = diag - 1 - i:
+//   A[i] <= Bs[floor(j/S)] <= B[j]   proves A[i] <= B[j]  (split above i),
+//   A[i] >  Bs[ceil(j/S)]  >= B[j]   proves A[i] >  B[j]  (split at most i),
+// and both tests are monotone in m.  Same result as k_merge_partition.
+constexpr int kSampleStride = 32;
+
+static __global__ void k_merge_partition_sampled(const int32_t *in, const int32_t *samp,
+                                                 int64_t n, int64_t w, int to, int tpg,
+                                                 int64_t nblocks, int64_t *part) {
+    constexpr int64_t S = kSampleStride;
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    int64_t g = b / tpg, t = b - g * tpg;
+    MergeGeom m = merge_geom(g, n, w);
+    int64_t diag = t * to;
+    if (diag > m.alen + m.blen) diag = m.alen + m.blen;
+    const int32_t *A = in + m.gs;
+    const int32_t *B = in + m.gs + w;
+    int64_t lo = diag > m.blen ? diag - m.blen : 0;
+    int64_t hi = diag < m.alen ? diag : m.alen;
+    if (lo < hi) {
+        const int32_t *SA = samp + m.gs / S, *SB = samp + (m.gs + w) / S;
+        const int64_t m0 = (lo + S - 1) / S, m1 = (hi - 1) / S;  // candidates m*S in [lo, hi - 1]
+        if (m0 <= m1) {
+            int64_t fl = m0, fh = m1 + 1;  // first m whose lower-bound test fails
+            int64_t tl = m0, th = m1 + 1;  // first m whose upper-bound test holds
+            while (fl < fh || tl < th) {
+                if (fl < fh) {
+                    const int64_t fm = (fl + fh) >> 1;
+                    const int64_t j = diag - 1 - fm * S;
+                    if (SA[fm] <= SB[j / S]) fl = fm + 1;
+                    else fh = fm;
+                }
+                if (tl < th) {
+                    const int64_t tm = (tl + th) >> 1;
+                    const int64_t j = diag - 1 - tm * S;
+                    const int64_t ju = (j + S - 1) / S;
+                    if (ju * S < m.blen && SA[tm] > SB[ju]) th = tm;
+                    else tl = tm + 1;
+                }
+            }
+            if (fl > m0) lo = hs_max(lo, (fl - 1) * S + 1);
+            if (tl <= m1) hi = hs_min(hi, tl * S);
+        }
+    }
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    part[b] = lo;
+}
+
+// Stores a tile staged in shared memory, s[0, cnt), to dst (16-byte aligned)
+// as 16-byte streaming stores.  With samp, also writes the tile's samples
+// samp[(base + q) / S] = s[q] for q % S == 0 (base % S == 0), taken from the
+// lanes whose 16-byte word starts on a sample, so no extra shared-memory
+// reads (which would all fall on one bank).
+template <int NT>
+HS_DEV void store_tile_out(int32_t *dst, const int32_t *s, int cnt, int32_t *samp, int64_t base) {
+    constexpr int Q = kSampleStride / 4;  // 16-byte words per sample
+    const int n4 = cnt >> 2;
+    int32_t *sp = samp ? samp + base / kSampleStride : nullptr;
+    for (int q = threadIdx.x; q < n4; q += NT) {
+        const int4 v = *reinterpret_cast<const int4 *>(s + 4 * q);
+        st_stream(reinterpret_cast<int4 *>(dst) + q, v);
+        if (sp && q % Q == 0) sp[q / Q] = v.x;
+    }
+    for (int i = 4 * n4 + threadIdx.x; i < cnt; i += NT) {
+        st_stream(dst + i, s[i]);
+        if (sp && i % kSampleStride == 0) sp[i / kSampleStride] = s[i];
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -30,7 +30,7 @@ struct TileMerge {
 template <int NT, int EO>
 __global__ void __launch_bounds__(NT)
     k_merge_tile(const int32_t *in, int32_t *out, int64_t n, int64_t w, const int64_t *part,
-                 int tpg) {
+                 int tpg, int32_t *samp) {
     using C = TileMerge<NT, EO>;
     constexpr int TO = C::TO, P = C::P;
     extern __shared__ __align__(16) int32_t smem[];
@@ -94,10 +94,7 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
     int32_t *dst = out + m.gs + o0;  // 16-byte aligned: gs and o0 are multiples of 4
-    const int n4 = tot >> 2;
-    for (int q = threadIdx.x; q < n4; q += NT)
-        st_stream(reinterpret_cast<int4 *>(dst) + q, *reinterpret_cast<const int4 *>(sA + 4 * q));
-    for (int i = 4 * n4 + threadIdx.x; i < tot; i += NT) st_stream(dst + i, sA[i]);
+    store_tile_out<NT>(dst, sA, tot, samp, m.gs + o0);
 }
 
 // Exact-window form (the default): each thread merges exactly its own EO
@@ -110,14 +107,16 @@ struct TileMerge2 {
     static constexpr int EOUT = EO;
     static constexpr int P = pow2_at_least(EO);
     static constexpr int TO = NT * EO;
-    static constexpr int REG = TO + 16;
+    // Covers (at most TO + 12 words) plus the P words of slack that the
+    // window loads of exact_window_merge may touch past the last B key.
+    static constexpr int REG = TO + 16 + P;
     static constexpr int SMEM_BYTES = REG * 4;
 };
 
 template <int NT, int EO>
 __global__ void __launch_bounds__(NT)
     k_merge_tile2(const int32_t *in, int32_t *out, int64_t n, int64_t w, const int64_t *part,
-                  int tpg) {
+                  int tpg, int32_t *samp) {
     using C = TileMerge2<NT, EO>;
     constexpr int TO = C::TO, P = C::P;
     extern __shared__ __align__(16) int32_t smem[];
@@ -173,43 +172,49 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
     int32_t *dst = out + m.gs + o0;  // 16-byte aligned: gs and o0 are multiples of 4
-    const int n4 = tot >> 2;
-    for (int q = threadIdx.x; q < n4; q += NT)
-        st_stream(reinterpret_cast<int4 *>(dst) + q, *reinterpret_cast<const int4 *>(sA + 4 * q));
-    for (int i = 4 * n4 + threadIdx.x; i < tot; i += NT) st_stream(dst + i, sA[i]);
+    store_tile_out<NT>(dst, sA, tot, samp, m.gs + o0);
 }
 
-// Partition pass + one tiled merge launch for one level.
+// Partition pass + one tiled merge launch for one level.  With samp (samples
+// of kin at stride kSampleStride) the partition searches the samples first,
+// and the merge writes the samples of kout for the next level.
 template <auto KERN, class C>
 static hs_status launch_tile(const int32_t *kin, int32_t *kout, int64_t n, int64_t w,
-                             int64_t *part, cudaStream_t st) {
+                             int64_t *part, int32_t *samp, cudaStream_t st) {
+    static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
     const LevelTiles lt = level_tiles(n, w, C::TO);
     LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
-    k_merge_partition<<<(unsigned)((lt.nblocks + 255) / 256), 256, 0, st>>>(
-        kin, n, w, C::TO, (int)lt.tpg, lt.nblocks, part);
+    const unsigned pgrid = (unsigned)((lt.nblocks + 255) / 256);
+    if (samp)
+        k_merge_partition_sampled<<<pgrid, 256, 0, st>>>(kin, samp, n, w, C::TO, (int)lt.tpg,
+                                                          lt.nblocks, part);
+    else
+        k_merge_partition<<<pgrid, 256, 0, st>>>(kin, n, w, C::TO, (int)lt.tpg, lt.nblocks, part);
     hs_status r = launch_end(t);
     if (r != HS_OK) return r;
     if ((r = ensure_smem((const void *)KERN, C::SMEM_BYTES)) != HS_OK) return r;
     constexpr int NTH = C::TO / C::EOUT;
     t = launch_begin(K_MERGE_KEYS, st);
-    KERN<<<(unsigned)lt.nblocks, NTH, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, (int)lt.tpg);
+    KERN<<<(unsigned)lt.nblocks, NTH, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, (int)lt.tpg, samp);
     return launch_end(t);
 }
 
-// One tiled keys level; `shape` is the option "merge_tile": 2 (the default,
-// 128 threads x 31 keys, exact windows), 0 (window form, 256 x 15), and the
-// exact-window variants 1 (64 x 31), 3 (64 x 63), 4 (128 x 23), 5 (96 x 31),
-// 6 (192 x 31).
+// One tiled keys level; `shape` is the option "merge_tile": 5 (the default,
+// 96 threads x 31 keys, exact windows: small CTAs, many per SM, so loads,
+// merges and stores of neighbouring CTAs overlap), 0 (window form, 256 x 15),
+// and the exact-window variants 1 (64 x 31), 2 (128 x 31), 3 (64 x 63),
+// 4 (128 x 23), 6 (192 x 31), 7 (256 x 31).
 static hs_status launch_keys_tile_level(int shape, const int32_t *kin, int32_t *kout, int64_t n,
-                                        int64_t w, int64_t *part, cudaStream_t st) {
+                                        int64_t w, int64_t *part, int32_t *samp, cudaStream_t st) {
     switch (shape) {
-        case 0: return launch_tile<k_merge_tile<256, 15>, TileMerge<256, 15>>(kin, kout, n, w, part, st);
-        case 1: return launch_tile<k_merge_tile2<64, 31>, TileMerge2<64, 31>>(kin, kout, n, w, part, st);
-        case 3: return launch_tile<k_merge_tile2<64, 63>, TileMerge2<64, 63>>(kin, kout, n, w, part, st);
-        case 4: return launch_tile<k_merge_tile2<128, 23>, TileMerge2<128, 23>>(kin, kout, n, w, part, st);
-        case 5: return launch_tile<k_merge_tile2<96, 31>, TileMerge2<96, 31>>(kin, kout, n, w, part, st);
-        case 6: return launch_tile<k_merge_tile2<192, 31>, TileMerge2<192, 31>>(kin, kout, n, w, part, st);
-        default: return launch_tile<k_merge_tile2<128, 31>, TileMerge2<128, 31>>(kin, kout, n, w, part, st);
+        case 0: return launch_tile<k_merge_tile<256, 15>, TileMerge<256, 15>>(kin, kout, n, w, part, samp, st);
+        case 1: return launch_tile<k_merge_tile2<64, 31>, TileMerge2<64, 31>>(kin, kout, n, w, part, samp, st);
+        case 3: return launch_tile<k_merge_tile2<64, 63>, TileMerge2<64, 63>>(kin, kout, n, w, part, samp, st);
+        case 4: return launch_tile<k_merge_tile2<128, 23>, TileMerge2<128, 23>>(kin, kout, n, w, part, samp, st);
+        default: return launch_tile<k_merge_tile2<96, 31>, TileMerge2<96, 31>>(kin, kout, n, w, part, samp, st);
+        case 6: return launch_tile<k_merge_tile2<192, 31>, TileMerge2<192, 31>>(kin, kout, n, w, part, samp, st);
+        case 7: return launch_tile<k_merge_tile2<256, 31>, TileMerge2<256, 31>>(kin, kout, n, w, part, samp, st);
+        case 2: return launch_tile<k_merge_tile2<128, 31>, TileMerge2<128, 31>>(kin, kout, n, w, part, samp, st);
     }
 }
 

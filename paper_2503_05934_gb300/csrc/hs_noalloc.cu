@@ -19,11 +19,10 @@
 namespace hs {
 
 constexpr size_t kNoallocMaxKeys = HS_NOALLOC_MAX_KEYS;
-// Keys ping-pong copy plus the merge partition indices, laid out exactly as
-// the merge path expects its workspace.
-constexpr size_t kNoallocKeyBytes = (kNoallocMaxKeys * sizeof(int32_t) + 255) / 256 * 256;
-constexpr size_t kNoallocPartBytes = ((kNoallocMaxKeys / 1024 + 8) * sizeof(int64_t) + 255) / 256 * 256;
-constexpr size_t kNoallocBytes = kNoallocKeyBytes + kNoallocPartBytes;
+// The merge path's keys workspace for the largest accepted input, by the same
+// formula as hs_sort_workspace_bytes (the layout grows monotonically in n, so
+// every shorter input fits).
+constexpr size_t kNoallocBytes = merge_workspace_size(kNoallocMaxKeys, 0);
 
 // The scratch area.  In host code this name is only a host-side stand-in for
 // the device symbol: its device address comes from cudaGetSymbolAddress below.
@@ -74,6 +73,7 @@ extern "C" hs_status hs_sort_i32_noalloc(int32_t *d_keys, size_t n, hs_netset s,
     hs_status st = noalloc_scratch(&scratch);
     if (st != HS_OK) return st;
     // Nothing in the scratch has to start at zero: the merge path writes every
-    // word it reads (keys copy and partition indices) earlier in the same call.
+    // word it reads (keys copy, partition indices, samples) earlier in the
+    // same call.
     return merge_sort(d_keys, nullptr, n, s, scratch, kNoallocBytes, (cudaStream_t)stream);
 }

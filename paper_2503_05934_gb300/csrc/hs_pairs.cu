@@ -222,7 +222,7 @@ hs_status pairs_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, v
             return fail(HS_ERR_INVALID_ARG, "pair sort: workspace smaller than hs_sort_workspace_bytes");
         if (!aligned(d_ws, 16)) return fail(HS_ERR_INVALID_ARG, "pair sort: workspace not 16-byte aligned");
         char *p = static_cast<char *>(d_ws);
-        const size_t kb = align_up(n_ * sizeof(int32_t), 256);
+        const size_t kb = merge_ws_keys_bytes(n_);
         kbuf = reinterpret_cast<int32_t *>(p);
         vbuf = reinterpret_cast<int32_t *>(p + kb);
         part = reinterpret_cast<int64_t *>(p + 2 * kb);

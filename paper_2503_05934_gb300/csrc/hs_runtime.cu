@@ -290,8 +290,8 @@ hs_status hs_set_option(const char *name, int64_t value) {
         return HS_OK;
     }
     if (std::strcmp(name, "merge_tile") == 0) {
-        if (value < 0 || value > 6)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_tile must be 0..6");
+        if (value < 0 || value > 7)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_tile must be 0..7");
         merge_set_tile((int)value);
         return HS_OK;
     }
@@ -305,6 +305,12 @@ hs_status hs_set_option(const char *name, int64_t value) {
         if (value != 512 && value != 1024)
             return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_threads must be 512 or 1024");
         merge_set_blocksort_threads((int)value);
+        return HS_OK;
+    }
+    if (std::strcmp(name, "merge_samples") == 0) {
+        if (value != 0 && value != 1)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_samples must be 0 or 1");
+        merge_set_samples((int)value);
         return HS_OK;
     }
     if (std::strcmp(name, "pairs_blocksort") == 0) {

@@ -222,6 +222,27 @@ def test_many_duplicates_and_runs(hs):
         assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), mod
 
 
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("samples", [0, 1])
+def test_merge_tile_shapes_and_samples(hs, tile, samples):
+    """Every tiled merge-level shape, with and without sampled partition
+    searches, on uniform keys, few distinct keys and presorted runs."""
+    hs.hs_set_option("merge_tile", tile)
+    hs.hs_set_option("merge_samples", samples)
+    try:
+        for n in [9000, 65_536, 250_000, 1 << 20]:
+            for kind in ["uniform", "few", "sorted"]:
+                a = g.random_i32(n, n + tile)
+                if kind == "few":
+                    a = (a % 3).astype(np.int32)
+                elif kind == "sorted":
+                    a = g.keys(n, "nearly", n + tile)
+                assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), (n, kind)
+    finally:
+        hs.hs_set_option("merge_tile", 5)
+        hs.hs_set_option("merge_samples", 1)
+
+
 @pytest.mark.parametrize("shape", [-1, 0, 1, 2, 3, 4])
 @pytest.mark.parametrize("kernel", [0, 1])
 def test_tuning_options_keep_results(hs, shape, kernel):
