@@ -35,11 +35,12 @@ METRIC = "int32 keys/s & %HBM roofline; batched vs plain keys/s; serve p50/p99"
 UNIT = "keys/s"
 FALLBACK_HBM_GBS = 6800.0
 SPEC_HBM_GBS = 8000.0
+# Sources of the dominant kernel (the tiled keys merge level), its launch
+# shape and its partition pass: the committed ncu traffic figure applies only
+# while these are unchanged.
 KERNEL_SOURCES = ["paper_2503_05934_gb300/csrc/hs_merge_tile.cuh",
                   "paper_2503_05934_gb300/csrc/hs_merge_prims.cuh",
-                  "paper_2503_05934_gb300/csrc/hs_merge.cu",
-                  "paper_2503_05934_gb300/csrc/hs_common.cuh",
-                  "paper_2503_05934_gb300/csrc/hs_networks.cuh"]
+                  "paper_2503_05934_gb300/csrc/hs_common.cuh"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "merge_keys_2p28_uniform.md")
 
 
@@ -69,7 +70,8 @@ def workload_config(args, n):
                     f"{args.netset} network leaves",
         "n": n, "dist": "uniform over [INT32_MIN, INT32_MAX]", "algo": "merge",
         "netset": args.netset, "seed": hs_inputs.config_seed(2),
-        "l2": "inputs larger than L2 (1 GiB per array vs 129 MB L2)",
+        "l2": (f"inputs larger than L2 ({4 * n / 2**20:.0f} MiB per array vs 129 MB L2)"
+               if 4 * n > 129e6 else f"input of {4 * n / 2**20:.1f} MiB may stay in the 129 MB L2"),
         "restore": "in-place sort; the input is restored from a pristine device copy "
                    "before each step, outside the timed events",
         "parallelism": "replicas (one independent array per GPU)",
@@ -81,6 +83,23 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(value: float, pg, device) -> float:
+    """The maximum of a per-rank float over all ranks (the value itself
+    without a process group): the slowest rank sets the job's time."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Units per second of the whole job: every rank processes its own
+    units (replicas), all within the slowest rank's time."""
+    return world * units_per_rank / seconds
 
 
 # ---------------------------------------------------------------- clocks
@@ -298,12 +317,8 @@ def run_ours(args):
     # Correctness guard on the last result (cheap: sortedness on the device).
     assert bool((work[1:] >= work[:-1]).all().item()), "benchmark output not sorted"
 
-    if pg:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-
-    value = ws_world * n * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, pg, dev)
+    value = whole_job_rate(ws_world, n * args.steps, total_ms / 1e3)
     peak, peak_kind = measured_peak()
     avg_mk_s = (mk_ms / mk_launches) / 1e3 if mk_launches else None
     alg_bytes = 8.0 * n  # one read + one write of every key per merge level
@@ -361,12 +376,9 @@ def run_ours(args):
             t0 = time.perf_counter()
             hs.hs_sort_i32_host(h_buf, "merge", args.netset, ws=ws_h, stream=stream)
             tot += time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([tot], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(tot, pg, dev)
         assert bool(np.all(h_buf.numpy()[1:] >= h_buf.numpy()[:-1])), "e2e output not sorted"
-        line["e2e"] = {"value": ws_world * n * e2e_steps / tot, "unit": UNIT,
+        line["e2e"] = {"value": whole_job_rate(ws_world, n * e2e_steps, tot), "unit": UNIT,
                        "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
                        "steps": e2e_steps, "api": "hs_sort_i32_host (pinned host buffer)"}
         del ws_h, h_buf

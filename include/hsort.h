@@ -299,8 +299,9 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *     before; 0 plain searches in the keys.
  *   "pairs_blocksort": pair block-sort shape, 0 (default) 256 threads x 4
  *     leaves, 1: 512 x 2, 2: 512 x 4, 3: 288 x 4.
- *   "pairs_merge": 1 (default) tiled pair levels (16-byte aligned keys and
- *     values, n % 4 == 0), 0 staged-load serial merges.
+ *   "pairs_merge": tiled pair levels (16-byte aligned keys and values,
+ *     n % 4 == 0) with 1 (default) 128 threads x 31 pairs or 2 96 x 31,
+ *     both with sampled partition searches; 0 staged-load serial merges.
  *     Every option gives identical results.
  * Unknown names or values return HS_ERR_INVALID_ARG. */
 HS_API hs_status hs_set_option(const char *name, int64_t value);

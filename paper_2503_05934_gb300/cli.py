@@ -1,0 +1,87 @@
+"""Sorts one synthetic array on the GPU through the library's public calls and
+prints the time per sort.
+
+    python -m paper_2503_05934_gb300.cli --what keys --log2n 26 --dist uniform
+    python -m paper_2503_05934_gb300.cli --what pairs --log2n 25 --reps 3
+    python -m paper_2503_05934_gb300.cli --what quick --dist nearly --option quick_max_levels=64
+
+Keys are int32 from the seeded generators of ``hs_inputs`` (uniform over the
+int32 range, sorted, or nearly sorted); pairs carry keys from 2^16 distinct
+values and values = original index.  Every run restores the input from a
+pristine device copy (untimed), times the sort with CUDA events on the
+sorting stream, and checks that the output is sorted (pairs: and stable).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--what", choices=["keys", "quick", "pairs"], default="keys")
+    ap.add_argument("--log2n", type=int, default=24)
+    ap.add_argument("--dist", choices=["uniform", "sorted", "nearly"], default="uniform")
+    ap.add_argument("--netset", default="6To8")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--option", action="append", default=[], help="name=value for hs_set_option")
+    args = ap.parse_args(argv)
+
+    import torch
+
+    import hs_inputs
+    import paper_2503_05934_gb300 as hs
+
+    for opt in args.option:
+        name, value = opt.split("=")
+        hs.hs_set_option(name, int(value))
+    dev = torch.device("cuda", 0)
+    n = 1 << args.log2n
+    st = torch.cuda.current_stream(dev)
+    if args.what == "pairs":
+        k, v = hs_inputs.pair_keys_16bit(n, args.seed)
+        src = [torch.from_numpy(k).to(dev), torch.from_numpy(v).to(dev)]
+        ws = torch.empty(hs.hs_sort_workspace_bytes(n, True), dtype=torch.uint8, device=dev)
+
+        def run(bufs):
+            hs.hs_sort_pairs_i32(bufs[0], bufs[1], "merge", args.netset, ws=ws, stream=st)
+    else:
+        dist = "random" if args.dist == "uniform" else args.dist
+        src = [torch.from_numpy(hs_inputs.keys(n, dist, args.seed)).to(dev)]
+        algo = "quick" if args.what == "quick" else "merge"
+        ws = torch.empty(hs.hs_sort_workspace_bytes(n, False, algo), dtype=torch.uint8, device=dev)
+
+        def run(bufs):
+            hs.hs_sort_i32(bufs[0], algo, args.netset, ws=ws, stream=st)
+    work = [torch.empty_like(t) for t in src]
+    times = []
+    for _ in range(args.reps):
+        for w_, s_ in zip(work, src):
+            w_.copy_(s_)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        run(work)
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    hs.hs_device_check()
+    keys = work[0]
+    ok = bool((keys[1:] >= keys[:-1]).all().item())
+    if args.what == "pairs":
+        same = keys[1:] == keys[:-1]
+        ok = ok and bool(((work[1][1:] > work[1][:-1]) | ~same).all().item())
+    print(json.dumps({"what": args.what, "n": n, "dist": args.dist, "netset": args.netset,
+                      "ms": times, "sorted": ok}))
+    return 0 if ok else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -233,7 +233,7 @@ struct BlockSortPairs {
 template <int NT, int L, int LEAVES = 2>
 HS_DEV void block_sort_pairs_tile(const int32_t *kin, int32_t *kout, const int32_t *vin,
                                   int32_t *vout, int cnt, uint32_t netset, bool vec,
-                                  int64_t *sw) {
+                                  int64_t *sw, int32_t *samp, int64_t base) {
     using C = BlockSortPairs<NT, L, LEAVES>;
     constexpr int EO = C::EO, P = C::P, T = C::T;
     int32_t *s32 = reinterpret_cast<int32_t *>(sw);  // 2 * W_WORDS int32 slots
@@ -275,21 +275,14 @@ HS_DEV void block_sort_pairs_tile(const int32_t *kin, int32_t *kout, const int32
     }
     __syncthreads();
     if (vec && (T % 4) == 0) {
-        const int n4 = cnt >> 2;
-        int4 *dk = reinterpret_cast<int4 *>(kout);
-        int4 *dv = reinterpret_cast<int4 *>(vout);
-        for (int q = threadIdx.x; q < n4; q += NT) {
-            st_stream(dk + q, *reinterpret_cast<const int4 *>(s32 + 4 * q));
-            st_stream(dv + q, *reinterpret_cast<const int4 *>(s32 + T + 4 * q));
-        }
-        for (int i = 4 * n4 + threadIdx.x; i < cnt; i += NT) {
-            kout[i] = s32[i];
-            vout[i] = s32[T + i];
-        }
+        store_tile_out<NT>(kout, s32, cnt, samp, base);
+        store_tile_out<NT>(vout, s32 + T, cnt, nullptr, 0);
     } else {
+        int32_t *sp = samp ? samp + base / kSampleStride : nullptr;
         for (int i = threadIdx.x; i < cnt; i += NT) {
             kout[i] = s32[i];
             vout[i] = s32[T + i];
+            if (sp && i % kSampleStride == 0) sp[i / kSampleStride] = s32[i];
         }
     }
 }
@@ -297,13 +290,14 @@ HS_DEV void block_sort_pairs_tile(const int32_t *kin, int32_t *kout, const int32
 template <int NT, int L, int LEAVES = 2>
 __global__ void __launch_bounds__(NT)
     k_blocksort_pairs(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
-                      int64_t n, uint32_t netset, int vec) {
+                      int64_t n, uint32_t netset, int vec, int32_t *samp) {
     constexpr int T = BlockSortPairs<NT, L, LEAVES>::T;
+    static_assert(T % kSampleStride == 0, "tiles start on sample positions");
     extern __shared__ __align__(16) int64_t smem64[];
     const int64_t base = (int64_t)blockIdx.x * T;
     const int cnt = (int)((n - base) < T ? (n - base) : T);
     block_sort_pairs_tile<NT, L, LEAVES>(kin + base, kout + base, vin + base, vout + base, cnt,
-                                         netset, vec != 0, smem64);
+                                         netset, vec != 0, smem64, samp, base);
 }
 
 }  // namespace hs

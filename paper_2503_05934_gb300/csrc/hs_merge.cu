@@ -90,7 +90,7 @@ hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, 
 // 16-byte aligned buffers with n % 4 == 0, in the shape of option
 // "merge_tile"; otherwise, or with option 0, the generic serial-merge pass.
 static int g_merge_kernel = 1;
-static int g_merge_tile = 5;
+static int g_merge_tile = kDefaultMergeTile;
 // Sampled partition searches (option "merge_samples", 1 by default): every
 // pass also writes each 32nd key of its output for the next partition.
 static int g_merge_samples = 1;

@@ -199,6 +199,8 @@ static hs_status launch_tile(const int32_t *kin, int32_t *kout, int64_t n, int64
     return launch_end(t);
 }
 
+constexpr int kDefaultMergeTile = 5;
+
 // One tiled keys level; `shape` is the option "merge_tile": 5 (the default,
 // 96 threads x 31 keys, exact windows: small CTAs, many per SM, so loads,
 // merges and stores of neighbouring CTAs overlap), 0 (window form, 256 x 15),
@@ -209,12 +211,12 @@ static hs_status launch_keys_tile_level(int shape, const int32_t *kin, int32_t *
     switch (shape) {
         case 0: return launch_tile<k_merge_tile<256, 15>, TileMerge<256, 15>>(kin, kout, n, w, part, samp, st);
         case 1: return launch_tile<k_merge_tile2<64, 31>, TileMerge2<64, 31>>(kin, kout, n, w, part, samp, st);
+        case 2: return launch_tile<k_merge_tile2<128, 31>, TileMerge2<128, 31>>(kin, kout, n, w, part, samp, st);
         case 3: return launch_tile<k_merge_tile2<64, 63>, TileMerge2<64, 63>>(kin, kout, n, w, part, samp, st);
         case 4: return launch_tile<k_merge_tile2<128, 23>, TileMerge2<128, 23>>(kin, kout, n, w, part, samp, st);
-        default: return launch_tile<k_merge_tile2<96, 31>, TileMerge2<96, 31>>(kin, kout, n, w, part, samp, st);
         case 6: return launch_tile<k_merge_tile2<192, 31>, TileMerge2<192, 31>>(kin, kout, n, w, part, samp, st);
         case 7: return launch_tile<k_merge_tile2<256, 31>, TileMerge2<256, 31>>(kin, kout, n, w, part, samp, st);
-        case 2: return launch_tile<k_merge_tile2<128, 31>, TileMerge2<128, 31>>(kin, kout, n, w, part, samp, st);
+        default: return launch_tile<k_merge_tile2<96, 31>, TileMerge2<96, 31>>(kin, kout, n, w, part, samp, st);
     }
 }
 

@@ -28,7 +28,7 @@ struct TileMergePairs {
 template <int NT, int EO>
 __global__ void __launch_bounds__(NT)
     k_merge_tile_pairs(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
-                       int64_t n, int64_t w, const int64_t *part, int tpg) {
+                       int64_t n, int64_t w, const int64_t *part, int tpg, int32_t *samp) {
     using C = TileMergePairs<NT, EO>;
     constexpr int TO = C::TO;
     extern __shared__ __align__(16) int32_t smem[];
@@ -110,15 +110,8 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
     int32_t *dk = kout + m.gs + o0, *dv = vout + m.gs + o0;  // 16-byte aligned
-    const int n4 = tot >> 2;
-    for (int q = threadIdx.x; q < n4; q += NT) {
-        st_stream(reinterpret_cast<int4 *>(dk) + q, *reinterpret_cast<const int4 *>(sK + 4 * q));
-        st_stream(reinterpret_cast<int4 *>(dv) + q, *reinterpret_cast<const int4 *>(sV + 4 * q));
-    }
-    for (int i = 4 * n4 + threadIdx.x; i < tot; i += NT) {
-        st_stream(dk + i, sK[i]);
-        st_stream(dv + i, sV[i]);
-    }
+    store_tile_out<NT>(dk, sK, tot, samp, m.gs + o0);
+    store_tile_out<NT>(dv, sV, tot, nullptr, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -129,8 +122,9 @@ __global__ void __launch_bounds__(NT)
 // leaves (one CTA per SM), 3 = 288 x 4 leaves (tiles of at least 8192 pairs
 // for the {6,7,8} set).
 static int g_pairs_bs = 0;
-// Merge level (option "pairs_merge"): 1 = tiled (the default when aligned),
-// 0 = the generic serial-merge pass.
+// Merge level (option "pairs_merge"): 1 = tiled, 128 threads x 31 pairs (the
+// default when aligned), 2 = tiled, 96 x 31, 0 = the generic
+// serial-merge pass.  The tiled levels use sampled partition searches.
 static int g_pairs_merge = 1;
 
 void pairs_set_blocksort(int v) { g_pairs_bs = v; }
@@ -148,56 +142,71 @@ int64_t pairs_tile(int L) {
 template <int NT, int L, int LEAVES>
 static hs_status launch_pairs_blocksort_t(const int32_t *kin, int32_t *kout, const int32_t *vin,
                                           int32_t *vout, int64_t n, hs_netset s, int vec,
-                                          cudaStream_t st) {
+                                          int32_t *samp, cudaStream_t st) {
     using C = BlockSortPairs<NT, L, LEAVES>;
     auto kern = k_blocksort_pairs<NT, L, LEAVES>;
     hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
     if (r != HS_OK) return r;
     const int64_t grid = (n + C::T - 1) / C::T;
     LaunchToken t = launch_begin(K_BLOCKSORT_PAIRS, st);
-    kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, s, vec);
+    kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, s, vec, samp);
     return launch_end(t);
 }
 
 template <int NT, int LEAVES>
 static hs_status launch_pairs_blocksort_nt(int L, const int32_t *kin, int32_t *kout,
                                            const int32_t *vin, int32_t *vout, int64_t n,
-                                           hs_netset s, int vec, cudaStream_t st) {
+                                           hs_netset s, int vec, int32_t *samp, cudaStream_t st) {
     switch (L) {
-        case 1: return launch_pairs_blocksort_t<NT, 1, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
-        case 3: return launch_pairs_blocksort_t<NT, 3, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
-        case 4: return launch_pairs_blocksort_t<NT, 4, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
-        case 5: return launch_pairs_blocksort_t<NT, 5, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
-        case 6: return launch_pairs_blocksort_t<NT, 6, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
-        case 7: return launch_pairs_blocksort_t<NT, 7, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
-        case 8: return launch_pairs_blocksort_t<NT, 8, LEAVES>(kin, kout, vin, vout, n, s, vec, st);
+        case 1: return launch_pairs_blocksort_t<NT, 1, LEAVES>(kin, kout, vin, vout, n, s, vec, samp, st);
+        case 3: return launch_pairs_blocksort_t<NT, 3, LEAVES>(kin, kout, vin, vout, n, s, vec, samp, st);
+        case 4: return launch_pairs_blocksort_t<NT, 4, LEAVES>(kin, kout, vin, vout, n, s, vec, samp, st);
+        case 5: return launch_pairs_blocksort_t<NT, 5, LEAVES>(kin, kout, vin, vout, n, s, vec, samp, st);
+        case 6: return launch_pairs_blocksort_t<NT, 6, LEAVES>(kin, kout, vin, vout, n, s, vec, samp, st);
+        case 7: return launch_pairs_blocksort_t<NT, 7, LEAVES>(kin, kout, vin, vout, n, s, vec, samp, st);
+        case 8: return launch_pairs_blocksort_t<NT, 8, LEAVES>(kin, kout, vin, vout, n, s, vec, samp, st);
     }
     return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
 }
 
-constexpr int PM_NT = 128, PM_EO = 31;  // tiled level
-constexpr int PG_NT = 256, PG_E = 8;    // generic level
+constexpr int PG_NT = 256, PG_E = 8;  // generic level
 
-static hs_status launch_pairs_level(const int32_t *kin, int32_t *kout, const int32_t *vin,
-                                    int32_t *vout, int64_t n, int64_t w, int64_t *part, int vec,
-                                    cudaStream_t st) {
-    const bool tiled = vec && g_pairs_merge == 1 && (n % 4) == 0;
-    const int64_t to = tiled ? TileMergePairs<PM_NT, PM_EO>::TO : PG_NT * PG_E;
-    const LevelTiles lt = level_tiles(n, w, to);
+template <int NT, int EO>
+static hs_status launch_pairs_tile(const int32_t *kin, int32_t *kout, const int32_t *vin,
+                                   int32_t *vout, int64_t n, int64_t w, int64_t *part,
+                                   int32_t *samp, cudaStream_t st) {
+    using C = TileMergePairs<NT, EO>;
+    static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
+    const LevelTiles lt = level_tiles(n, w, C::TO);
     LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
-    k_merge_partition<<<(unsigned)((lt.nblocks + 255) / 256), 256, 0, st>>>(
-        kin, n, w, (int)to, (int)lt.tpg, lt.nblocks, part);
+    k_merge_partition_sampled<<<(unsigned)((lt.nblocks + 255) / 256), 256, 0, st>>>(
+        kin, samp, n, w, C::TO, (int)lt.tpg, lt.nblocks, part);
     hs_status r = launch_end(t);
     if (r != HS_OK) return r;
-    if (tiled) {
-        using C = TileMergePairs<PM_NT, PM_EO>;
-        auto kern = k_merge_tile_pairs<PM_NT, PM_EO>;
-        if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
-        t = launch_begin(K_MERGE_PAIRS, st);
-        kern<<<(unsigned)lt.nblocks, PM_NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, w, part,
-                                                                 (int)lt.tpg);
-        return launch_end(t);
+    auto kern = k_merge_tile_pairs<NT, EO>;
+    if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
+    t = launch_begin(K_MERGE_PAIRS, st);
+    kern<<<(unsigned)lt.nblocks, NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, w, part,
+                                                          (int)lt.tpg, samp);
+    return launch_end(t);
+}
+
+static bool pairs_tiled(int64_t n, int vec) { return vec && g_pairs_merge >= 1 && (n % 4) == 0; }
+
+static hs_status launch_pairs_level(const int32_t *kin, int32_t *kout, const int32_t *vin,
+                                    int32_t *vout, int64_t n, int64_t w, int64_t *part,
+                                    int32_t *samp, int vec, cudaStream_t st) {
+    if (pairs_tiled(n, vec)) {
+        return g_pairs_merge == 1
+                   ? launch_pairs_tile<128, 31>(kin, kout, vin, vout, n, w, part, samp, st)
+                   : launch_pairs_tile<96, 31>(kin, kout, vin, vout, n, w, part, samp, st);
     }
+    const LevelTiles lt = level_tiles(n, w, PG_NT * PG_E);
+    LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
+    k_merge_partition<<<(unsigned)((lt.nblocks + 255) / 256), 256, 0, st>>>(
+        kin, n, w, PG_NT * PG_E, (int)lt.tpg, lt.nblocks, part);
+    hs_status r = launch_end(t);
+    if (r != HS_OK) return r;
     const int smem = merge_smem_words<PG_NT, PG_E>() * (int)sizeof(int32_t) * 2;
     auto kern = k_merge_pass<PG_NT, PG_E, true>;
     if ((r = ensure_smem((const void *)kern, smem)) != HS_OK) return r;
@@ -215,8 +224,9 @@ hs_status pairs_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, v
     int passes = 0;
     for (int64_t w = T; w < n; w *= 2) ++passes;
 
-    int32_t *kbuf = nullptr, *vbuf = nullptr;
+    int32_t *kbuf = nullptr, *vbuf = nullptr, *samp = nullptr;
     int64_t *part = nullptr;
+    const int vec = aligned(d_keys, 16) && aligned(d_vals, 16) ? 1 : 0;
     if (passes > 0) {
         if (!d_ws || ws_bytes < merge_workspace_bytes(n_, 1))
             return fail(HS_ERR_INVALID_ARG, "pair sort: workspace smaller than hs_sort_workspace_bytes");
@@ -226,8 +236,9 @@ hs_status pairs_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, v
         kbuf = reinterpret_cast<int32_t *>(p);
         vbuf = reinterpret_cast<int32_t *>(p + kb);
         part = reinterpret_cast<int64_t *>(p + 2 * kb);
+        if (pairs_tiled(n, vec))
+            samp = reinterpret_cast<int32_t *>(p + 2 * kb + merge_ws_part_bytes(n_));
     }
-    const int vec = aligned(d_keys, 16) && aligned(d_vals, 16) ? 1 : 0;
 
     // With an even number of global levels the block sort writes in place, so
     // the last level lands in the caller's arrays.
@@ -238,14 +249,14 @@ hs_status pairs_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, v
 
     hs_status r;
     switch (g_pairs_bs) {
-        case 1: r = launch_pairs_blocksort_nt<512, 2>(L, d_keys, kcur, d_vals, vcur, n, s, vec, st); break;
-        case 2: r = launch_pairs_blocksort_nt<512, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, st); break;
-        case 3: r = launch_pairs_blocksort_nt<288, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, st); break;
-        default: r = launch_pairs_blocksort_nt<256, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, st);
+        case 1: r = launch_pairs_blocksort_nt<512, 2>(L, d_keys, kcur, d_vals, vcur, n, s, vec, samp, st); break;
+        case 2: r = launch_pairs_blocksort_nt<512, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, samp, st); break;
+        case 3: r = launch_pairs_blocksort_nt<288, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, samp, st); break;
+        default: r = launch_pairs_blocksort_nt<256, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, samp, st);
     }
     if (r != HS_OK) return r;
     for (int64_t w = T; w < n; w *= 2) {
-        if ((r = launch_pairs_level(kcur, kalt, vcur, valt, n, w, part, vec, st)) != HS_OK) return r;
+        if ((r = launch_pairs_level(kcur, kalt, vcur, valt, n, w, part, samp, vec, st)) != HS_OK) return r;
         std::swap(kcur, kalt);
         std::swap(vcur, valt);
     }

@@ -320,8 +320,8 @@ hs_status hs_set_option(const char *name, int64_t value) {
         return HS_OK;
     }
     if (std::strcmp(name, "pairs_merge") == 0) {
-        if (value != 0 && value != 1)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: pairs_merge must be 0 or 1");
+        if (value < 0 || value > 2)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: pairs_merge must be 0..2");
         pairs_set_merge((int)value);
         return HS_OK;
     }

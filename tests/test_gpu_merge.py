@@ -135,7 +135,7 @@ def test_pairs_unaligned(hs):
 
 
 @pytest.mark.parametrize("bs", [0, 1, 2, 3])
-@pytest.mark.parametrize("merge", [0, 1])
+@pytest.mark.parametrize("merge", [0, 1, 2])
 def test_pairs_options_keep_results(hs, bs, merge):
     """Every pair block-sort shape and merge-level kernel gives the oracle's
     stable order: sizes around the tiles (7936 / 7680 / 15872 / 8928 pairs

@@ -83,3 +83,19 @@ def test_over_budget_and_unsupported_requests(hs):
         assert err.value.status == 2
     finally:
         srv.destroy()
+
+
+def test_destroy_finishes_submitted_work(hs):
+    """Shutting the server down with requests still queued (none waited for,
+    under a budget that forces admission to throttle) completes every one of
+    them before it frees anything."""
+    import torch
+    inputs = _requests(200, 13, 8, 1 << 19)
+    mixed = [torch.from_numpy(a.copy()).cuda() for a in inputs]
+    srv = hs.Server(16 << 20)
+    for t in mixed:
+        srv.submit(t)
+    srv.destroy()
+    torch.cuda.synchronize()
+    for a, y in zip(inputs, mixed):
+        assert np.array_equal(y.cpu().numpy(), np.sort(a))
