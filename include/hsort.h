@@ -283,7 +283,7 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *     guard merge-sorts the segments still open (default -1 = automatic,
  *     4*ceil(log2 n) + 16).
  *   "blocksort_shape": keys block-sort shape, 0: 512 threads x 2 leaves,
- *     1: 1024 x 2, 2: 256 x 4, 3: 512 x 4, 4: 288 x 4, -1 (default): per
+ *     1: 1024 x 2, 2: 256 x 4, 3: 512 x 4, 4: 288 x 4, 5: 576 x 4, -1 (default): per
  *     array, 4 when its larger tile saves a global level over 2, else 2.  A thread holds its
  *     leaves as leaf, ..., leaf, leaf-1 keys, so the first merge tile holds
  *     (leaves * leaf - 1) * threads keys.

@@ -199,8 +199,8 @@ HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_
 // Tile t covers keys [t*T, (t+1)*T); the last tile may be short.  kin/kout
 // may alias: each CTA reads its whole tile into shared memory before writing.
 // Resident CTAs per SM the register budget must allow (about as many as the
-// shared tiles fit): 5 of up to 288 threads, 3 of 512.
-constexpr int blocksort_min_ctas(int nt) { return nt <= 288 ? 5 : nt <= 512 ? 3 : 1; }
+// shared tiles fit): 5 of up to 288 threads, 3 of 512, 2 of 576.
+constexpr int blocksort_min_ctas(int nt) { return nt <= 288 ? 5 : nt <= 512 ? 3 : nt <= 576 ? 2 : 1; }
 
 template <int NT, int L, int LEAVES = 2>
 __global__ void __launch_bounds__(NT, blocksort_min_ctas(NT))

@@ -15,7 +15,7 @@ size_t merge_workspace_bytes(size_t n, int with_values) { return merge_workspace
 // Keys block sort: block_sort_tile3 with two leaves (L, L-1) or four leaves
 // (L, L, L, L-1) per thread.  Shapes (option "blocksort_shape"):
 //   0: 512 threads x 2 leaves   1: 1024 x 2   2: 256 x 4   3: 512 x 4
-//   4: 288 x 4 (tiles of 8928 keys for the {6,7,8} set)
+//   4: 288 x 4 (tiles of 8928 keys for the {6,7,8} set)   5: 576 x 4
 //  -1 (default): per n, shape 4 when its larger tile needs fewer global
 //      levels than shape 2's (e.g. every power of two from 2^14 up), else 2.
 static int g_bs_shape = -1;
@@ -25,6 +25,7 @@ static int shape_threads(int shape) {
         case 1: return 1024;
         case 2: return 256;
         case 4: return 288;
+        case 5: return 576;
         default: return 512;
     }
 }
@@ -82,6 +83,7 @@ hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, 
         case 2: return launch_blocksort_nt<256, 4>(L, kin, kout, n, s, vec, samp, st);
         case 3: return launch_blocksort_nt<512, 4>(L, kin, kout, n, s, vec, samp, st);
         case 4: return launch_blocksort_nt<288, 4>(L, kin, kout, n, s, vec, samp, st);
+        case 5: return launch_blocksort_nt<576, 4>(L, kin, kout, n, s, vec, samp, st);
         default: return launch_blocksort_nt<512, 2>(L, kin, kout, n, s, vec, samp, st);
     }
 }

@@ -9,16 +9,21 @@
 // by the block sort, whose leaves are the network base cases.
 //
 // Per level (all segments at once, chunks of QS_C keys):
-//   k_qs_pivot    median of three per segment, zero its counters
-//   k_qs_count    per chunk: #<, #= ; atomically summed per segment
-//   k_qs_scatter  per chunk: reserve ranges with atomic cursors, write < and >
-//                 keys to the other buffer (coalesced runs per warp)
-//   k_qs_fill     per chunk: write the pivot over the chunk's share of the
-//                 segment's = range in the caller's array (final positions)
-//   k_qs_next     children -> next level (> tile) or small list (<= tile)
-//   k_qs_small    block sort of each small child into the caller's array
-//   k_qs_chunkmap chunk -> segment map of the next level
-// The host reads three counters back per level to size the next launches.
+//   k_qs_pivot     median of three per segment, zero its cursors
+//   k_qs_partition per chunk: classify against the pivot, stage the < keys
+//                  and the > keys contiguously in shared memory, reserve one
+//                  range for each with an atomic cursor (< from the segment's
+//                  front, > from its back), and write both as coalesced runs
+//                  to the other buffer: one read and one write per key
+//   k_qs_fill      per chunk: write the pivot over the chunk's share of the
+//                  segment's = range (what the two cursors left in the
+//                  middle) in the caller's array (final positions)
+//   k_qs_next      children -> next level (> tile) or small list (<= tile)
+//   k_qs_small     block sort of each small child into the caller's array
+//   k_qs_chunkmap  chunk -> segment map of the next level
+// The order of the chunks' runs inside a < or > range depends on timing;
+// the sorted output does not.  The host reads three counters back per level
+// to size the next launches.
 #include <algorithm>
 #include <vector>
 
@@ -35,9 +40,10 @@ static int64_t qs_tile(int L) { return (int64_t)QS_BS_NT * (4 * L - 1); }
 
 struct QSeg {
     int64_t begin, end, chunk0;
-    unsigned long long lt, eq;                  // totals from the count pass
-    unsigned long long cur_lt, cur_eq, cur_gt;  // reservation cursors
-    int32_t buf, pivot;                         // buf 0: caller's array, 1: workspace
+    // Reservation cursors of the < range (from begin) and the > range (back
+    // from end); after the partition pass, the segment's < and > counts.
+    unsigned long long n_lt, n_gt;
+    int32_t buf, pivot;  // buf 0: caller's array, 1: workspace
 };
 
 struct QSmall {
@@ -77,8 +83,7 @@ __global__ void k_qs_pivot(QSeg *segs, int64_t nseg, const int32_t *X, const int
     const int64_t len = s.end - s.begin;
     const int32_t a = src[s.begin], b = src[s.begin + (len - 1) / 2], c = src[s.end - 1];
     s.pivot = hs_max(hs_min(a, b), hs_min(hs_max(a, b), c));  // median of three
-    s.lt = s.eq = 0;
-    s.cur_lt = s.cur_eq = s.cur_gt = 0;
+    s.n_lt = s.n_gt = 0;
 }
 
 struct ChunkView {
@@ -97,51 +102,15 @@ HS_DEV ChunkView chunk_view(const QSeg *segs, const int32_t *chunk_seg, int64_t 
     return v;
 }
 
-template <int NT>
-HS_DEV int block_sum(int x, int *red) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[warp] = x;
-    __syncthreads();
-    int tot = 0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < NT / 32; ++w) tot += red[w];
-    return tot;  // valid in thread 0
-}
-
-__global__ void __launch_bounds__(QS_NT)
-    k_qs_count(QSeg *segs, const int32_t *chunk_seg, const int32_t *X, const int32_t *Y) {
-    __shared__ int red[2][QS_NT / 32];
-    const ChunkView cv = chunk_view(segs, chunk_seg, blockIdx.x);
-    const QSeg &sg = segs[cv.s];
-    const int32_t p = sg.pivot;
-    const int32_t *src = qs_src(sg, X, Y) + cv.start;
-    int lt = 0, eq = 0;
-#pragma unroll 8
-    for (int j = 0; j < QS_IPT; ++j) {
-        int i = j * QS_NT + threadIdx.x;
-        if (i < cv.len) {
-            int32_t k = ld_stream(src + i);
-            lt += k < p;
-            eq += k == p;
-        }
-    }
-    int tlt = block_sum<QS_NT>(lt, red[0]);
-    int teq = block_sum<QS_NT>(eq, red[1]);
-    if (threadIdx.x == 0) {
-        if (tlt) atomicAdd(&segs[cv.s].lt, (unsigned long long)tlt);
-        if (teq) atomicAdd(&segs[cv.s].eq, (unsigned long long)teq);
-    }
-}
-
-__global__ void __launch_bounds__(QS_NT)
-    k_qs_scatter(QSeg *segs, const int32_t *chunk_seg, const int32_t *X, const int32_t *Y,
-                 int32_t *Xw, int32_t *Yw) {
+__global__ void __launch_bounds__(QS_NT, 4)
+    k_qs_partition(QSeg *segs, const int32_t *chunk_seg, const int32_t *X, const int32_t *Y,
+                   int32_t *Xw, int32_t *Yw) {
     constexpr int NW = QS_NT / 32;
     constexpr int PER_LANE = QS_IPT * NW / 32;  // (j, warp) entries per lane in the scan
     __shared__ int s_cnt[2][QS_IPT * NW];       // 0: <, 1: >  (index j*NW + warp)
     __shared__ int s_tot[2];
     __shared__ unsigned long long s_base[2];
+    __shared__ int32_t stage[QS_C];  // < keys, then > keys
 
     const ChunkView cv = chunk_view(segs, chunk_seg, blockIdx.x);
     const QSeg &sg = segs[cv.s];
@@ -193,14 +162,12 @@ __global__ void __launch_bounds__(QS_NT)
         if (lane == 31) s_tot[warp] = incl;
     }
     __syncthreads();
+    const int tot_lt = s_tot[0], tot_gt = s_tot[1];
     if (threadIdx.x == 0) {
         QSeg &sw = segs[cv.s];
-        s_base[0] = s_tot[0] ? atomicAdd(&sw.cur_lt, (unsigned long long)s_tot[0]) : 0ull;
-        s_base[1] = s_tot[1] ? atomicAdd(&sw.cur_gt, (unsigned long long)s_tot[1]) : 0ull;
+        s_base[0] = tot_lt ? atomicAdd(&sw.n_lt, (unsigned long long)tot_lt) : 0ull;
+        s_base[1] = tot_gt ? atomicAdd(&sw.n_gt, (unsigned long long)tot_gt) : 0ull;
     }
-    __syncthreads();
-    const int64_t lt_base = sg.begin + (int64_t)s_base[0];
-    const int64_t gt_base = sg.begin + (int64_t)sg.lt + (int64_t)sg.eq + (int64_t)s_base[1];
 #pragma unroll
     for (int j = 0; j < QS_IPT; ++j) {
         bool valid = j * QS_NT + (int)threadIdx.x < cv.len;
@@ -208,9 +175,14 @@ __global__ void __launch_bounds__(QS_NT)
         bool is_gt = valid && k[j] > p;
         unsigned ml = __ballot_sync(0xffffffffu, is_lt);
         unsigned mg = __ballot_sync(0xffffffffu, is_gt);
-        if (is_lt) dst[lt_base + s_cnt[0][j * NW + warp] + __popc(ml & below)] = k[j];
-        if (is_gt) dst[gt_base + s_cnt[1][j * NW + warp] + __popc(mg & below)] = k[j];
+        if (is_lt) stage[s_cnt[0][j * NW + warp] + __popc(ml & below)] = k[j];
+        if (is_gt) stage[tot_lt + s_cnt[1][j * NW + warp] + __popc(mg & below)] = k[j];
     }
+    __syncthreads();
+    int32_t *lt_dst = dst + sg.begin + (int64_t)s_base[0];
+    int32_t *gt_dst = dst + sg.end - (int64_t)s_base[1] - tot_gt;
+    for (int i = threadIdx.x; i < tot_lt; i += QS_NT) st_stream(lt_dst + i, stage[i]);
+    for (int i = threadIdx.x; i < tot_gt; i += QS_NT) st_stream(gt_dst + i, stage[tot_lt + i]);
 }
 
 // The = range of a segment is final: write the pivot over the part of it that
@@ -218,7 +190,7 @@ __global__ void __launch_bounds__(QS_NT)
 __global__ void k_qs_fill(const QSeg *segs, const int32_t *chunk_seg, int32_t *X) {
     const ChunkView cv = chunk_view(segs, chunk_seg, blockIdx.x);
     const QSeg &sg = segs[cv.s];
-    const int64_t e0 = sg.begin + (int64_t)sg.lt, e1 = e0 + (int64_t)sg.eq;
+    const int64_t e0 = sg.begin + (int64_t)sg.n_lt, e1 = sg.end - (int64_t)sg.n_gt;
     const int64_t lo = hs_max(e0, cv.start), hi = hs_min(e1, cv.start + cv.len);
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) X[i] = sg.pivot;
 }
@@ -258,8 +230,8 @@ __global__ void k_qs_next(const QSeg *segs, int64_t nseg, int64_t tile, QSeg *ne
     if (i >= nseg) return;
     const QSeg s = segs[i];
     const int32_t dbuf = s.buf ^ 1;
-    const int64_t lt_end = s.begin + (int64_t)s.lt;
-    const int64_t gt_begin = lt_end + (int64_t)s.eq;
+    const int64_t lt_end = s.begin + (int64_t)s.n_lt;
+    const int64_t gt_begin = s.end - (int64_t)s.n_gt;
     qs_emit(s.begin, lt_end, dbuf, tile, next, cap_seg, small, cap_small, ctr);
     qs_emit(gt_begin, s.end, dbuf, tile, next, cap_seg, small, cap_small, ctr);
 }
@@ -292,9 +264,10 @@ struct QLayout {
 static QLayout qs_layout(size_t n) {
     QLayout q{};
     // Segments of one level are disjoint and longer than the smallest tile
-    // (1024 keys), so a level holds at most n/1024 of them; each contributes
-    // at most one partial chunk; each yields at most two small children.
-    q.cap_seg = (int64_t)(n / 1024 + 2);
+    // (qs_tile(1) = 768 keys, the set without networks), so a level holds at
+    // most n/768 of them; each contributes at most one partial chunk; each
+    // yields at most two small children.
+    q.cap_seg = (int64_t)(n / (size_t)qs_tile(1) + 2);
     q.cap_chunk = (int64_t)(n / QS_C) + q.cap_seg + 2;
     q.cap_small = 2 * q.cap_seg + 2;
     size_t off = 0;
@@ -415,11 +388,8 @@ hs_status quick_sort(int32_t *d_keys, size_t n_, hs_netset s, void *d_ws, size_t
         t = launch_begin(K_QS_PLAN, st);
         k_qs_pivot<<<gseg, 256, 0, st>>>(cur, nseg, X, Y);
         if ((r = launch_end(t)) != HS_OK) return r;
-        t = launch_begin(K_QS_COUNT, st);
-        k_qs_count<<<(unsigned)nchunks, QS_NT, 0, st>>>(cur, ccur, X, Y);
-        if ((r = launch_end(t)) != HS_OK) return r;
-        t = launch_begin(K_QS_SCATTER, st);
-        k_qs_scatter<<<(unsigned)nchunks, QS_NT, 0, st>>>(cur, ccur, X, Y, X, Y);
+        t = launch_begin(K_QS_PARTITION, st);
+        k_qs_partition<<<(unsigned)nchunks, QS_NT, 0, st>>>(cur, ccur, X, Y, X, Y);
         if ((r = launch_end(t)) != HS_OK) return r;
         t = launch_begin(K_QS_FILL, st);
         k_qs_fill<<<(unsigned)nchunks, 256, 0, st>>>(cur, ccur, X);

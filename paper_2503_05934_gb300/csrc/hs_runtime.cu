@@ -13,8 +13,8 @@ namespace hs {
 
 static const char *const kKernelNames[K_COUNT] = {
     "blocksort_keys", "blocksort_pairs", "merge_partition", "merge_keys",
-    "merge_pairs",    "qs_plan",         "qs_count",        "qs_fill",
-    "qs_scatter",     "qs_small",        "seg_classify",    "seg_sort"};
+    "merge_pairs",    "qs_plan",         "qs_fill",
+    "qs_partition",   "qs_small",        "seg_classify",    "seg_sort"};
 
 const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kKernelNames[id] : "?"; }
 
@@ -296,8 +296,8 @@ hs_status hs_set_option(const char *name, int64_t value) {
         return HS_OK;
     }
     if (std::strcmp(name, "blocksort_shape") == 0) {
-        if (value < -1 || value > 4)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_shape must be -1..4");
+        if (value < -1 || value > 5)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_shape must be -1..5");
         merge_set_blocksort_shape((int)value);
         return HS_OK;
     }

@@ -243,7 +243,7 @@ def test_merge_tile_shapes_and_samples(hs, tile, samples):
         hs.hs_set_option("merge_samples", 1)
 
 
-@pytest.mark.parametrize("shape", [-1, 0, 1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [-1, 0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("kernel", [0, 1])
 def test_tuning_options_keep_results(hs, shape, kernel):
     """Block-sort shape and merge-level kernel change speed, not bytes."""
@@ -251,7 +251,7 @@ def test_tuning_options_keep_results(hs, shape, kernel):
     hs.hs_set_option("merge_kernel", kernel)
     try:
         for netset in ["6To8", "3To5", "none", "Odd"]:
-            for n in [1, 7, 8191, 8928, 8929, 16385, 100_003, 1 << 20]:
+            for n in [1, 7, 8191, 8928, 8929, 16385, 17856, 17857, 100_003, 1 << 20]:
                 a = g.random_i32(n, n + 10 * (shape + 1) + kernel)
                 assert np.array_equal(gpu_sort(hs, a, "merge", netset), oracle.merge_sort(a, netset))
     finally:
