@@ -102,15 +102,21 @@ HS_DEV ChunkView chunk_view(const QSeg *segs, const int32_t *chunk_seg, int64_t 
     return v;
 }
 
+// One chunk: each warp classifies its 32*QS_IPT keys (slice j of the chunk
+// holds keys j*QS_NT + [0, QS_NT); warp w takes 32 of them) and compacts them
+// into its own shared region, < keys from the front and > keys from the back,
+// with running offsets that every lane knows from the ballots.  A scan over
+// the warps' totals gives each warp's place in the chunk's < and > runs; one
+// atomic per run reserves the chunk's place in the segment; each warp then
+// copies its keys out as coalesced runs.
 __global__ void __launch_bounds__(QS_NT, 4)
     k_qs_partition(QSeg *segs, const int32_t *chunk_seg, const int32_t *X, const int32_t *Y,
                    int32_t *Xw, int32_t *Yw) {
     constexpr int NW = QS_NT / 32;
-    constexpr int PER_LANE = QS_IPT * NW / 32;  // (j, warp) entries per lane in the scan
-    __shared__ int s_cnt[2][QS_IPT * NW];       // 0: <, 1: >  (index j*NW + warp)
-    __shared__ int s_tot[2];
+    constexpr int WK = 32 * QS_IPT;  // keys per warp
+    __shared__ int32_t stage[QS_C];  // warp w: [w*WK, (w+1)*WK), < from the front, > from the back
+    __shared__ int s_wlt[NW], s_wgt[NW];
     __shared__ unsigned long long s_base[2];
-    __shared__ int32_t stage[QS_C];  // < keys, then > keys
 
     const ChunkView cv = chunk_view(segs, chunk_seg, blockIdx.x);
     const QSeg &sg = segs[cv.s];
@@ -123,66 +129,47 @@ __global__ void __launch_bounds__(QS_NT, 4)
     int32_t k[QS_IPT];
 #pragma unroll
     for (int j = 0; j < QS_IPT; ++j) {
-        int i = j * QS_NT + threadIdx.x;
-        k[j] = i < cv.len ? ld_stream(src + i) : 0;
+        const int i = j * QS_NT + threadIdx.x;
+        k[j] = i < cv.len ? ld_stream(src + i) : p;  // padding counts as "=" and is dropped
     }
+    int32_t *ws = stage + warp * WK;
+    int nlt = 0, ngt = 0;  // warp-uniform running counts
 #pragma unroll
     for (int j = 0; j < QS_IPT; ++j) {
-        bool valid = j * QS_NT + (int)threadIdx.x < cv.len;
-        unsigned ml = __ballot_sync(0xffffffffu, valid && k[j] < p);
-        unsigned mg = __ballot_sync(0xffffffffu, valid && k[j] > p);
-        if (lane == 0) {
-            s_cnt[0][j * NW + warp] = __popc(ml);
-            s_cnt[1][j * NW + warp] = __popc(mg);
-        }
+        const bool is_lt = k[j] < p, is_gt = k[j] > p;
+        const unsigned ml = __ballot_sync(0xffffffffu, is_lt);
+        const unsigned mg = __ballot_sync(0xffffffffu, is_gt);
+        if (is_lt) ws[nlt + __popc(ml & below)] = k[j];
+        if (is_gt) ws[WK - 1 - (ngt + __popc(mg & below))] = k[j];
+        nlt += __popc(ml);
+        ngt += __popc(mg);
+    }
+    if (lane == 0) {
+        s_wlt[warp] = nlt;
+        s_wgt[warp] = ngt;
     }
     __syncthreads();
-    // Exclusive scan of the per-(slice, warp) counts in slice-major order:
-    // warp 0 scans "<", warp 1 scans ">".
-    if (warp < 2) {
-        int *c = s_cnt[warp];
-        int loc[PER_LANE];
-        int sum = 0;
+    // Each warp's offsets inside the chunk's runs, and the chunk totals (every
+    // thread scans the NW warp counts itself).
+    int off_lt = 0, off_gt = 0, tot_lt = 0, tot_gt = 0;
 #pragma unroll
-        for (int e = 0; e < PER_LANE; ++e) {
-            loc[e] = c[lane * PER_LANE + e];
-            sum += loc[e];
-        }
-        int incl = sum;
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        int run = incl - sum;
-#pragma unroll
-        for (int e = 0; e < PER_LANE; ++e) {
-            c[lane * PER_LANE + e] = run;
-            run += loc[e];
-        }
-        if (lane == 31) s_tot[warp] = incl;
+    for (int w = 0; w < NW; ++w) {
+        const int a = s_wlt[w], b = s_wgt[w];
+        off_lt += (w < warp) ? a : 0;
+        off_gt += (w < warp) ? b : 0;
+        tot_lt += a;
+        tot_gt += b;
     }
-    __syncthreads();
-    const int tot_lt = s_tot[0], tot_gt = s_tot[1];
     if (threadIdx.x == 0) {
         QSeg &sw = segs[cv.s];
         s_base[0] = tot_lt ? atomicAdd(&sw.n_lt, (unsigned long long)tot_lt) : 0ull;
         s_base[1] = tot_gt ? atomicAdd(&sw.n_gt, (unsigned long long)tot_gt) : 0ull;
     }
-#pragma unroll
-    for (int j = 0; j < QS_IPT; ++j) {
-        bool valid = j * QS_NT + (int)threadIdx.x < cv.len;
-        bool is_lt = valid && k[j] < p;
-        bool is_gt = valid && k[j] > p;
-        unsigned ml = __ballot_sync(0xffffffffu, is_lt);
-        unsigned mg = __ballot_sync(0xffffffffu, is_gt);
-        if (is_lt) stage[s_cnt[0][j * NW + warp] + __popc(ml & below)] = k[j];
-        if (is_gt) stage[tot_lt + s_cnt[1][j * NW + warp] + __popc(mg & below)] = k[j];
-    }
     __syncthreads();
-    int32_t *lt_dst = dst + sg.begin + (int64_t)s_base[0];
-    int32_t *gt_dst = dst + sg.end - (int64_t)s_base[1] - tot_gt;
-    for (int i = threadIdx.x; i < tot_lt; i += QS_NT) st_stream(lt_dst + i, stage[i]);
-    for (int i = threadIdx.x; i < tot_gt; i += QS_NT) st_stream(gt_dst + i, stage[tot_lt + i]);
+    int32_t *lt_dst = dst + sg.begin + (int64_t)s_base[0] + off_lt;
+    int32_t *gt_dst = dst + sg.end - (int64_t)s_base[1] - tot_gt + off_gt;
+    for (int i = lane; i < nlt; i += 32) st_stream(lt_dst + i, ws[i]);
+    for (int i = lane; i < ngt; i += 32) st_stream(gt_dst + i, ws[WK - 1 - i]);
 }
 
 // The = range of a segment is final: write the pivot over the part of it that
