@@ -451,6 +451,12 @@ def run_extras(hs, torch, dev, stream, args, rank, pristine):
                                  + f", {args.netset} leaves"}
             if algo == "merge" and p_counted:
                 entry["frac_of_measured"] = p_counted * 8 * n_keys / (ms / 1e3) / (peak * 1e9)
+            elif algo == "quick" and tile:
+                # Partition levels of (2 reads + 1 write) per key for a binary
+                # split down to one tile, plus the final block-sort pass.
+                qbytes = 12 * n_keys * (sort_passes(n_keys, tile) - 1) + 8 * n_keys
+                entry["roofline_bytes"] = qbytes
+                entry["frac_of_measured"] = qbytes / (ms / 1e3) / (peak * 1e9)
             out[f"{algo}_2p{args.log2n}_{dist}"] = entry
         del src
     del work, wsm, wsq

@@ -103,7 +103,7 @@ HS_DEV void sort_thread_leaves(K *k, int avail, uint32_t netset) {
 // unpadded.  NT need not be a power of two: the last group of a level may
 // hold a short B run or none (then its keys stay as they are).  On return k
 // holds the thread's EO keys of the sorted tile.
-template <int NT, int EO, int P, class K>
+template <int NT, int EO, int P, bool SKIP, class K>
 HS_DEV void block_merge_levels(K *s, int *wsplit, K (&k)[EO], int cnt) {
     constexpr int T = NT * EO;
     const int my0 = threadIdx.x * EO;
@@ -119,8 +119,13 @@ HS_DEV void block_merge_levels(K *s, int *wsplit, K (&k)[EO], int cnt) {
         // With no B run (a short last group) B points at A, so the unused
         // window slots still read inside the tile.
         const K *A = s + gs, *B = s + (blen > 0 ? gs + w : gs);
+        // A group that starts at or past the live keys holds only sentinels
+        // (merges permute keys within their group), so it is already merged:
+        // with SKIP (for tiles that are often partly empty) it is left alone.
+        const bool live = !SKIP || gs < cnt;
         int lo = diag > blen ? diag - blen : 0;
         int hi = diag < alen ? diag : alen;
+        if (!live) lo = hi;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
@@ -135,10 +140,12 @@ HS_DEV void block_merge_levels(K *s, int *wsplit, K (&k)[EO], int cnt) {
             if ((threadIdx.x & 31) == 31 && !last) end = wsplit[(threadIdx.x >> 5) + 1];
         }
         if (last) end = alen;
-        K o[P];
-        exact_window_merge<EO, P>(A, lo, B, diag - lo, end - lo, EO, o);
+        if (live) {
+            K o[P];
+            exact_window_merge<EO, P>(A, lo, B, diag - lo, end - lo, EO, o);
 #pragma unroll
-        for (int j = 0; j < EO; ++j) k[j] = o[j];
+            for (int j = 0; j < EO; ++j) k[j] = o[j];
+        }
     }
 }
 
@@ -156,8 +163,10 @@ struct BlockSort3 {
 };
 
 // With samp, also writes the tile's samples (every kSampleStride-th key,
-// samp[(base + q) / S] for q % S == 0; base % S == 0).
-template <int NT, int L, int LEAVES = 2>
+// samp[(base + q) / S] for q % S == 0; base % S == 0).  SKIP: threads past
+// the live keys skip their leaves and merges (for tiles that are often partly
+// empty, such as small segments).
+template <int NT, int L, int LEAVES = 2, bool SKIP = false>
 HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_t netset,
                              bool vec, int32_t *s, int32_t *samp = nullptr, int64_t base = 0) {
     using C = BlockSort3<NT, L, LEAVES>;
@@ -178,8 +187,8 @@ HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_
     int32_t k[EO];
 #pragma unroll
     for (int j = 0; j < EO; ++j) k[j] = s[my0 + j];
-    sort_thread_leaves<L, LEAVES, P>(k, cnt - my0, netset);
-    block_merge_levels<NT, EO, P>(s, wsplit, k, cnt);
+    if (!SKIP || my0 < cnt) sort_thread_leaves<L, LEAVES, P>(k, cnt - my0, netset);
+    block_merge_levels<NT, EO, P, SKIP>(s, wsplit, k, cnt);
 
     __syncthreads();
 #pragma unroll
@@ -262,7 +271,7 @@ HS_DEV void block_sort_pairs_tile(const int32_t *kin, int32_t *kout, const int32
     for (int j = 0; j < EO; ++j)
         k[j] = (my0 + j < cnt) ? pack_word(s32[my0 + j], (uint32_t)(my0 + j)) : word_max<int64_t>();
     sort_thread_leaves<L, LEAVES, P>(k, cnt - my0, netset);
-    block_merge_levels<NT, EO, P>(sw, wsplit, k, cnt);
+    block_merge_levels<NT, EO, P, false>(sw, wsplit, k, cnt);
 
     // Output keys to s32[0, T), values (gathered by position) to s32[T, 2T).
     __syncthreads();

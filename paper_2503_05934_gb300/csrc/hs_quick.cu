@@ -237,8 +237,8 @@ __global__ void __launch_bounds__(QS_BS_NT)
     extern __shared__ __align__(16) int32_t smem[];
     const QSmall s = small[blockIdx.x];
     const int32_t *src = s.buf ? Y : X;
-    block_sort_tile3<QS_BS_NT, L, 4>(src + s.begin, Xw + s.begin, (int)(s.end - s.begin), netset,
-                                     false, smem);
+    block_sort_tile3<QS_BS_NT, L, 4, true>(src + s.begin, Xw + s.begin, (int)(s.end - s.begin),
+                                           netset, false, smem);
 }
 
 // ---------------------------------------------------------------- host side

@@ -128,7 +128,7 @@ HS_DEV void sort_segment(const SegDesc &d, uint32_t netset, int32_t *s, int64_t 
     const int64_t n = d.n;
     if (n <= 1) return;
     if (n <= T) {
-        block_sort_tile3<NT, L, LV>(d.keys, d.keys, (int)n, netset, aligned16(d.keys), s);
+        block_sort_tile3<NT, L, LV, true>(d.keys, d.keys, (int)n, netset, aligned16(d.keys), s);
         return;
     }
     int levels = 0;
