@@ -267,6 +267,10 @@ HS_API uint64_t hs_launch_count(void);
  * launches and summed milliseconds of the kernel named `kernel` since the
  * last reset; unknown names give 0 launches. */
 HS_API void hs_prof_enable(int on);
+/* Restricts the timing to launches of the kernel named `kernel` (the names
+ * hs_prof_read accepts), so that the other launches carry no extra events;
+ * NULL times every kernel again.  Unknown names return HS_ERR_INVALID_ARG. */
+HS_API hs_status hs_prof_select(const char *kernel);
 HS_API void hs_prof_reset(void);
 HS_API hs_status hs_prof_read(const char *kernel, uint64_t *launches, double *total_ms);
 

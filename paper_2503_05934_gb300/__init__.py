@@ -26,7 +26,7 @@ __all__ = [
     "NETSETS", "ALGOS", "HsortError", "lib", "netset_mask", "algo_id",
     "hs_sort_workspace_bytes", "hs_sort_i32", "hs_sort_pairs_i32",
     "hs_sort_host_workspace_bytes", "hs_sort_i32_host", "hs_launch_count",
-    "hs_prof_enable", "hs_prof_reset", "hs_prof_read", "hs_version", "hs_set_option",
+    "hs_prof_enable", "hs_prof_select", "hs_prof_reset", "hs_prof_read", "hs_version", "hs_set_option",
     "hs_sort_i32_noalloc", "NOALLOC_MAX_KEYS", "hs_device_check", "Plan", "make_plan",
     "hs_segsort_workspace_bytes", "hs_segsort_i32", "hs_sort_i32_many", "Graph",
     "hs_segsort_capture", "hs_segsort_autotune", "hs_tune_cache_save", "hs_tune_cache_load",
@@ -286,6 +286,11 @@ def hs_launch_count() -> int:
 
 def hs_prof_enable(on: bool = True) -> None:
     lib().hs_prof_enable(1 if on else 0)
+
+
+def hs_prof_select(kernel: str | None) -> None:
+    """Time only launches of `kernel` (None: every kernel)."""
+    check(lib().hs_prof_select(kernel.encode() if kernel else None))
 
 
 def hs_prof_reset() -> None:

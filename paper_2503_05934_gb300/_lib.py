@@ -54,6 +54,7 @@ SIGNATURES = {
     "hs_version": (ctypes.c_char_p, []),
     "hs_launch_count": (ctypes.c_uint64, []),
     "hs_prof_enable": (None, [_int]),
+    "hs_prof_select": (_int, [ctypes.c_char_p]),
     "hs_prof_reset": (None, []),
     "hs_prof_read": (_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64),
                             ctypes.POINTER(ctypes.c_double)]),

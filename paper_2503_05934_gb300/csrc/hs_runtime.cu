@@ -36,6 +36,7 @@ void clear_error() { t_last_error.clear(); }
 // ------------------------------------------------------------ launch stats
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<int> g_prof_on{0};
+static std::atomic<int> g_prof_only{-1};  // kernel id timed alone, or -1 for all
 
 struct ProfSlot {
     int id;
@@ -49,7 +50,8 @@ static double g_prof_ms[K_COUNT];
 
 LaunchToken launch_begin(int id, cudaStream_t stream) {
     LaunchToken t{id, stream, nullptr, nullptr};
-    if (g_prof_on.load(std::memory_order_relaxed)) {
+    const int only = g_prof_only.load(std::memory_order_relaxed);
+    if (g_prof_on.load(std::memory_order_relaxed) && (only < 0 || only == id)) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
         if (!g_event_pool.empty()) {
@@ -180,6 +182,20 @@ const char *hs_version(void) { return "hsort 0.1 (sm_103a)"; }
 uint64_t hs_launch_count(void) { return g_launches.load(); }
 
 void hs_prof_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+hs_status hs_prof_select(const char *kernel) {
+    clear_error();
+    if (!kernel) {
+        g_prof_only.store(-1);
+        return HS_OK;
+    }
+    for (int i = 0; i < K_COUNT; ++i)
+        if (std::strcmp(kernel, kKernelNames[i]) == 0) {
+            g_prof_only.store(i);
+            return HS_OK;
+        }
+    return fail(HS_ERR_INVALID_ARG, std::string("hs_prof_select: unknown kernel ") + kernel);
+}
 
 void hs_prof_reset(void) {
     std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -278,6 +278,24 @@ def test_profiling_counters(hs):
     assert n_bs == 1 and n_mk == levels and ms_bs > 0 and ms_mk > 0
 
 
+def test_profiling_one_kernel(hs):
+    """hs_prof_select restricts the event timing to one kernel."""
+    import torch
+    hs.hs_prof_reset()
+    hs.hs_prof_select("merge_keys")
+    hs.hs_prof_enable(True)
+    try:
+        t = to_dev(g.random_i32(1 << 18, 2))
+        hs.hs_sort_i32(t, "merge", "6To8")
+        torch.cuda.synchronize()
+        n_bs, _ = hs.hs_prof_read("blocksort_keys")
+        n_mk, ms_mk = hs.hs_prof_read("merge_keys")
+    finally:
+        hs.hs_prof_enable(False)
+        hs.hs_prof_select(None)
+    assert n_bs == 0 and n_mk > 0 and ms_mk > 0
+
+
 def test_full_size_keys_2p28(hs):
     """2^28 uniform int32 keys, {6,7,8}: the benchmark's workload and launch
     configuration, checked by sortedness, multiset fingerprint and sampled

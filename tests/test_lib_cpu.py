@@ -116,3 +116,10 @@ def test_workspace_sizes(hs):
         assert ws >= 4 * n
         assert hs.hs_sort_workspace_bytes(n, 1, 0) >= 8 * n
         assert hs.hs_sort_host_workspace_bytes(n, 0) >= ws + 4 * n
+
+
+def test_prof_select_names(hs):
+    assert hs.hs_prof_select(b"merge_keys") == 0
+    assert hs.hs_prof_select(None) == 0
+    assert hs.hs_prof_select(b"no_such_kernel") == 1
+    assert b"unknown kernel" in hs.hs_last_error()
