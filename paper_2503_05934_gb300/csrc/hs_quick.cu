@@ -9,21 +9,23 @@
 // by the block sort, whose leaves are the network base cases.
 //
 // Per level (all segments at once, chunks of QS_C keys):
-//   k_qs_pivot     median of three per segment, zero its cursors
-//   k_qs_partition per chunk: classify against the pivot, stage the < keys
-//                  and the > keys contiguously in shared memory, reserve one
+//   k_qs_partition per chunk: classify against the pivot, compact the < keys
+//                  and the > keys per warp in shared memory, reserve one
 //                  range for each with an atomic cursor (< from the segment's
 //                  front, > from its back), and write both as coalesced runs
 //                  to the other buffer: one read and one write per key
-//   k_qs_fill      per chunk: write the pivot over the chunk's share of the
-//                  segment's = range (what the two cursors left in the
-//                  middle) in the caller's array (final positions)
-//   k_qs_next      children -> next level (> tile) or small list (<= tile)
+//   k_qs_next      per segment: the = range (what the two cursors left in the
+//                  middle) is final; short ones are written here, long ones
+//                  listed; children go to the next level (> tile, with their
+//                  median-of-three pivots) or to the small list (<= tile)
+//   k_qs_fill      the listed = ranges, in the caller's array
 //   k_qs_small     block sort of each small child into the caller's array
 //   k_qs_chunkmap  chunk -> segment map of the next level
-// The order of the chunks' runs inside a < or > range depends on timing;
-// the sorted output does not.  The host reads three counters back per level
-// to size the next launches.
+// The host reads the level's counters back once, after k_qs_next, to size
+// the remaining launches exactly (one CTA per chunk, per small child, per
+// listed range, per next-level segment); the kernels also read their counts
+// on the device and skip work past them.  The order of the chunks' runs
+// inside a < or > range depends on timing; the sorted output does not.
 #include <algorithm>
 #include <vector>
 
@@ -35,7 +37,8 @@ namespace hs {
 constexpr int QS_NT = 256;
 constexpr int QS_IPT = 32;
 constexpr int QS_C = QS_NT * QS_IPT;  // keys per partition chunk
-constexpr int QS_BS_NT = 256;  // small-segment sort: 256 threads x four leaves
+constexpr int QS_BS_NT = 256;         // small-segment sort: 256 threads x four leaves
+constexpr int QS_EQ_INLINE = 64;      // = ranges up to this length are written by k_qs_next
 static int64_t qs_tile(int L) { return (int64_t)QS_BS_NT * (4 * L - 1); }
 
 struct QSeg {
@@ -51,147 +54,143 @@ struct QSmall {
     int32_t buf, pad;
 };
 
+struct QFill {
+    int64_t begin, end;
+    int32_t value, pad;
+};
+
+// Level k uses counter slot k % 2: nseg and nchunks describe its segment list
+// (written by level k - 1); nsmall and nfill count the small children and
+// long = ranges that level k itself lists and consumes.
 struct QCounters {
-    unsigned long long nseg, nchunks, nsmall, overflow;
+    unsigned long long nseg, nchunks, nsmall, nfill;
+};
+
+struct QCaps {
+    int64_t seg, chunk, small, fill;
 };
 
 static int64_t qs_option_max_levels = -1;  // < 0: automatic
 
-HS_DEV const int32_t *qs_src(const QSeg &s, const int32_t *X, const int32_t *Y) {
-    return s.buf ? Y : X;
+HS_DEV const int32_t *qs_src(int32_t buf, const int32_t *X, const int32_t *Y) { return buf ? Y : X; }
+
+HS_DEV int32_t median_of_three(const int32_t *a, int64_t b, int64_t e) {
+    const int32_t x = a[b], y = a[b + (e - b - 1) / 2], z = a[e - 1];
+    return hs_max(hs_min(x, y), hs_min(hs_max(x, y), z));
 }
 
-__global__ void k_qs_init(QSeg *segs, int32_t *chunk_seg, int64_t n, int64_t nchunks) {
+HS_DEV int64_t clamp_count(unsigned long long c, int64_t cap) {
+    return (int64_t)c < cap ? (int64_t)c : cap;
+}
+
+__global__ void k_qs_init(QSeg *segs, int32_t *chunk_seg, int64_t n, int64_t nchunks,
+                          const int32_t *X, QCounters *ctr, unsigned long long *status) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         QSeg s{};
         s.begin = 0;
         s.end = n;
         s.chunk0 = 0;
         s.buf = 0;
+        s.pivot = median_of_three(X, 0, n);
         segs[0] = s;
+        ctr[0] = QCounters{1ull, (unsigned long long)nchunks, 0ull, 0ull};
+        ctr[1] = QCounters{0ull, 0ull, 0ull, 0ull};
+        *status = 0ull;
     }
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
          c += (int64_t)gridDim.x * blockDim.x)
         chunk_seg[c] = 0;
 }
 
-__global__ void k_qs_pivot(QSeg *segs, int64_t nseg, const int32_t *X, const int32_t *Y) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nseg) return;
-    QSeg &s = segs[i];
-    const int32_t *src = qs_src(s, X, Y);
-    const int64_t len = s.end - s.begin;
-    const int32_t a = src[s.begin], b = src[s.begin + (len - 1) / 2], c = src[s.end - 1];
-    s.pivot = hs_max(hs_min(a, b), hs_min(hs_max(a, b), c));  // median of three
-    s.n_lt = s.n_gt = 0;
-}
-
-struct ChunkView {
-    int64_t start;
-    int len;
-    int s;
-};
-
-HS_DEV ChunkView chunk_view(const QSeg *segs, const int32_t *chunk_seg, int64_t c) {
-    ChunkView v;
-    v.s = chunk_seg[c];
-    const QSeg &sg = segs[v.s];
-    v.start = sg.begin + (c - sg.chunk0) * (int64_t)QS_C;
-    int64_t rest = sg.end - v.start;
-    v.len = (int)(rest < QS_C ? rest : QS_C);
-    return v;
-}
-
-// One chunk: each warp classifies its 32*QS_IPT keys (slice j of the chunk
-// holds keys j*QS_NT + [0, QS_NT); warp w takes 32 of them) and compacts them
-// into its own shared region, < keys from the front and > keys from the back,
-// with running offsets that every lane knows from the ballots.  A scan over
-// the warps' totals gives each warp's place in the chunk's < and > runs; one
-// atomic per run reserves the chunk's place in the segment; each warp then
-// copies its keys out as coalesced runs.
+// One chunk per CTA: each warp classifies its 32*QS_IPT keys (slice j of the
+// chunk holds keys j*QS_NT + [0, QS_NT); warp w takes 32 of them) and
+// compacts them into its own shared region, < keys from the front and > keys
+// from the back, with running offsets that every lane knows from the ballots.
+// A scan over the warps' totals gives each warp's place in the chunk's < and
+// > runs; one atomic per run reserves the chunk's place in the segment; each
+// warp then copies its keys out as coalesced runs.
 __global__ void __launch_bounds__(QS_NT, 4)
-    k_qs_partition(QSeg *segs, const int32_t *chunk_seg, const int32_t *X, const int32_t *Y,
-                   int32_t *Xw, int32_t *Yw) {
+    k_qs_partition(QSeg *segs, const int32_t *chunk_seg, const QCounters *ctr, QCaps caps,
+                   const int32_t *X, const int32_t *Y, int32_t *Xw, int32_t *Yw) {
     constexpr int NW = QS_NT / 32;
     constexpr int WK = 32 * QS_IPT;  // keys per warp
     __shared__ int32_t stage[QS_C];  // warp w: [w*WK, (w+1)*WK), < from the front, > from the back
     __shared__ int s_wlt[NW], s_wgt[NW];
     __shared__ unsigned long long s_base[2];
-
-    const ChunkView cv = chunk_view(segs, chunk_seg, blockIdx.x);
-    const QSeg &sg = segs[cv.s];
-    const int32_t p = sg.pivot;
-    const int32_t *src = qs_src(sg, X, Y) + cv.start;
-    int32_t *dst = sg.buf ? Xw : Yw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
+    const int64_t c = blockIdx.x;
+    if (c >= clamp_count(ctr->nchunks, caps.chunk)) return;
+    {
+        const int si = chunk_seg[c];
+        const QSeg &sg = segs[si];
+        const int64_t start = sg.begin + (c - sg.chunk0) * (int64_t)QS_C;
+        const int64_t rest = sg.end - start;
+        const int len = (int)(rest < QS_C ? rest : QS_C);
+        const int32_t p = sg.pivot;
+        const int32_t *src = qs_src(sg.buf, X, Y) + start;
+        int32_t *dst = sg.buf ? Xw : Yw;
 
-    int32_t k[QS_IPT];
+        int32_t k[QS_IPT];
 #pragma unroll
-    for (int j = 0; j < QS_IPT; ++j) {
-        const int i = j * QS_NT + threadIdx.x;
-        k[j] = i < cv.len ? ld_stream(src + i) : p;  // padding counts as "=" and is dropped
-    }
-    int32_t *ws = stage + warp * WK;
-    int nlt = 0, ngt = 0;  // warp-uniform running counts
+        for (int j = 0; j < QS_IPT; ++j) {
+            const int i = j * QS_NT + threadIdx.x;
+            k[j] = i < len ? ld_stream(src + i) : p;  // padding counts as "=" and is dropped
+        }
+        int32_t *ws = stage + warp * WK;
+        int nlt = 0, ngt = 0;  // warp-uniform running counts
 #pragma unroll
-    for (int j = 0; j < QS_IPT; ++j) {
-        const bool is_lt = k[j] < p, is_gt = k[j] > p;
-        const unsigned ml = __ballot_sync(0xffffffffu, is_lt);
-        const unsigned mg = __ballot_sync(0xffffffffu, is_gt);
-        if (is_lt) ws[nlt + __popc(ml & below)] = k[j];
-        if (is_gt) ws[WK - 1 - (ngt + __popc(mg & below))] = k[j];
-        nlt += __popc(ml);
-        ngt += __popc(mg);
-    }
-    if (lane == 0) {
-        s_wlt[warp] = nlt;
-        s_wgt[warp] = ngt;
-    }
-    __syncthreads();
-    // Each warp's offsets inside the chunk's runs, and the chunk totals (every
-    // thread scans the NW warp counts itself).
-    int off_lt = 0, off_gt = 0, tot_lt = 0, tot_gt = 0;
+        for (int j = 0; j < QS_IPT; ++j) {
+            const bool is_lt = k[j] < p, is_gt = k[j] > p;
+            const unsigned ml = __ballot_sync(0xffffffffu, is_lt);
+            const unsigned mg = __ballot_sync(0xffffffffu, is_gt);
+            if (is_lt) ws[nlt + __popc(ml & below)] = k[j];
+            if (is_gt) ws[WK - 1 - (ngt + __popc(mg & below))] = k[j];
+            nlt += __popc(ml);
+            ngt += __popc(mg);
+        }
+        if (lane == 0) {
+            s_wlt[warp] = nlt;
+            s_wgt[warp] = ngt;
+        }
+        __syncthreads();
+        // Each warp's offsets inside the chunk's runs, and the chunk totals
+        // (every thread scans the NW warp counts itself).
+        int off_lt = 0, off_gt = 0, tot_lt = 0, tot_gt = 0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        const int a = s_wlt[w], b = s_wgt[w];
-        off_lt += (w < warp) ? a : 0;
-        off_gt += (w < warp) ? b : 0;
-        tot_lt += a;
-        tot_gt += b;
+        for (int w = 0; w < NW; ++w) {
+            const int a = s_wlt[w], b = s_wgt[w];
+            off_lt += (w < warp) ? a : 0;
+            off_gt += (w < warp) ? b : 0;
+            tot_lt += a;
+            tot_gt += b;
+        }
+        if (threadIdx.x == 0) {
+            QSeg &sw = segs[si];
+            s_base[0] = tot_lt ? atomicAdd(&sw.n_lt, (unsigned long long)tot_lt) : 0ull;
+            s_base[1] = tot_gt ? atomicAdd(&sw.n_gt, (unsigned long long)tot_gt) : 0ull;
+        }
+        __syncthreads();
+        int32_t *lt_dst = dst + sg.begin + (int64_t)s_base[0] + off_lt;
+        int32_t *gt_dst = dst + sg.end - (int64_t)s_base[1] - tot_gt + off_gt;
+        for (int i = lane; i < nlt; i += 32) st_stream(lt_dst + i, ws[i]);
+        for (int i = lane; i < ngt; i += 32) st_stream(gt_dst + i, ws[WK - 1 - i]);
     }
-    if (threadIdx.x == 0) {
-        QSeg &sw = segs[cv.s];
-        s_base[0] = tot_lt ? atomicAdd(&sw.n_lt, (unsigned long long)tot_lt) : 0ull;
-        s_base[1] = tot_gt ? atomicAdd(&sw.n_gt, (unsigned long long)tot_gt) : 0ull;
-    }
-    __syncthreads();
-    int32_t *lt_dst = dst + sg.begin + (int64_t)s_base[0] + off_lt;
-    int32_t *gt_dst = dst + sg.end - (int64_t)s_base[1] - tot_gt + off_gt;
-    for (int i = lane; i < nlt; i += 32) st_stream(lt_dst + i, ws[i]);
-    for (int i = lane; i < ngt; i += 32) st_stream(gt_dst + i, ws[WK - 1 - i]);
 }
 
-// The = range of a segment is final: write the pivot over the part of it that
-// falls inside this chunk's index range.
-__global__ void k_qs_fill(const QSeg *segs, const int32_t *chunk_seg, int32_t *X) {
-    const ChunkView cv = chunk_view(segs, chunk_seg, blockIdx.x);
-    const QSeg &sg = segs[cv.s];
-    const int64_t e0 = sg.begin + (int64_t)sg.n_lt, e1 = sg.end - (int64_t)sg.n_gt;
-    const int64_t lo = hs_max(e0, cv.start), hi = hs_min(e1, cv.start + cv.len);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) X[i] = sg.pivot;
-}
+HS_DEV void qs_flag(unsigned long long *status) { atomicExch(status, 1ull); }
 
-HS_DEV void qs_emit(int64_t b, int64_t e, int32_t buf, int64_t tile, QSeg *next, int64_t cap_seg,
-                    QSmall *small, int64_t cap_small, QCounters *ctr) {
+HS_DEV void qs_emit(int64_t b, int64_t e, int32_t buf, int64_t tile, const int32_t *X,
+                    const int32_t *Y, QSeg *next, QCounters *nctr, QSmall *small,
+                    QCounters *cctr, const QCaps &caps, unsigned long long *status) {
     const int64_t len = e - b;
     if (len <= 0) return;
     if (len > tile) {
-        unsigned long long idx = atomicAdd(&ctr->nseg, 1ull);
+        unsigned long long idx = atomicAdd(&nctr->nseg, 1ull);
         unsigned long long nch = (unsigned long long)((len + QS_C - 1) / QS_C);
-        unsigned long long c0 = atomicAdd(&ctr->nchunks, nch);
-        if ((int64_t)idx >= cap_seg) {
-            atomicExch(&ctr->overflow, 1ull);
+        unsigned long long c0 = atomicAdd(&nctr->nchunks, nch);
+        if ((int64_t)idx >= caps.seg || (int64_t)(c0 + nch) > caps.chunk) {
+            qs_flag(status);
             return;
         }
         QSeg s{};
@@ -199,80 +198,108 @@ HS_DEV void qs_emit(int64_t b, int64_t e, int32_t buf, int64_t tile, QSeg *next,
         s.end = e;
         s.chunk0 = (int64_t)c0;
         s.buf = buf;
+        s.pivot = median_of_three(qs_src(buf, X, Y), b, e);
         next[idx] = s;
     } else {
-        unsigned long long idx = atomicAdd(&ctr->nsmall, 1ull);
-        if ((int64_t)idx >= cap_small) {
-            atomicExch(&ctr->overflow, 1ull);
+        unsigned long long idx = atomicAdd(&cctr->nsmall, 1ull);
+        if ((int64_t)idx >= caps.small) {
+            qs_flag(status);
             return;
         }
-        QSmall s{b, e, buf, 0};
-        small[idx] = s;
+        small[idx] = QSmall{b, e, buf, 0};
     }
 }
 
-__global__ void k_qs_next(const QSeg *segs, int64_t nseg, int64_t tile, QSeg *next,
-                          int64_t cap_seg, QSmall *small, int64_t cap_small, QCounters *ctr) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nseg) return;
-    const QSeg s = segs[i];
-    const int32_t dbuf = s.buf ^ 1;
-    const int64_t lt_end = s.begin + (int64_t)s.n_lt;
-    const int64_t gt_begin = s.end - (int64_t)s.n_gt;
-    qs_emit(s.begin, lt_end, dbuf, tile, next, cap_seg, small, cap_small, ctr);
-    qs_emit(gt_begin, s.end, dbuf, tile, next, cap_seg, small, cap_small, ctr);
+__global__ void k_qs_next(const QSeg *segs, QCounters *cctr, QCounters *nctr, QCaps caps,
+                          int64_t tile, QSeg *next, QSmall *small, QFill *fill, int32_t *X,
+                          const int32_t *Y, unsigned long long *status) {
+    const int64_t nseg = clamp_count(cctr->nseg, caps.seg);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nseg;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const QSeg s = segs[i];
+        const int32_t dbuf = s.buf ^ 1;
+        const int64_t lt_end = s.begin + (int64_t)s.n_lt;
+        const int64_t gt_begin = s.end - (int64_t)s.n_gt;
+        // The = range is final: write the pivot into the caller's array.
+        if (gt_begin - lt_end <= QS_EQ_INLINE) {
+            for (int64_t x = lt_end; x < gt_begin; ++x) X[x] = s.pivot;
+        } else {
+            unsigned long long idx = atomicAdd(&cctr->nfill, 1ull);
+            if ((int64_t)idx < caps.fill) fill[idx] = QFill{lt_end, gt_begin, s.pivot, 0};
+            else qs_flag(status);
+        }
+        qs_emit(s.begin, lt_end, dbuf, tile, X, Y, next, nctr, small, cctr, caps, status);
+        qs_emit(gt_begin, s.end, dbuf, tile, X, Y, next, nctr, small, cctr, caps, status);
+    }
 }
 
-__global__ void k_qs_chunkmap(const QSeg *segs, int32_t *chunk_seg, int64_t cap_chunk) {
-    const QSeg &s = segs[blockIdx.x];
-    const int64_t nch = (s.end - s.begin + QS_C - 1) / QS_C;
-    for (int64_t c = threadIdx.x; c < nch; c += blockDim.x)
-        if (s.chunk0 + c < cap_chunk) chunk_seg[s.chunk0 + c] = (int32_t)blockIdx.x;
+__global__ void k_qs_fill(const QFill *fill, const QCounters *cctr, QCaps caps, int32_t *X) {
+    const int64_t nfill = clamp_count(cctr->nfill, caps.fill);
+    for (int64_t f = blockIdx.x; f < nfill; f += gridDim.x) {
+        const QFill q = fill[f];
+        for (int64_t i = q.begin + threadIdx.x; i < q.end; i += blockDim.x) X[i] = q.value;
+    }
+}
+
+__global__ void k_qs_chunkmap(const QSeg *segs, const QCounters *nctr, QCaps caps,
+                              int32_t *chunk_seg) {
+    const int64_t nseg = clamp_count(nctr->nseg, caps.seg);
+    for (int64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const QSeg &g = segs[s];
+        const int64_t nch = (g.end - g.begin + QS_C - 1) / QS_C;
+        for (int64_t c = threadIdx.x; c < nch; c += blockDim.x)
+            if (g.chunk0 + c < caps.chunk) chunk_seg[g.chunk0 + c] = (int32_t)s;
+    }
 }
 
 template <int L>
 __global__ void __launch_bounds__(QS_BS_NT)
-    k_qs_small(const QSmall *small, const int32_t *X, const int32_t *Y, int32_t *Xw,
-               uint32_t netset) {
+    k_qs_small(const QSmall *small, const QCounters *cctr, QCaps caps, const int32_t *X,
+               const int32_t *Y, int32_t *Xw, uint32_t netset) {
     extern __shared__ __align__(16) int32_t smem[];
+    if ((int64_t)blockIdx.x >= clamp_count(cctr->nsmall, caps.small)) return;
     const QSmall s = small[blockIdx.x];
-    const int32_t *src = s.buf ? Y : X;
-    block_sort_tile3<QS_BS_NT, L, 4, true>(src + s.begin, Xw + s.begin, (int)(s.end - s.begin),
-                                           netset, false, smem);
+    block_sort_tile3<QS_BS_NT, L, 4, true>(qs_src(s.buf, X, Y) + s.begin, Xw + s.begin,
+                                           (int)(s.end - s.begin), netset, false, smem);
 }
 
 // ---------------------------------------------------------------- host side
 
 struct QLayout {
-    size_t y, part, seg_a, seg_b, chunk_a, chunk_b, small, ctr, total;
-    int64_t cap_seg, cap_chunk, cap_small;
+    size_t y, part, seg_a, seg_b, chunk_a, chunk_b, small, fill, ctr, status, total;
+    QCaps caps;
 };
 
 static QLayout qs_layout(size_t n) {
     QLayout q{};
     // Segments of one level are disjoint and longer than the smallest tile
     // (qs_tile(1) = 768 keys, the set without networks), so a level holds at
-    // most n/768 of them; each contributes at most one partial chunk; each
-    // yields at most two small children.
-    q.cap_seg = (int64_t)(n / (size_t)qs_tile(1) + 2);
-    q.cap_chunk = (int64_t)(n / QS_C) + q.cap_seg + 2;
-    q.cap_small = 2 * q.cap_seg + 2;
+    // most n/768 of them; each contributes at most one partial chunk, yields
+    // at most two small children and at most one listed = range.
+    q.caps.seg = (int64_t)(n / (size_t)qs_tile(1) + 2);
+    q.caps.chunk = (int64_t)(n / QS_C) + q.caps.seg + 2;
+    q.caps.small = 2 * q.caps.seg + 2;
+    q.caps.fill = q.caps.seg;
     size_t off = 0;
     q.y = off;
     off += align_up(n * sizeof(int32_t), 256);
-    q.part = off;  // merge partitions for the depth fallback (contiguous after y)
+    q.part = off;  // merge workspace tail for the depth fallback (contiguous after y)
     off += align_up(merge_workspace_bytes(n, 0) - align_up(n * sizeof(int32_t), 256), 256);
     q.seg_a = off;
-    off += align_up((size_t)q.cap_seg * sizeof(QSeg), 256);
+    off += align_up((size_t)q.caps.seg * sizeof(QSeg), 256);
     q.seg_b = off;
-    off += align_up((size_t)q.cap_seg * sizeof(QSeg), 256);
+    off += align_up((size_t)q.caps.seg * sizeof(QSeg), 256);
     q.chunk_a = off;
-    off += align_up((size_t)q.cap_chunk * sizeof(int32_t), 256);
+    off += align_up((size_t)q.caps.chunk * sizeof(int32_t), 256);
     q.chunk_b = off;
-    off += align_up((size_t)q.cap_chunk * sizeof(int32_t), 256);
+    off += align_up((size_t)q.caps.chunk * sizeof(int32_t), 256);
     q.small = off;
-    off += align_up((size_t)q.cap_small * sizeof(QSmall), 256);
+    off += align_up((size_t)q.caps.small * sizeof(QSmall), 256);
+    q.fill = off;
+    off += align_up((size_t)q.caps.fill * sizeof(QFill), 256);
     q.ctr = off;
+    off += align_up(2 * sizeof(QCounters), 256);
+    q.status = off;
     off += 256;
     q.total = off;
     return q;
@@ -283,27 +310,29 @@ size_t quick_workspace_bytes(size_t n) { return qs_layout(n).total; }
 void quick_set_max_levels(int64_t v) { qs_option_max_levels = v; }
 
 template <int L>
-static hs_status launch_small_t(const QSmall *small, int64_t nsmall, const int32_t *X,
-                                const int32_t *Y, int32_t *Xw, hs_netset s, cudaStream_t st) {
+static hs_status launch_small_t(int64_t nsmall, const QSmall *small, const QCounters *cctr,
+                                const QCaps &caps, const int32_t *X, const int32_t *Y, int32_t *Xw,
+                                hs_netset s, cudaStream_t st) {
     const int smem = BlockSort3<QS_BS_NT, L, 4>::SMEM_BYTES;
     auto kern = k_qs_small<L>;
     hs_status r = ensure_smem((const void *)kern, smem);
     if (r != HS_OK) return r;
     LaunchToken t = launch_begin(K_QS_SMALL, st);
-    kern<<<(unsigned)nsmall, QS_BS_NT, smem, st>>>(small, X, Y, Xw, s);
+    kern<<<(unsigned)nsmall, QS_BS_NT, smem, st>>>(small, cctr, caps, X, Y, Xw, s);
     return launch_end(t);
 }
 
-static hs_status launch_small(int L, const QSmall *small, int64_t nsmall, const int32_t *X,
-                              const int32_t *Y, int32_t *Xw, hs_netset s, cudaStream_t st) {
+static hs_status launch_small(int L, int64_t nsmall, const QSmall *small, const QCounters *cctr,
+                              const QCaps &caps, const int32_t *X, const int32_t *Y, int32_t *Xw,
+                              hs_netset s, cudaStream_t st) {
     switch (L) {
-        case 1: return launch_small_t<1>(small, nsmall, X, Y, Xw, s, st);
-        case 3: return launch_small_t<3>(small, nsmall, X, Y, Xw, s, st);
-        case 4: return launch_small_t<4>(small, nsmall, X, Y, Xw, s, st);
-        case 5: return launch_small_t<5>(small, nsmall, X, Y, Xw, s, st);
-        case 6: return launch_small_t<6>(small, nsmall, X, Y, Xw, s, st);
-        case 7: return launch_small_t<7>(small, nsmall, X, Y, Xw, s, st);
-        case 8: return launch_small_t<8>(small, nsmall, X, Y, Xw, s, st);
+        case 1: return launch_small_t<1>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
+        case 3: return launch_small_t<3>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
+        case 4: return launch_small_t<4>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
+        case 5: return launch_small_t<5>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
+        case 6: return launch_small_t<6>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
+        case 7: return launch_small_t<7>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
+        case 8: return launch_small_t<8>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
     }
     return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
 }
@@ -352,55 +381,59 @@ hs_status quick_sort(int32_t *d_keys, size_t n_, hs_netset s, void *d_ws, size_t
     int32_t *ccur = reinterpret_cast<int32_t *>(base + q.chunk_a);
     int32_t *cnxt = reinterpret_cast<int32_t *>(base + q.chunk_b);
     QSmall *small = reinterpret_cast<QSmall *>(base + q.small);
+    QFill *fill = reinterpret_cast<QFill *>(base + q.fill);
     QCounters *ctr = reinterpret_cast<QCounters *>(base + q.ctr);
+    unsigned long long *status = reinterpret_cast<unsigned long long *>(base + q.status);
 
-    int64_t nseg = 1, nchunks = (n + QS_C - 1) / QS_C;
+    const int64_t nchunks0 = (n + QS_C - 1) / QS_C;
     LaunchToken t = launch_begin(K_QS_PLAN, st);
-    k_qs_init<<<(unsigned)std::min<int64_t>((nchunks + 255) / 256, 4096), 256, 0, st>>>(cur, ccur, n,
-                                                                                      nchunks);
+    k_qs_init<<<(unsigned)std::min<int64_t>((nchunks0 + 255) / 256, 4096), 256, 0, st>>>(
+        cur, ccur, n, nchunks0, X, ctr, status);
     hs_status r = launch_end(t);
     if (r != HS_OK) return r;
 
     int lg = 0;
     while ((int64_t(1) << lg) < n) ++lg;
     const int64_t max_levels = qs_option_max_levels >= 0 ? qs_option_max_levels : 4 * lg + 16;
-
-    for (int64_t level = 0; nseg > 0; ++level) {
+    QCounters h{1ull, (unsigned long long)nchunks0, 0ull, 0ull};
+    for (int64_t level = 0; h.nseg > 0; ++level) {
         if (level >= max_levels)
-            return qs_fallback(X, Y, cur, nseg, s, base + q.y,
+            return qs_fallback(X, Y, cur, (int64_t)h.nseg, s, base + q.y,
                                merge_workspace_bytes(n_, 0), st);
-        cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(QCounters), st);
+        QCounters *cc = ctr + (level & 1), *nc = ctr + ((level + 1) & 1);
+        cudaError_t e = cudaMemsetAsync(nc, 0, sizeof(QCounters), st);
         if (e != cudaSuccess) return fail_cuda(e, "quick sort: counter reset");
-        const unsigned gseg = (unsigned)((nseg + 255) / 256);
-        t = launch_begin(K_QS_PLAN, st);
-        k_qs_pivot<<<gseg, 256, 0, st>>>(cur, nseg, X, Y);
-        if ((r = launch_end(t)) != HS_OK) return r;
         t = launch_begin(K_QS_PARTITION, st);
-        k_qs_partition<<<(unsigned)nchunks, QS_NT, 0, st>>>(cur, ccur, X, Y, X, Y);
-        if ((r = launch_end(t)) != HS_OK) return r;
-        t = launch_begin(K_QS_FILL, st);
-        k_qs_fill<<<(unsigned)nchunks, 256, 0, st>>>(cur, ccur, X);
+        k_qs_partition<<<(unsigned)h.nchunks, QS_NT, 0, st>>>(cur, ccur, cc, q.caps, X, Y, X, Y);
         if ((r = launch_end(t)) != HS_OK) return r;
         t = launch_begin(K_QS_PLAN, st);
-        k_qs_next<<<gseg, 256, 0, st>>>(cur, nseg, tile, nxt, q.cap_seg, small, q.cap_small, ctr);
+        k_qs_next<<<(unsigned)((h.nseg + 255) / 256), 256, 0, st>>>(cur, cc, nc, q.caps, tile, nxt,
+                                                                    small, fill, X, Y, status);
         if ((r = launch_end(t)) != HS_OK) return r;
 
-        QCounters h{};
-        e = cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st);
+        QCounters hc{}, hn{};
+        unsigned long long hst = 0;
+        e = cudaMemcpyAsync(&hc, cc, sizeof(hc), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hn, nc, sizeof(hn), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, status, sizeof(hst), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return fail_cuda(e, "quick sort: reading level counters");
-        if (h.overflow || (int64_t)h.nchunks > q.cap_chunk)
-            return fail(HS_ERR_CUDA, "quick sort: internal work-list overflow");
-        if (h.nsmall > 0 &&
-            (r = launch_small(L, small, (int64_t)h.nsmall, X, Y, X, s, st)) != HS_OK)
-            return r;
-        nseg = (int64_t)h.nseg;
-        nchunks = (int64_t)h.nchunks;
-        if (nseg > 0) {
-            t = launch_begin(K_QS_PLAN, st);
-            k_qs_chunkmap<<<(unsigned)nseg, 256, 0, st>>>(nxt, cnxt, q.cap_chunk);
+        if (hst) return fail(HS_ERR_CUDA, "quick sort: internal work-list overflow");
+        if (hc.nfill > 0) {
+            t = launch_begin(K_QS_FILL, st);
+            k_qs_fill<<<(unsigned)std::min<unsigned long long>(hc.nfill, 4096), 256, 0, st>>>(
+                fill, cc, q.caps, X);
             if ((r = launch_end(t)) != HS_OK) return r;
         }
+        if (hc.nsmall > 0 &&
+            (r = launch_small(L, (int64_t)hc.nsmall, small, cc, q.caps, X, Y, X, s, st)) != HS_OK)
+            return r;
+        if (hn.nseg > 0) {
+            t = launch_begin(K_QS_PLAN, st);
+            k_qs_chunkmap<<<(unsigned)hn.nseg, 256, 0, st>>>(nxt, nc, q.caps, cnxt);
+            if ((r = launch_end(t)) != HS_OK) return r;
+        }
+        h = hn;
         std::swap(cur, nxt);
         std::swap(ccur, cnxt);
     }
