@@ -514,7 +514,8 @@ def run_extras(hs, torch, dev, stream, args, rank, pristine):
 
 
 ABLATION_SIZES = (10_000, 25_000, 100_000, 1_000_000)
-ABLATION_SETS = ("none", "3", "3To4", "3To5", "6To8", "3To8", "PowerOf2", "Even", "Odd")
+ABLATION_SETS = ("none", "3", "3To4", "3To5", "6To8", "3To8", "PowerOf2", "Even", "Odd",
+                 "VarSort3", "VarSort4", "VarSort5")
 
 
 def run_netset_ablation(hs, torch, dev, stream):

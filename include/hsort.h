@@ -60,10 +60,14 @@ typedef enum {
 } hs_algo;
 
 /* Network set (Table 3): bit k set <=> the size-k network may be used,
- * k in 3..8.  0 is the classical algorithm (no networks).  Any other bit is
- * HS_ERR_INVALID_ARG.  The GPU leaf is the largest size in the set; a ragged
- * last leaf of r keys uses the size-r network when the set has it, else the
- * next larger size in the set padded with +infinity sentinels. */
+ * k in 3..8.  0 is the classical algorithm (no networks).  HS_NETS_VARSORT
+ * with exactly one size bit k is VarSortk (Table 3's VarSort3/4/5, a
+ * "dynamic sorting network" for any input of up to k elements): every leaf
+ * of up to k keys is sorted by the size-k network on +infinity-padded input.
+ * Any other bit pattern is HS_ERR_INVALID_ARG.  The GPU leaf is the largest
+ * size in the set; a ragged last leaf of r keys uses the size-r network when
+ * the set has it, else the next larger size in the set padded with +infinity
+ * sentinels (so on the GPU VarSortk and the set {k} run the same networks). */
 typedef uint32_t hs_netset;
 #define HS_NETS_NONE 0x000u
 #define HS_NETS_3 0x008u        /* {3} */
@@ -74,6 +78,10 @@ typedef uint32_t hs_netset;
 #define HS_NETS_POWEROF2 0x110u /* {4,8} */
 #define HS_NETS_EVEN 0x150u     /* {4,6,8} */
 #define HS_NETS_ODD 0x0A8u      /* {3,5,7} */
+#define HS_NETS_VARSORT 0x10000u
+#define HS_NETS_VARSORT3 0x10008u /* VarSort3 */
+#define HS_NETS_VARSORT4 0x10010u /* VarSort4 */
+#define HS_NETS_VARSORT5 0x10020u /* VarSort5 */
 
 /* ---------------------------------------------------------------- sorting */
 

@@ -32,6 +32,11 @@ NETSETS = {
     "3To5": (1 << 3) | (1 << 4) | (1 << 5),
     "3To8": 0x1F8,
     "6To8": (1 << 6) | (1 << 7) | (1 << 8),
+    # VarSortk: any subarray of 2..k elements is a leaf, sorted by the size-k
+    # network on a copy padded with +infinity (flag 0x10000 plus size bit k).
+    "VarSort3": 0x10000 | (1 << 3),
+    "VarSort4": 0x10000 | (1 << 4),
+    "VarSort5": 0x10000 | (1 << 5),
 }
 
 

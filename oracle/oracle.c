@@ -116,13 +116,37 @@ static void apply_network_pairs(int m, int32_t *k, int32_t *v, int64_t *p) {
     }
 }
 
-/* "size matches sorting network size" (Algorithm 1 and 2) read as membership
- * of size in the configuration's set (Table 3). */
-static int size_in_set(int64_t size, uint32_t netset) {
-    return size >= 3 && size <= 8 && ((netset >> size) & 1u);
+/* The size k of a VarSortk configuration, else 0. */
+static int varsort_size(uint32_t netset) {
+    if (!(netset & OR_VARSORT)) return 0;
+    for (int k = 3; k <= 8; ++k)
+        if ((netset & ~OR_VARSORT) == (1u << k)) return k;
+    return 0;
 }
 
-static int netset_valid(uint32_t netset) { return (netset & ~0x1F8u) == 0; }
+/* "size matches sorting network size" (Algorithm 1 and 2): for a set of fixed
+ * networks, membership of size in the configuration's set (Table 3); for
+ * VarSortk, any size from 2 to k.  Returns the network to apply (0: none). */
+static int leaf_network(int64_t size, uint32_t netset) {
+    const int k = varsort_size(netset);
+    if (k) return (size >= 2 && size <= k) ? k : 0;
+    return (size >= 3 && size <= 8 && ((netset >> size) & 1u)) ? (int)size : 0;
+}
+
+static int netset_valid(uint32_t netset) {
+    if (netset & OR_VARSORT) return varsort_size(netset) != 0;
+    return (netset & ~0x1F8u) == 0;
+}
+
+/* Sorts a[0..size) with the size-m network (m >= size): the keys are copied
+ * into m slots, the missing ones set to +infinity, and the first size copied
+ * back (for size == m this is the plain network). */
+static void apply_leaf(int m, int32_t *a, int64_t size) {
+    int32_t t[8];
+    for (int i = 0; i < m; ++i) t[i] = i < size ? a[i] : INT32_MAX;
+    or_apply_network(m, t);
+    for (int64_t i = 0; i < size; ++i) a[i] = t[i];
+}
 
 /* ------------------------------------------------------------------------ */
 /* Algorithm 1.                                                              */
@@ -142,9 +166,10 @@ static void merge_sort_rec(int32_t *a, int64_t left, int64_t right, uint32_t net
                            int32_t *tmp, or_counters *c, uint64_t depth) {
     if (c && depth > c->max_depth) c->max_depth = depth;
     int64_t size = right - left + 1;
-    if (size_in_set(size, netset)) {
-        or_apply_network((int)size, a + left);
-        if (c) c->net_calls[size]++;
+    const int m = leaf_network(size, netset);
+    if (m) {
+        apply_leaf(m, a + left, size);
+        if (c) c->net_calls[m]++;
         return;
     }
     if (left < right) {
@@ -188,9 +213,23 @@ static void merge_sort_pairs_rec(int32_t *k, int32_t *v, int64_t *p, int64_t lef
                                  int64_t *tp, or_counters *c, uint64_t depth) {
     if (c && depth > c->max_depth) c->max_depth = depth;
     int64_t size = right - left + 1;
-    if (size_in_set(size, netset)) {
-        apply_network_pairs((int)size, k + left, v + left, p + left);
-        if (c) c->net_calls[size]++;
+    const int m = leaf_network(size, netset);
+    if (m) {
+        /* Padded slots carry key +infinity and a position past every real one. */
+        int32_t tk8[8], tv8[8];
+        int64_t tp8[8];
+        for (int i = 0; i < m; ++i) {
+            tk8[i] = i < size ? k[left + i] : INT32_MAX;
+            tv8[i] = i < size ? v[left + i] : 0;
+            tp8[i] = i < size ? p[left + i] : INT64_MAX;
+        }
+        apply_network_pairs(m, tk8, tv8, tp8);
+        for (int64_t i = 0; i < size; ++i) {
+            k[left + i] = tk8[i];
+            v[left + i] = tv8[i];
+            p[left + i] = tp8[i];
+        }
+        if (c) c->net_calls[m]++;
         return;
     }
     if (left < right) {
@@ -256,9 +295,10 @@ static void quick_sort_rec(int32_t *a, int64_t low, int64_t high, uint32_t netse
                            or_counters *c, uint64_t depth) {
     if (c && depth > c->max_depth) c->max_depth = depth;
     int64_t size = high - low + 1;
-    if (size_in_set(size, netset)) {
-        or_apply_network((int)size, a + low);
-        if (c) c->net_calls[size]++;
+    const int m = leaf_network(size, netset);
+    if (m) {
+        apply_leaf(m, a + low, size);
+        if (c) c->net_calls[m]++;
         return;
     }
     if (low < high) {

@@ -15,7 +15,10 @@
  *
  * Network sets (Table 3, "Sorting Network Configurations"): bit k of a netset
  * means "a network of size k is available", k in 3..8.  0 is the classical
- * algorithm with no networks.
+ * algorithm with no networks.  OR_VARSORT together with exactly one size bit
+ * k is VarSortk (Table 3's VarSort3/4/5, "dynamic sorting networks" for any
+ * input of up to k elements): every subarray of 2..k elements is a leaf,
+ * sorted by the size-k network on a copy padded with +infinity sentinels.
  */
 #ifndef HS_ORACLE_H
 #define HS_ORACLE_H
@@ -25,6 +28,8 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+#define OR_VARSORT 0x10000u
 
 /* Instrumentation counters, filled by the sorts when non-NULL. */
 typedef struct {

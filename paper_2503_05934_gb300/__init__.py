@@ -19,6 +19,7 @@ from ._lib import HsortError, Plan, check, lib
 NETSETS = {
     "none": 0x000, "3": 0x008, "3To4": 0x018, "3To5": 0x038, "6To8": 0x1C0,
     "3To8": 0x1F8, "PowerOf2": 0x110, "Even": 0x150, "Odd": 0x0A8,
+    "VarSort3": 0x10008, "VarSort4": 0x10010, "VarSort5": 0x10020,
 }
 ALGOS = {"merge": 0, "quick": 1}
 

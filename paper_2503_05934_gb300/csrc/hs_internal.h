@@ -46,7 +46,13 @@ void count_launches(uint64_t k);
 hs_status launch_end(const LaunchToken &t);
 
 // Validation shared by the entry points.
-inline bool netset_ok(hs_netset s) { return (s & ~0x1F8u) == 0; }
+inline bool netset_ok(hs_netset s) {
+    if (s & HS_NETS_VARSORT) {  // VarSortk: the flag and exactly one size bit k in 3..8
+        const hs_netset k = s & ~HS_NETS_VARSORT;
+        return k != 0 && (k & ~0x1F8u) == 0 && (k & (k - 1)) == 0;
+    }
+    return (s & ~0x1F8u) == 0;
+}
 inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

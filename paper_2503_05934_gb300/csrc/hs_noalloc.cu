@@ -60,7 +60,7 @@ extern "C" hs_status hs_sort_i32_noalloc(int32_t *d_keys, size_t n, hs_netset s,
                                          hs_stream_t stream) {
     clear_error();
     if (!netset_ok(s))
-        return fail(HS_ERR_INVALID_ARG, "hs_sort_i32_noalloc: netset has bits outside sizes 3..8");
+        return fail(HS_ERR_INVALID_ARG, "hs_sort_i32_noalloc: netset is neither a set of sizes 3..8 nor a VarSort configuration");
     if (n > 0 && !d_keys) return fail(HS_ERR_INVALID_ARG, "hs_sort_i32_noalloc: NULL keys with n > 0");
     if (n > 0 && !aligned(d_keys, 4))
         return fail(HS_ERR_INVALID_ARG, "hs_sort_i32_noalloc: keys not 4-byte aligned");

@@ -229,7 +229,7 @@ static hs_status check_common(const void *d_keys, size_t n, hs_algo a, hs_netset
     if (a != HS_ALGO_MERGE && a != HS_ALGO_QUICK)
         return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": unknown algo");
     if (!netset_ok(s))
-        return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": netset has bits outside sizes 3..8");
+        return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": netset is neither a set of sizes 3..8 nor a VarSort configuration");
     if (n > 0 && !d_keys) return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": NULL keys with n > 0");
     if (n > 0 && !aligned(d_keys, 4)) return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": keys not 4-byte aligned");
     if (n > (size_t)INT64_MAX / 16) return fail(HS_ERR_INVALID_ARG, std::string(fn) + ": n too large");

@@ -250,7 +250,7 @@ hs_plan default_seg_plan(hs_netset s) {
 }
 
 hs_status check_plan(const hs_plan &p) {
-    if (!netset_ok(p.netset)) return fail(HS_ERR_INVALID_ARG, "plan netset has bits outside sizes 3..8");
+    if (!netset_ok(p.netset)) return fail(HS_ERR_INVALID_ARG, "plan netset is neither a set of sizes 3..8 nor a VarSort configuration");
     if (p.block_threads != 256 && p.block_threads != 512)
         return fail(HS_ERR_INVALID_ARG, "plan block_threads must be 256 or 512");
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 8)

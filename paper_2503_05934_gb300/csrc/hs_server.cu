@@ -299,7 +299,7 @@ hs_status hs_server_submit(hs_server *srv, int32_t *d_keys, size_t n, hs_algo a,
     if (a != HS_ALGO_MERGE)
         return fail(a == HS_ALGO_QUICK ? HS_ERR_UNSUPPORTED : HS_ERR_INVALID_ARG,
                     "hs_server_submit: the server runs the merge path (HS_ALGO_MERGE) only");
-    if (!netset_ok(s)) return fail(HS_ERR_INVALID_ARG, "hs_server_submit: netset has bits outside sizes 3..8");
+    if (!netset_ok(s)) return fail(HS_ERR_INVALID_ARG, "hs_server_submit: netset is neither a set of sizes 3..8 nor a VarSort configuration");
     if (n > 0 && (!d_keys || !aligned(d_keys, 4)))
         return fail(HS_ERR_INVALID_ARG, "hs_server_submit: NULL or unaligned keys");
     Req *r = new (std::nothrow) Req();

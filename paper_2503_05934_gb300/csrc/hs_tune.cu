@@ -255,7 +255,7 @@ static hs_status plan_from(const hs_plan *plan, hs_netset s, hs_plan *out) {
         if (plan->reserved != 0) return fail(HS_ERR_INVALID_ARG, "plan reserved field must be 0");
         *out = *plan;
     } else {
-        if (!netset_ok(s)) return fail(HS_ERR_INVALID_ARG, "netset has bits outside sizes 3..8");
+        if (!netset_ok(s)) return fail(HS_ERR_INVALID_ARG, "netset is neither a set of sizes 3..8 nor a VarSort configuration");
         *out = default_seg_plan(s);
     }
     return check_plan(*out);

@@ -37,10 +37,17 @@ def _read_golden(name):
 # ---------------------------------------------------------------- networks
 
 def test_table3_netsets_match_paper():
+    names = set()
     for row in _read_golden("table3_netsets.txt"):
         name, sizes = row.split(":")
-        mask = sum(1 << int(s) for s in sizes.split())
+        words = sizes.split()
+        if words[0] == "var":  # VarSortk: dynamic network for any size up to k
+            mask = 0x10000 | (1 << int(words[1]))
+        else:
+            mask = sum(1 << int(w) for w in words)
         assert oracle.NETSETS[name] == mask, name
+        names.add(name)
+    assert names | {"none"} == set(oracle.NETSETS)  # the 11 configurations + classical
 
 
 @pytest.mark.parametrize("m", range(3, 9))
@@ -189,17 +196,24 @@ def closed_form_leaves(n, netset_mask):
     ceil(s/2) and floor(s/2) keys.  Walk the depths tracking how many live
     nodes have each of the two sizes."""
     live = {n: 1}
-    nets = {}
+    nets = {}    # network size -> applications
+    leaf_keys = 0
     ones = 0
     merges = 0
     depth = 0
+    var_k = 0
+    if netset_mask & 0x10000:  # VarSortk: leaves are the sizes 2..k, all by the size-k network
+        var_k = (netset_mask & ~0x10000).bit_length() - 1
     while live:
         q = n >> depth
         assert set(live) <= {q, q + 1}, (depth, live)  # closed form holds
         nxt = {}
         for s, cnt in live.items():
-            if 3 <= s <= 8 and (netset_mask >> s) & 1:
-                nets[s] = nets.get(s, 0) + cnt
+            leaf_net = (var_k if 2 <= s <= var_k else 0) if var_k else \
+                (s if 3 <= s <= 8 and (netset_mask >> s) & 1 else 0)
+            if leaf_net:
+                nets[leaf_net] = nets.get(leaf_net, 0) + cnt
+                leaf_keys += s * cnt
             elif s == 1:
                 ones += cnt
             elif s >= 2:
@@ -208,21 +222,31 @@ def closed_form_leaves(n, netset_mask):
                     nxt[c] = nxt.get(c, 0) + cnt
         live = nxt
         depth += 1
-    return nets, merges, ones
+    return nets, merges, ones, leaf_keys
 
 
 @pytest.mark.parametrize("n", [10_000, 25_000, 100_000, 1_000_000, 12345, 1 << 16])
-@pytest.mark.parametrize("netset", ["3To5", "6To8", "3To8", "none", "PowerOf2", "Odd"])
+@pytest.mark.parametrize("netset", ["3To5", "6To8", "3To8", "none", "PowerOf2", "Odd",
+                                    "VarSort3", "VarSort4", "VarSort5"])
 def test_leaf_histogram_closed_form(n, netset):
     a = hs_inputs.random_i32(n, 3)
     out, c = oracle.merge_sort(a, netset, counters=True)
-    nets, merges, ones = closed_form_leaves(n, oracle.NETSETS[netset])
+    nets, merges, ones, leaf_keys = closed_form_leaves(n, oracle.NETSETS[netset])
     assert c["net_calls"] == nets
     assert c["merge_calls"] == merges
     leaves = sum(nets.values()) + ones
     assert c["merge_calls"] == leaves - 1           # binary tree
-    assert sum(s * k for s, k in nets.items()) + ones == n
+    assert leaf_keys + ones == n
     assert np.array_equal(out, np.sort(a))
+
+
+def test_varsort_leaves_cover_sizes_two_to_k():
+    # n = 10,000 halves down to 4/5 keys: VarSort4 sorts the 4s and splits the
+    # 5s into 3 + 2 (both <= 4), VarSort5 stops at the 4/5 level, VarSort3
+    # goes one level below; every leaf uses the size-k network.
+    for k, name in [(3, "VarSort3"), (4, "VarSort4"), (5, "VarSort5")]:
+        _, c = oracle.merge_sort(hs_inputs.random_i32(10_000, 2), name, counters=True)
+        assert set(c["net_calls"]) == {k}, name
 
 
 def test_ten_thousand_has_no_six_to_eight_leaf():
