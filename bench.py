@@ -504,6 +504,19 @@ def run_extras(hs, torch, dev, stream, args, rank, pristine):
         "workload": f"2^{args.log2n - 1} (int32 key from 2^16 values, int32 index) "
                     f"stable merge sort, {args.netset} leaves"}
     del pk, pv, wk, wv, wsb
+    # int64 keys: 2^27 (1 GiB), uniform over the int64 range.
+    a64 = torch.from_numpy(hs_inputs.keys_i64(n, "random", hs_inputs.config_seed(2, salt=64))).to(dev)
+    w64 = torch.empty_like(a64)
+    ws64 = torch.empty(hs.hs_sort_i64_workspace_bytes(n), dtype=torch.uint8, device=dev)
+    ms = time_sorts(torch, stream, max(3, args.steps // 4), 2, lambda: w64.copy_(a64),
+                    lambda: hs.hs_sort_i64(w64, "merge", args.netset, ws=ws64, stream=stream))
+    assert bool((w64[1:] >= w64[:-1]).all().item()), "int64 sort output not sorted"
+    p64 = sort_passes(n, 256 * (4 * 8 - 1))
+    out[f"merge_int64_2p{args.log2n - 1}"] = {
+        "value": n / (ms / 1e3), "unit": "keys/s", "ms_per_sort": ms, "passes": p64,
+        "frac_of_measured": min(p64, sort_passes(n, 8192)) * 16 * n / (ms / 1e3) / (peak * 1e9),
+        "workload": f"2^{args.log2n - 1} uniform int64 keys, hybrid merge sort, {args.netset} leaves"}
+    del a64, w64, ws64
     if not args.no_ablation:
         out["netset_ablation"] = run_netset_ablation(hs, torch, dev, stream)
     if not args.no_batched:

@@ -180,6 +180,30 @@ def keys(n: int, dist: str, seed: int) -> np.ndarray:
     raise ValueError(dist)
 
 
+def keys_i64(n: int, dist: str, seed: int) -> np.ndarray:
+    """int64 keys: 'random' is each SplitMix64 output as a signed 64-bit word
+    (uniform over the int64 range); 'sorted' is a running sum of random gaps
+    spread over the int64 range (no sort involved); 'nearly' is the sorted
+    keys with floor(n/100) sequential swaps of uniform pairs.  The sorted keys
+    start near INT64_MIN and span about half the range."""
+    if dist == "random":
+        return splitmix64(seed ^ 0x693634, 0, n).view(np.int64).copy()
+    if dist not in ("sorted", "nearly"):
+        raise ValueError(dist)
+    max_gap = np.uint64(max(1, (1 << 64) // max(n, 1) - 1))
+    gaps = splitmix64(seed ^ 0x67617073, 0, n) % max_gap
+    run = np.cumsum(gaps, dtype=np.uint64)  # below 2^64: n gaps of less than 2^64/n
+    a = (run + np.uint64(1 << 63)).view(np.int64)  # shift to start near INT64_MIN
+    if dist == "sorted":
+        return a
+    k = n // 100
+    if k:
+        draws = splitmix64(seed ^ 0x6E6561726C79, 0, 2 * k) % np.uint64(n)
+        for i, j in zip(draws[0::2].astype(np.int64).tolist(), draws[1::2].astype(np.int64).tolist()):
+            a[i], a[j] = a[j], a[i]
+    return a
+
+
 def pair_keys_16bit(n: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
     """Keys from 2^16 distinct int32 values and values = original index."""
     u = (random_i32(n, seed).view(np.uint32) & np.uint32(0xFFFF)).astype(np.uint32)

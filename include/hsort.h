@@ -115,6 +115,16 @@ HS_API hs_status hs_sort_i32(int32_t *d_keys, size_t n, hs_algo a, hs_netset s, 
 HS_API hs_status hs_sort_pairs_i32(int32_t *d_keys, int32_t *d_vals, size_t n, hs_algo a,
                             hs_netset s, void *d_ws, size_t ws_bytes, hs_stream_t stream);
 
+/* int64 keys (Algorithm 1 on 8-byte keys, the same network leaves and merge
+ * levels as hs_sort_i32): sorts d_keys[0..n) (signed order) in place.  Merge
+ * path only: HS_ALGO_QUICK returns HS_ERR_UNSUPPORTED.  d_keys must be 8-byte
+ * aligned; the workspace (hs_sort_i64_workspace_bytes, 16-byte aligned,
+ * owned by the caller) holds a keys copy, the merge partitions and every
+ * 32nd key.  Errors as hs_sort_i32.  Asynchronous on stream. */
+HS_API size_t hs_sort_i64_workspace_bytes(size_t n);
+HS_API hs_status hs_sort_i64(int64_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
+                             size_t ws_bytes, hs_stream_t stream);
+
 /* Host-buffer form, for callers whose keys live in host memory: copies
  * h_keys to the device, sorts them as hs_sort_i32 does, copies the result
  * back into h_keys and waits for `stream` before returning (synchronous).

@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
         L.or_merge.restype = None
         L.or_merge_sort.argtypes = [i32p, ctypes.c_int64, ctypes.c_uint32, cp]
         L.or_merge_sort.restype = ctypes.c_int
+        L.or_merge_sort_i64.argtypes = [i64p, ctypes.c_int64, ctypes.c_uint32, cp]
+        L.or_merge_sort_i64.restype = ctypes.c_int
         L.or_median_of_three.argtypes = [i32p, ctypes.c_int64, ctypes.c_int64]
         L.or_median_of_three.restype = ctypes.c_int64
         L.or_hoare_partition.argtypes = [i32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
@@ -155,6 +157,17 @@ def merge_sort(a: np.ndarray, netset="6To8", counters: bool = False):
     rc = lib().or_merge_sort(_i32(out), out.size, netset_mask(netset), ctypes.byref(c))
     if rc:
         raise ValueError(f"or_merge_sort failed ({rc})")
+    return (out, c.as_dict()) if counters else out
+
+
+def merge_sort_i64(a: np.ndarray, netset="6To8", counters: bool = False):
+    """Algorithm 1 on a copy of the int64 array ``a``; returns the sorted copy
+    (and counters)."""
+    out = np.ascontiguousarray(a, dtype=np.int64).copy()
+    c = Counters()
+    rc = lib().or_merge_sort_i64(_i64(out), out.size, netset_mask(netset), ctypes.byref(c))
+    if rc:
+        raise ValueError(f"or_merge_sort_i64 failed ({rc})")
     return (out, c.as_dict()) if counters else out
 
 

@@ -192,6 +192,69 @@ int or_merge_sort(int32_t *a, int64_t n, uint32_t netset, or_counters *c) {
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 on int64 keys: the same recursion, leaf rule and stable merge. */
+
+static void apply_network_i64(int m, int64_t *a) {
+    const or_net *net = &g_nets[m];
+    for (int c = 0; c < net->n; c++) {
+        int i = net->lo[c], j = net->hi[c];
+        if (a[j] < a[i]) {
+            int64_t t = a[i];
+            a[i] = a[j];
+            a[j] = t;
+        }
+    }
+}
+
+static void apply_leaf_i64(int m, int64_t *a, int64_t size) {
+    int64_t t[8];
+    for (int i = 0; i < m; ++i) t[i] = i < size ? a[i] : INT64_MAX;
+    apply_network_i64(m, t);
+    for (int64_t i = 0; i < size; ++i) a[i] = t[i];
+}
+
+static void merge_i64(int64_t *a, int64_t left, int64_t mid, int64_t right, int64_t *tmp) {
+    int64_t i = left, j = mid + 1, o = 0;
+    while (i <= mid && j <= right) {
+        if (a[j] < a[i]) tmp[o++] = a[j++];
+        else tmp[o++] = a[i++];
+    }
+    while (i <= mid) tmp[o++] = a[i++];
+    while (j <= right) tmp[o++] = a[j++];
+    memcpy(a + left, tmp, (size_t)o * sizeof(int64_t));
+}
+
+static void merge_sort_rec_i64(int64_t *a, int64_t left, int64_t right, uint32_t netset,
+                               int64_t *tmp, or_counters *c, uint64_t depth) {
+    if (c && depth > c->max_depth) c->max_depth = depth;
+    int64_t size = right - left + 1;
+    const int m = leaf_network(size, netset);
+    if (m) {
+        apply_leaf_i64(m, a + left, size);
+        if (c) c->net_calls[m]++;
+        return;
+    }
+    if (left < right) {
+        int64_t mid = left + (right - left) / 2;
+        merge_sort_rec_i64(a, left, mid, netset, tmp, c, depth + 1);
+        merge_sort_rec_i64(a, mid + 1, right, netset, tmp, c, depth + 1);
+        merge_i64(a, left, mid, right, tmp);
+        if (c) c->merge_calls++;
+    }
+}
+
+int or_merge_sort_i64(int64_t *a, int64_t n, uint32_t netset, or_counters *c) {
+    if (!netset_valid(netset) || n < 0) return -1;
+    if (n == 0) return 0;
+    build_nets();
+    int64_t *tmp = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!tmp) return -2;
+    merge_sort_rec_i64(a, 0, n - 1, netset, tmp, c, 0);
+    free(tmp);
+    return 0;
+}
+
 /* Pairs: the same recursion; positions ride along only to order equal keys
  * inside networks. */
 static void merge_pairs(int32_t *k, int32_t *v, int64_t *p, int64_t left, int64_t mid,

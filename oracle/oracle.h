@@ -56,6 +56,10 @@ void or_merge(int32_t *a, int64_t left, int64_t mid, int64_t right, int32_t *tmp
 /* Algorithm 1 on a[0..n-1].  netset: Table 3 bitmask (0 = classical). */
 int or_merge_sort(int32_t *a, int64_t n, uint32_t netset, or_counters *c);
 
+/* Algorithm 1 on int64 keys a[0..n-1] (same networks, leaf rule and stable
+ * Merge as or_merge_sort). */
+int or_merge_sort_i64(int64_t *a, int64_t n, uint32_t netset, or_counters *c);
+
 /* MedianOfThree(array, low, high) of Algorithm 2: orders a[low], a[mid],
  * a[high] in place, mid = low + (high-low)/2, and returns mid. */
 int64_t or_median_of_three(int32_t *a, int64_t low, int64_t high);

@@ -25,7 +25,8 @@ ALGOS = {"merge": 0, "quick": 1}
 
 __all__ = [
     "NETSETS", "ALGOS", "HsortError", "lib", "netset_mask", "algo_id",
-    "hs_sort_workspace_bytes", "hs_sort_i32", "hs_sort_pairs_i32",
+    "hs_sort_workspace_bytes", "hs_sort_i32", "hs_sort_pairs_i32", "hs_sort_i64",
+    "hs_sort_i64_workspace_bytes",
     "hs_sort_host_workspace_bytes", "hs_sort_i32_host", "hs_launch_count",
     "hs_prof_enable", "hs_prof_select", "hs_prof_reset", "hs_prof_read", "hs_version", "hs_set_option",
     "hs_sort_i32_noalloc", "NOALLOC_MAX_KEYS", "hs_device_check", "Plan", "make_plan",
@@ -94,6 +95,22 @@ def hs_sort_pairs_i32(keys: torch.Tensor, vals: torch.Tensor, algo="merge", nets
                                   n, algo_id(algo), netset_mask(netset), ws.data_ptr(),
                                   ws.numel() * ws.element_size(), _stream_ptr(stream)))
     return keys, vals
+
+
+def hs_sort_i64_workspace_bytes(n: int) -> int:
+    return int(lib().hs_sort_i64_workspace_bytes(n))
+
+
+def hs_sort_i64(keys: torch.Tensor, algo="merge", netset="6To8", ws: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """Sorts ``keys`` (CUDA int64, contiguous) in place; returns ``keys``."""
+    if keys.dtype != torch.int64 or not keys.is_contiguous() or not keys.is_cuda:
+        raise ValueError("keys must be a contiguous int64 CUDA tensor")
+    n = keys.numel()
+    ws = _workspace(hs_sort_i64_workspace_bytes(n), keys.device, ws)
+    check(lib().hs_sort_i64(keys.data_ptr() if n else None, n, algo_id(algo), netset_mask(netset),
+                            ws.data_ptr(), ws.numel() * ws.element_size(), _stream_ptr(stream)))
+    return keys
 
 
 def hs_sort_host_workspace_bytes(n: int, algo="merge") -> int:

@@ -26,6 +26,8 @@ SIGNATURES = {
     "hs_sort_workspace_bytes": (_sz, [_sz, _int, _int]),
     "hs_sort_i32": (_int, [_vp, _sz, _int, _u32, _vp, _sz, _vp]),
     "hs_sort_pairs_i32": (_int, [_vp, _vp, _sz, _int, _u32, _vp, _sz, _vp]),
+    "hs_sort_i64_workspace_bytes": (_sz, [_sz]),
+    "hs_sort_i64": (_int, [_vp, _sz, _int, _u32, _vp, _sz, _vp]),
     "hs_sort_host_workspace_bytes": (_sz, [_sz, _int]),
     "hs_sort_i32_host": (_int, [_vp, _sz, _int, _u32, _vp, _sz, _vp]),
     "hs_sort_i32_noalloc": (_int, [_vp, _sz, _u32, _vp]),

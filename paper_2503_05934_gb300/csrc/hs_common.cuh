@@ -44,6 +44,14 @@ HS_DEV void st_stream(int4 *p, int4 v) {
 HS_DEV void st_stream(int32_t *p, int32_t v) {
     asm volatile("st.global.cs.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+HS_DEV int64_t ld_stream(const int64_t *p) {
+    int64_t v;
+    asm volatile("ld.global.cs.s64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+HS_DEV void st_stream(int64_t *p, int64_t v) {
+    asm volatile("st.global.cs.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 }  // namespace hs
 

@@ -81,6 +81,9 @@ hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, vo
 hs_status pairs_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, void *d_ws,
                      size_t ws_bytes, cudaStream_t st);
 int64_t pairs_tile(int L);
+size_t merge_workspace_bytes_i64(size_t n);
+hs_status merge_sort_i64(int64_t *d_keys, size_t n, hs_netset s, void *d_ws, size_t ws_bytes,
+                         cudaStream_t st);
 void pairs_set_blocksort(int v);
 void pairs_set_merge(int v);
 

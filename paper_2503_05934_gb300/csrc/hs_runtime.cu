@@ -259,6 +259,24 @@ hs_status hs_sort_pairs_i32(int32_t *d_keys, int32_t *d_vals, size_t n, hs_algo 
     return merge_sort(d_keys, d_vals, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
+size_t hs_sort_i64_workspace_bytes(size_t n) { return merge_workspace_bytes_i64(n); }
+
+hs_status hs_sort_i64(int64_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
+                      size_t ws_bytes, hs_stream_t stream) {
+    clear_error();
+    if (a != HS_ALGO_MERGE && a != HS_ALGO_QUICK)
+        return fail(HS_ERR_INVALID_ARG, "hs_sort_i64: unknown algorithm");
+    if (!netset_ok(s))
+        return fail(HS_ERR_INVALID_ARG, "hs_sort_i64: netset is neither a set of sizes 3..8 nor a VarSort configuration");
+    if (n > 0 && !d_keys) return fail(HS_ERR_INVALID_ARG, "hs_sort_i64: NULL keys with n > 0");
+    if (n > 0 && !aligned(d_keys, 8)) return fail(HS_ERR_INVALID_ARG, "hs_sort_i64: keys not 8-byte aligned");
+    if (n > (size_t)INT64_MAX / 16) return fail(HS_ERR_INVALID_ARG, "hs_sort_i64: n too large");
+    if (a == HS_ALGO_QUICK)
+        return fail(HS_ERR_UNSUPPORTED, "hs_sort_i64: int64 keys use the merge path");
+    if (n <= 1) return HS_OK;
+    return merge_sort_i64(d_keys, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
 size_t hs_sort_host_workspace_bytes(size_t n, hs_algo a) {
     return align_up(n * sizeof(int32_t), 256) + hs_sort_workspace_bytes(n, 0, a);
 }

@@ -71,3 +71,15 @@ def test_c_forms_match_numpy_definitions():
     a = g.segmented(400, 9)
     b = g.np_segmented(400, 9)
     assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_int64_keys():
+    n = 100_000
+    r = g.keys_i64(n, "random", 1)
+    assert r.dtype == np.int64 and np.array_equal(r, g.keys_i64(n, "random", 1))
+    assert r.min() < -(1 << 62) and r.max() > (1 << 62)
+    s = g.keys_i64(n, "sorted", 2)
+    assert np.all(s[1:] >= s[:-1]) and s[0] < -(1 << 62) and int(s[-1]) - int(s[0]) > (1 << 62)
+    nearly = g.keys_i64(n, "nearly", 2)
+    assert 0 < np.count_nonzero(nearly != s) <= 2 * (n // 100)
+    assert np.array_equal(np.sort(nearly), s)

@@ -283,3 +283,22 @@ def test_checks():
     a = np.array([3, 1, 2, 2], np.int32)
     assert not oracle.is_sorted(a) and oracle.is_sorted(np.sort(a))
     assert oracle.count_less(a, 2) == 1 and oracle.count_less_equal(a, 2) == 3
+
+
+# ---------------------------------------------------------------- int64 keys
+
+@pytest.mark.parametrize("netset", ["none", "6To8", "3To5", "VarSort4"])
+def test_int64_merge_sort(netset):
+    """Algorithm 1 on int64 keys: numpy's sort on every edge size and
+    distribution, the extremes of the type, and the same recursion (leaf and
+    Merge counts) as the int32 form for the same n."""
+    for n in EDGE_SIZES:
+        for dist in hs_inputs.DISTS:
+            a = hs_inputs.keys_i64(n, dist, 2000 + n)
+            assert np.array_equal(oracle.merge_sort_i64(a, netset), np.sort(a)), (n, dist)
+    ext = np.array([2**63 - 1, -2**63, 0, -1, 1] * 41, np.int64)
+    assert np.array_equal(oracle.merge_sort_i64(ext, netset), np.sort(ext))
+    for n in [10_000, 12_345]:
+        _, c64 = oracle.merge_sort_i64(hs_inputs.keys_i64(n, "random", 1), netset, counters=True)
+        _, c32 = oracle.merge_sort(hs_inputs.random_i32(n, 1), netset, counters=True)
+        assert c64["net_calls"] == c32["net_calls"] and c64["merge_calls"] == c32["merge_calls"]
