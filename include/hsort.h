@@ -304,6 +304,9 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *   "quick_max_levels": partition levels the quick path runs before its depth
  *     guard merge-sorts the segments still open (default -1 = automatic,
  *     4*ceil(log2 n) + 16).
+ *   "quick_partition": 3 (default) 3-way partitions (< / = / > pivot); 2 the
+ *     2-way form of Algorithm 2 (left <= pivot <= right, keys equal to the
+ *     pivot alternating sides by their rank among the equal keys).
  *   "blocksort_shape": keys block-sort shape, 0: 512 threads x 2 leaves,
  *     1: 1024 x 2, 2: 256 x 4, 3: 512 x 4, 4: 288 x 4, 5: 576 x 4, -1 (default): per
  *     array, 4 when its larger tile saves a global level over 2, else 2.  A thread holds its

@@ -108,6 +108,7 @@ hs_status device_check(cudaStream_t st);
 
 size_t quick_workspace_bytes(size_t n);
 void quick_set_max_levels(int64_t v);
+void quick_set_two_way(int v);
 hs_status quick_sort(int32_t *d_keys, size_t n, hs_netset s, void *d_ws, size_t ws_bytes,
                      cudaStream_t st);
 

@@ -46,7 +46,8 @@ struct QSeg {
     // Reservation cursors of the < range (from begin) and the > range (back
     // from end); after the partition pass, the segment's < and > counts.
     unsigned long long n_lt, n_gt;
-    int32_t buf, pivot;  // buf 0: caller's array, 1: workspace
+    unsigned long long n_eq;  // 2-way form: ranks handed out to keys equal to the pivot
+    int32_t buf, pivot;       // buf 0: caller's array, 1: workspace
 };
 
 struct QSmall {
@@ -102,6 +103,14 @@ __global__ void k_qs_init(QSeg *segs, int32_t *chunk_seg, int64_t n, int64_t nch
         chunk_seg[c] = 0;
 }
 
+// Option "quick_partition" 2: Algorithm 2's 2-way form (every key goes to
+// one side: left <= pivot <= right).  Keys equal to the pivot alternate sides
+// by their rank among the segment's equal keys (an atomic per chunk hands out
+// the ranks), so each side gets half of them: with a median-of-three pivot
+// both sides are then non-empty and every level makes progress, as Hoare's
+// scan does by stopping on equal keys from both ends.
+static int g_qs_two_way = 0;
+
 // One chunk per CTA: each warp classifies its 32*QS_IPT keys (slice j of the
 // chunk holds keys j*QS_NT + [0, QS_NT); warp w takes 32 of them) and
 // compacts them into its own shared region, < keys from the front and > keys
@@ -109,14 +118,15 @@ __global__ void k_qs_init(QSeg *segs, int32_t *chunk_seg, int64_t n, int64_t nch
 // A scan over the warps' totals gives each warp's place in the chunk's < and
 // > runs; one atomic per run reserves the chunk's place in the segment; each
 // warp then copies its keys out as coalesced runs.
+template <bool TWO_WAY>
 __global__ void __launch_bounds__(QS_NT, 4)
     k_qs_partition(QSeg *segs, const int32_t *chunk_seg, const QCounters *ctr, QCaps caps,
                    const int32_t *X, const int32_t *Y, int32_t *Xw, int32_t *Yw) {
     constexpr int NW = QS_NT / 32;
     constexpr int WK = 32 * QS_IPT;  // keys per warp
     __shared__ int32_t stage[QS_C];  // warp w: [w*WK, (w+1)*WK), < from the front, > from the back
-    __shared__ int s_wlt[NW], s_wgt[NW];
-    __shared__ unsigned long long s_base[2];
+    __shared__ int s_wlt[NW], s_wgt[NW], s_weq[NW];
+    __shared__ unsigned long long s_base[3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const int64_t c = blockIdx.x;
@@ -137,11 +147,40 @@ __global__ void __launch_bounds__(QS_NT, 4)
             const int i = j * QS_NT + threadIdx.x;
             k[j] = i < len ? ld_stream(src + i) : p;  // padding counts as "=" and is dropped
         }
+        // 2-way form: the global rank of each equal key among the segment's
+        // equal keys (chunk base from an atomic, then warp and slice order).
+        int eq_rank0 = 0;
+        if constexpr (TWO_WAY) {
+            int neq = 0;
+#pragma unroll
+            for (int j = 0; j < QS_IPT; ++j)
+                neq += __popc(__ballot_sync(0xffffffffu, k[j] == p && j * QS_NT + (int)threadIdx.x < len));
+            if (lane == 0) s_weq[warp] = neq;
+            __syncthreads();
+            int off = 0, tot = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                off += (w < warp) ? s_weq[w] : 0;
+                tot += s_weq[w];
+            }
+            if (threadIdx.x == 0)
+                s_base[2] = tot ? atomicAdd(&segs[si].n_eq, (unsigned long long)tot) : 0ull;
+            __syncthreads();
+            eq_rank0 = (int)(s_base[2] & 1ull) + off;  // only the parity of the rank matters
+        }
         int32_t *ws = stage + warp * WK;
-        int nlt = 0, ngt = 0;  // warp-uniform running counts
+        int nlt = 0, ngt = 0, neq_run = 0;  // warp-uniform running counts
 #pragma unroll
         for (int j = 0; j < QS_IPT; ++j) {
-            const bool is_lt = k[j] < p, is_gt = k[j] > p;
+            bool is_lt = k[j] < p, is_gt = k[j] > p;
+            if constexpr (TWO_WAY) {
+                const bool is_eq = k[j] == p && j * QS_NT + (int)threadIdx.x < len;
+                const unsigned me = __ballot_sync(0xffffffffu, is_eq);
+                const int rank = eq_rank0 + neq_run + __popc(me & below);
+                is_lt = is_lt || (is_eq && (rank & 1) == 0);
+                is_gt = is_gt || (is_eq && (rank & 1) != 0);
+                neq_run += __popc(me);
+            }
             const unsigned ml = __ballot_sync(0xffffffffu, is_lt);
             const unsigned mg = __ballot_sync(0xffffffffu, is_gt);
             if (is_lt) ws[nlt + __popc(ml & below)] = k[j];
@@ -308,6 +347,7 @@ static QLayout qs_layout(size_t n) {
 size_t quick_workspace_bytes(size_t n) { return qs_layout(n).total; }
 
 void quick_set_max_levels(int64_t v) { qs_option_max_levels = v; }
+void quick_set_two_way(int v) { g_qs_two_way = v; }
 
 template <int L>
 static hs_status launch_small_t(int64_t nsmall, const QSmall *small, const QCounters *cctr,
@@ -404,7 +444,10 @@ hs_status quick_sort(int32_t *d_keys, size_t n_, hs_netset s, void *d_ws, size_t
         cudaError_t e = cudaMemsetAsync(nc, 0, sizeof(QCounters), st);
         if (e != cudaSuccess) return fail_cuda(e, "quick sort: counter reset");
         t = launch_begin(K_QS_PARTITION, st);
-        k_qs_partition<<<(unsigned)h.nchunks, QS_NT, 0, st>>>(cur, ccur, cc, q.caps, X, Y, X, Y);
+        if (g_qs_two_way)
+            k_qs_partition<true><<<(unsigned)h.nchunks, QS_NT, 0, st>>>(cur, ccur, cc, q.caps, X, Y, X, Y);
+        else
+            k_qs_partition<false><<<(unsigned)h.nchunks, QS_NT, 0, st>>>(cur, ccur, cc, q.caps, X, Y, X, Y);
         if ((r = launch_end(t)) != HS_OK) return r;
         t = launch_begin(K_QS_PLAN, st);
         k_qs_next<<<(unsigned)((h.nseg + 255) / 256), 256, 0, st>>>(cur, cc, nc, q.caps, tile, nxt,

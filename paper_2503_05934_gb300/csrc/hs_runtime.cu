@@ -317,6 +317,12 @@ hs_status hs_set_option(const char *name, int64_t value) {
         quick_set_max_levels(value);
         return HS_OK;
     }
+    if (std::strcmp(name, "quick_partition") == 0) {
+        if (value != 2 && value != 3)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: quick_partition must be 2 or 3");
+        quick_set_two_way(value == 2 ? 1 : 0);
+        return HS_OK;
+    }
     if (std::strcmp(name, "merge_kernel") == 0) {
         if (value != 0 && value != 1)
             return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_kernel must be 0 or 1");

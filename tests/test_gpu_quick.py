@@ -92,3 +92,22 @@ def test_large_quick_2p26(hs):
     out = t.cpu().numpy()
     del t
     check_sorted_permutation(a, out, samples=4)
+
+
+@pytest.mark.parametrize("netset", ["6To8", "3To5", "none"])
+def test_two_way_partition_option(hs, netset):
+    """Option quick_partition = 2 (Algorithm 2's 2-way form, equal keys
+    alternating sides): the oracle's Algorithm 2 (Hoare's scan) result on
+    every distribution, few distinct keys, all-equal keys and sizes around
+    the chunk and tile."""
+    hs.hs_set_option("quick_partition", 2)
+    try:
+        for n in [7937, 8192, 8193, 100_000, 1_000_003]:
+            for dist in g.DISTS:
+                a = g.keys(n, dist, 7000 + n)
+                assert np.array_equal(gpu_quick(hs, a, netset), oracle.quick_sort(a, netset)), (n, dist)
+        for a in [np.full(300_001, 7, np.int32), (g.random_i32(500_000, 3) % 4).astype(np.int32),
+                  np.concatenate([np.full(50_000, -1, np.int32), g.random_i32(50_000, 4)])]:
+            assert np.array_equal(gpu_quick(hs, a, netset), np.sort(a))
+    finally:
+        hs.hs_set_option("quick_partition", 3)
