@@ -128,6 +128,9 @@ HS_API hs_status hs_sort_i64(int64_t *d_keys, size_t n, hs_algo a, hs_netset s, 
 /* Host-buffer form, for callers whose keys live in host memory: copies
  * h_keys to the device, sorts them as hs_sort_i32 does, copies the result
  * back into h_keys and waits for `stream` before returning (synchronous).
+ * For merge sorts of 2^22 keys or more the copy in travels in 8 chunks on a
+ * second stream and each chunk is sorted as soon as it has arrived; merge
+ * levels over the sorted chunks finish the sort.
  * Pinned host memory makes the copies faster; pageable memory also works.
  *   d_ws: ws_bytes >= hs_sort_host_workspace_bytes(n, a); it holds the
  *   device copy of the keys followed by the sort workspace. */

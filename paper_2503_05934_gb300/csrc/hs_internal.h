@@ -80,6 +80,10 @@ hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, vo
                      size_t ws_bytes, cudaStream_t st);
 hs_status pairs_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, void *d_ws,
                      size_t ws_bytes, cudaStream_t st);
+// Host keys in and out, input copy overlapped with per-chunk sorts (merge
+// path; synchronous).  d_keys: device space for n keys; d_ws: merge workspace.
+hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n, hs_netset s,
+                                  void *d_ws, cudaStream_t st);
 int64_t pairs_tile(int L);
 size_t merge_workspace_bytes_i64(size_t n);
 hs_status merge_sort_i64(int64_t *d_keys, size_t n, hs_netset s, void *d_ws, size_t ws_bytes,

@@ -124,30 +124,17 @@ static hs_status launch_keys_level(const int32_t *kin, int32_t *kout, int64_t n,
     return launch_end(t);
 }
 
-hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, void *d_ws,
-                     size_t ws_bytes, cudaStream_t st) {
-    if (d_vals) return pairs_sort(d_keys, d_vals, n_, s, d_ws, ws_bytes, st);
-    const int64_t n = (int64_t)n_;
+// Sorts d_keys[0, n) with explicit scratch: kbuf (n keys), part (the
+// partition entries of n keys) and samp (every 32nd key of n keys, or null
+// for plain partition searches).  The result lands in d_keys.
+static hs_status merge_sort_with(int32_t *d_keys, int64_t n, hs_netset s, int32_t *kbuf,
+                                 int64_t *part, int32_t *samp, cudaStream_t st) {
     const int L = leaf_size(s);
     const int64_t T = keys_tile(L, n);
     int passes = 0;
     for (int64_t w = T; w < n; w *= 2) ++passes;
-
-    int32_t *kbuf = nullptr, *samp = nullptr;
-    int64_t *part = nullptr;
     const int vec = aligned(d_keys, 16) ? 1 : 0;
-    if (passes > 0) {
-        if (!d_ws || ws_bytes < merge_workspace_bytes(n_, 0))
-            return fail(HS_ERR_INVALID_ARG, "merge sort: workspace smaller than hs_sort_workspace_bytes");
-        if (!aligned(d_ws, 16)) return fail(HS_ERR_INVALID_ARG, "merge sort: workspace not 16-byte aligned");
-        char *p = static_cast<char *>(d_ws);
-        kbuf = reinterpret_cast<int32_t *>(p);
-        part = reinterpret_cast<int64_t *>(p + merge_ws_keys_bytes(n_));
-        // Samples feed the tiled levels' partition searches.
-        if (tiled_levels(n, vec) && g_merge_samples)
-            samp = reinterpret_cast<int32_t *>(p + merge_ws_keys_bytes(n_) + merge_ws_part_bytes(n_));
-    }
-
+    if (!tiled_levels(n, vec)) samp = nullptr;
     // Land the last level in the caller's array: with an even number of
     // global levels the block sort writes in place.
     int32_t *kcur = (passes % 2 == 0) ? d_keys : kbuf;
@@ -159,6 +146,88 @@ hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, v
         std::swap(kcur, kalt);
     }
     return HS_OK;
+}
+
+struct MergeScratch {
+    int32_t *kbuf, *samp;
+    int64_t *part;
+};
+
+static MergeScratch carve_merge_workspace(void *d_ws, size_t n) {
+    char *p = static_cast<char *>(d_ws);
+    MergeScratch m;
+    m.kbuf = reinterpret_cast<int32_t *>(p);
+    m.part = reinterpret_cast<int64_t *>(p + merge_ws_keys_bytes(n));
+    m.samp = g_merge_samples
+                 ? reinterpret_cast<int32_t *>(p + merge_ws_keys_bytes(n) + merge_ws_part_bytes(n))
+                 : nullptr;
+    return m;
+}
+
+hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, void *d_ws,
+                     size_t ws_bytes, cudaStream_t st) {
+    if (d_vals) return pairs_sort(d_keys, d_vals, n_, s, d_ws, ws_bytes, st);
+    const int64_t n = (int64_t)n_;
+    const int L = leaf_size(s);
+    if (n <= keys_tile(L, n)) return blocksort_launch(L, d_keys, d_keys, n, s, aligned(d_keys, 16) ? 1 : 0, st);
+    if (!d_ws || ws_bytes < merge_workspace_bytes(n_, 0))
+        return fail(HS_ERR_INVALID_ARG, "merge sort: workspace smaller than hs_sort_workspace_bytes");
+    if (!aligned(d_ws, 16)) return fail(HS_ERR_INVALID_ARG, "merge sort: workspace not 16-byte aligned");
+    const MergeScratch m = carve_merge_workspace(d_ws, n_);
+    return merge_sort_with(d_keys, n, s, m.kbuf, m.part, m.samp, st);
+}
+
+// Host buffer in, sorted host buffer out, with the input copy overlapped: the
+// keys travel in kChunks equal chunks on a copy stream; each chunk is merge-
+// sorted on `st` as soon as it has arrived (block sort and the levels inside
+// the chunk), while the next chunks are still in flight; global merge levels
+// of run width C, 2C, ... then merge the sorted chunks (the same levels a
+// whole-array sort runs), and the result is copied back.  d_keys is device
+// memory for n keys; d_ws the merge workspace for n keys.
+hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, hs_netset s,
+                                  void *d_ws, cudaStream_t st) {
+    constexpr int kChunks = 8;
+    const int64_t n = (int64_t)n_;
+    // Chunk length: a multiple of 1024 keys (16-byte aligned chunk starts and
+    // sample positions that are multiples of 32).
+    const int64_t C = ((n + kChunks - 1) / kChunks + 1023) / 1024 * 1024;
+    const int nch = (int)((n + C - 1) / C);
+    const MergeScratch m = carve_merge_workspace(d_ws, n_);
+    const int vec = aligned(d_keys, 16) ? 1 : 0;
+    int32_t *samp = tiled_levels(n, vec) ? m.samp : nullptr;
+
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[kChunks] = {};
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    hs_status r = HS_OK;
+    for (int c = 0; c < nch && e == cudaSuccess; ++c) e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming);
+    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
+        const int64_t b = c * C, len = std::min<int64_t>(C, n - b);
+        e = cudaMemcpyAsync(d_keys + b, h_keys + b, (size_t)len * sizeof(int32_t), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[c], cs);
+    }
+    if (e != cudaSuccess) r = fail_cuda(e, "host sort: chunked copy in");
+    for (int c = 0; c < nch && r == HS_OK; ++c) {
+        const int64_t b = c * C, len = std::min<int64_t>(C, n - b);
+        if ((e = cudaStreamWaitEvent(st, ev[c], 0)) != cudaSuccess) {
+            r = fail_cuda(e, "host sort: wait for a chunk");
+            break;
+        }
+        r = merge_sort_with(d_keys + b, len, s, m.kbuf + b, m.part, samp ? samp + b / 32 : nullptr, st);
+    }
+    int32_t *kcur = d_keys, *kalt = m.kbuf;
+    for (int64_t w = C; w < n && r == HS_OK; w *= 2) {
+        r = launch_keys_level(kcur, kalt, n, w, m.part, samp, vec, st);
+        std::swap(kcur, kalt);
+    }
+    if (r == HS_OK && (e = cudaMemcpyAsync(h_keys, kcur, n_ * sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        r = fail_cuda(e, "host sort: copy out");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess && r == HS_OK) r = fail_cuda(e, "host sort: synchronize");
+    if (cs && (e = cudaStreamSynchronize(cs)) != cudaSuccess && r == HS_OK) r = fail_cuda(e, "host sort: copy stream");
+    for (int c = 0; c < nch; ++c)
+        if (ev[c]) cudaEventDestroy(ev[c]);
+    if (cs) cudaStreamDestroy(cs);
+    return r;
 }
 
 }  // namespace hs

@@ -294,6 +294,9 @@ hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, vo
     cudaStream_t cs = (cudaStream_t)stream;
     int32_t *d_keys = static_cast<int32_t *>(d_ws);
     size_t kb = align_up(n * sizeof(int32_t), 256);
+    // Large merge sorts overlap the copy in with per-chunk sorts.
+    if (a == HS_ALGO_MERGE && n >= ((size_t)1 << 22))
+        return merge_sort_host_chunked(h_keys, d_keys, n, s, static_cast<char *>(d_ws) + kb, cs);
     cudaError_t e = cudaMemcpyAsync(d_keys, h_keys, n * sizeof(int32_t), cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return fail_cuda(e, "hs_sort_i32_host: host-to-device copy");
     st = hs_sort_i32(d_keys, n, a, s, static_cast<char *>(d_ws) + kb, ws_bytes - kb, stream);

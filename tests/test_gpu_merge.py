@@ -185,6 +185,22 @@ def test_host_buffer_entry(hs):
     assert np.array_equal(h.numpy(), oracle.merge_sort(a, "6To8"))
 
 
+@pytest.mark.parametrize("n", [1 << 22, (1 << 22) + 12_345, 5 * (1 << 22) + 2, 3 * (1 << 23)])
+def test_host_buffer_entry_chunked(hs, n):
+    """Host sorts of 2^22 keys or more copy in by chunks and sort each chunk
+    on arrival, then merge the chunks: the result must equal the oracle's
+    order statistics and numpy's sort (pinned and pageable buffers)."""
+    import torch
+    a = g.random_i32(n, 40 + n)
+    h = torch.from_numpy(a.copy()).pin_memory()
+    hs.hs_sort_i32_host(h, "merge", "6To8")
+    want = np.sort(a)
+    assert np.array_equal(h.numpy(), want)
+    p = torch.from_numpy(a.copy())  # pageable
+    hs.hs_sort_i32_host(p, "merge", "3To5")
+    assert np.array_equal(p.numpy(), want)
+
+
 def test_workspace_reuse_and_launch_count(hs):
     import torch
     n = 1 << 20
