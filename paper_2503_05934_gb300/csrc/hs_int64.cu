@@ -28,7 +28,7 @@ struct BlockSort64 {
 
 template <int NT, int L>
 __global__ void __launch_bounds__(NT)
-    k_blocksort64(const K64 *kin, K64 *kout, int64_t n, uint32_t netset, K64 *samp) {
+    k_blocksort64(const K64 *kin, K64 *kout, int64_t n, uint32_t netset, K64 *samp, int vec) {
     using C = BlockSort64<NT, L>;
     constexpr int EO = C::EO, P = C::P, T = C::T;
     static_assert(T % kSampleStride == 0, "tiles start on sample positions");
@@ -37,7 +37,12 @@ __global__ void __launch_bounds__(NT)
     const int64_t base = (int64_t)blockIdx.x * T;
     const int cnt = (int)((n - base) < T ? (n - base) : T);
     const K64 *src = kin + base;
-    for (int i = threadIdx.x; i < T; i += NT) s64[i] = i < cnt ? ld_stream(src + i) : word_max<K64>();
+    if (vec && cnt == T) {  // T is even: 16-byte loads of two keys
+        const int4 *s4 = reinterpret_cast<const int4 *>(src);
+        for (int q = threadIdx.x; q < T / 2; q += NT) reinterpret_cast<int4 *>(s64)[q] = ld_stream(s4 + q);
+    } else {
+        for (int i = threadIdx.x; i < T; i += NT) s64[i] = i < cnt ? ld_stream(src + i) : word_max<K64>();
+    }
     __syncthreads();
     const int my0 = threadIdx.x * EO;
     K64 k[EO];
@@ -110,11 +115,13 @@ template <int NT, int EO>
 struct TileMerge64 {
     static constexpr int P = pow2_at_least(EO);
     static constexpr int TO = NT * EO;
-    static constexpr int REG = TO + P;  // A and B back to back + window slack
+    // A's and B's 16-byte covers back to back (at most one extra key at each
+    // end of each) + the window slack.
+    static constexpr int REG = TO + 4 + P;
     static constexpr int SMEM_BYTES = REG * 8;
 };
 
-template <int NT, int EO>
+template <int NT, int EO, bool VEC>
 __global__ void __launch_bounds__(NT)
     k_merge_tile64(const K64 *in, K64 *out, int64_t n, int64_t w, const int64_t *part, int tpg,
                    K64 *samp) {
@@ -132,10 +139,28 @@ __global__ void __launch_bounds__(NT)
     const int na = (int)(a1 - a0);
     const int tot = (int)(o1 - o0);
     const int nb = tot - na;
-    const K64 *gA = in + m.gs + a0, *gB = in + m.gs + w + (o0 - a0);
-    for (int q = threadIdx.x; q < tot; q += NT) s64[q] = ld_stream(q < na ? gA + q : gB + (q - na));
-    __syncthreads();
-    const K64 *A = s64, *B = s64 + na;
+    const K64 *A, *B;
+    if constexpr (VEC) {
+        // 16-byte buffers: stage the 16-byte covers of A and B by cp.async.
+        const int64_t ga = m.gs + a0, gb = m.gs + w + (o0 - a0);
+        const int64_t ca = ga & ~int64_t(1), cb = gb & ~int64_t(1);
+        const int nca = (int)(((ga + na + 1) & ~int64_t(1)) - ca) / 2;
+        const int ncb = (int)(((gb + nb + 1) & ~int64_t(1)) - cb) / 2;
+        for (int q = threadIdx.x; q < nca + ncb; q += NT) {
+            if (q < nca) cp_async16(s64 + 2 * q, in + ca + 2 * q);
+            else cp_async16(s64 + 2 * q, in + cb + 2 * (q - nca));
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        A = s64 + (int)(ga - ca);
+        B = s64 + 2 * nca + (int)(gb - cb);
+    } else {
+        const K64 *gA = in + m.gs + a0, *gB = in + m.gs + w + (o0 - a0);
+        for (int q = threadIdx.x; q < tot; q += NT) s64[q] = ld_stream(q < na ? gA + q : gB + (q - na));
+        __syncthreads();
+        A = s64;
+        B = s64 + na;
+    }
 
     const int diag = threadIdx.x * EO;
     const int lane = threadIdx.x & 31;
@@ -165,9 +190,21 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
     K64 *dst = out + m.gs + o0;
-    for (int i = threadIdx.x; i < tot; i += NT) {
+    int i0 = 0;
+    if constexpr (VEC) {  // gs and o0 are even: 16-byte aligned output
+        const int n2 = tot >> 1;
+        for (int q = threadIdx.x; q < n2; q += NT) {
+            const int4 v = *reinterpret_cast<const int4 *>(s64 + 2 * q);
+            st_stream(reinterpret_cast<int4 *>(dst) + q, v);
+        }
+        i0 = 2 * n2;
+        if (samp)
+            for (int q = threadIdx.x * kSampleStride; q < tot; q += NT * kSampleStride)
+                samp[(m.gs + o0 + q) / kSampleStride] = s64[q];
+    }
+    for (int i = i0 + threadIdx.x; i < tot; i += NT) {
         st_stream(dst + i, s64[i]);
-        if (samp && i % kSampleStride == 0) samp[(m.gs + o0 + i) / kSampleStride] = s64[i];
+        if (!VEC && samp && i % kSampleStride == 0) samp[(m.gs + o0 + i) / kSampleStride] = s64[i];
     }
 }
 
@@ -185,12 +222,13 @@ size_t merge_workspace_bytes_i64(size_t n) {
 template <int L>
 static hs_status launch_blocksort64_t(const K64 *kin, K64 *kout, int64_t n, hs_netset s, K64 *samp,
                                       cudaStream_t st) {
+    const int vec = aligned(kin, 16) ? 1 : 0;
     using C = BlockSort64<B64_NT, L>;
     auto kern = k_blocksort64<B64_NT, L>;
     hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
     if (r != HS_OK) return r;
     LaunchToken t = launch_begin(K_BLOCKSORT_KEYS, st);
-    kern<<<(unsigned)((n + C::T - 1) / C::T), B64_NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, samp);
+    kern<<<(unsigned)((n + C::T - 1) / C::T), B64_NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, samp, vec);
     return launch_end(t);
 }
 
@@ -234,7 +272,8 @@ hs_status merge_sort_i64(int64_t *d_keys, size_t n_, hs_netset s, void *d_ws, si
     if (r != HS_OK) return r;
     using C = TileMerge64<M64_NT, M64_EO>;
     static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
-    auto kern = k_merge_tile64<M64_NT, M64_EO>;
+    const bool vec = aligned(d_keys, 16) && (!kbuf || aligned(kbuf, 16)) && (n % 2) == 0;
+    auto kern = vec ? k_merge_tile64<M64_NT, M64_EO, true> : k_merge_tile64<M64_NT, M64_EO, false>;
     for (int64_t w = T; w < n; w *= 2) {
         const LevelTiles lt = level_tiles(n, w, C::TO);
         LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
