@@ -631,7 +631,17 @@ def run_batched(hs, torch, dev, stream, args):
     assert torch.equal(work, batched), "per-array result differs from batched result"
     graph.destroy()
     del work, pristine, batched, offs, d
+    # Roofline bytes: one read and one write per key per pass, 1 + the merge
+    # levels above the plan's tile for each segment (two-way merges).
+    pd = plan.as_dict()
+    leaf = max((k for k in range(3, 9) if (pd["netset"] >> k) & 1), default=1)
+    tile = 256 * (4 * leaf - 1) if pd["block_threads"] == 256 else 512 * (2 * leaf - 1)
+    sizes = np.diff(off)
+    levels = np.where(sizes > tile, np.ceil(np.log2(np.maximum(sizes, 1) / tile)), 0)
+    rbytes = float(np.sum(8.0 * sizes * (1 + levels)))
+    peak, _ = measured_peak()
     return {"value": n / (ms / 1e3), "unit": "keys/s", "ms_per_batch": ms,
+            "roofline_bytes": rbytes, "frac_of_measured": rbytes / (ms / 1e3) / (peak * 1e9),
             "plain_value": n / plain_s, "plain_s": plain_s,
             "speedup_vs_plain": plain_s / (ms / 1e3), "keys": int(n), "segments": 200_000,
             "plan": plan.as_dict(), "autotune_best_ms": tune_ms,
