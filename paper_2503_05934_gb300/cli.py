@@ -4,10 +4,13 @@ prints the time per sort.
     python -m paper_2503_05934_gb300.cli --what keys --log2n 26 --dist uniform
     python -m paper_2503_05934_gb300.cli --what pairs --log2n 25 --reps 3
     python -m paper_2503_05934_gb300.cli --what quick --dist nearly --option quick_max_levels=64
+    python -m paper_2503_05934_gb300.cli --what batched --segments 20000
 
 Keys are int32 from the seeded generators of ``hs_inputs`` (uniform over the
 int32 range, sorted, or nearly sorted); pairs carry keys from 2^16 distinct
-values and values = original index.  Every run restores the input from a
+values and values = original index; batched runs sort --segments arrays of
+log-uniform sizes in [3, 65536] (mixed distributions) in one launch with the
+default plan.  Every run restores the input from a
 pristine device copy (untimed), times the sort with CUDA events on the
 sorting stream, and checks that the output is sorted (pairs: and stable).
 """
@@ -25,7 +28,8 @@ if ROOT not in sys.path:
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--what", choices=["keys", "quick", "pairs"], default="keys")
+    ap.add_argument("--what", choices=["keys", "quick", "pairs", "batched"], default="keys")
+    ap.add_argument("--segments", type=int, default=20000)
     ap.add_argument("--log2n", type=int, default=24)
     ap.add_argument("--dist", choices=["uniform", "sorted", "nearly"], default="uniform")
     ap.add_argument("--netset", default="6To8")
@@ -52,6 +56,14 @@ def main(argv=None) -> int:
 
         def run(bufs):
             hs.hs_sort_pairs_i32(bufs[0], bufs[1], "merge", args.netset, ws=ws, stream=st)
+    elif args.what == "batched":
+        keys, off, _ = hs_inputs.segmented(args.segments, args.seed)
+        n = keys.size
+        src = [torch.from_numpy(keys).to(dev)]
+        offs = torch.from_numpy(off).to(dev)
+
+        def run(bufs):
+            hs.hs_segsort_i32(bufs[0], offs, "merge", args.netset, stream=st)
     else:
         dist = "random" if args.dist == "uniform" else args.dist
         src = [torch.from_numpy(hs_inputs.keys(n, dist, args.seed)).to(dev)]
@@ -74,7 +86,12 @@ def main(argv=None) -> int:
         times.append(e0.elapsed_time(e1))
     hs.hs_device_check()
     keys = work[0]
-    ok = bool((keys[1:] >= keys[:-1]).all().item())
+    if args.what == "batched":
+        d = keys[1:] >= keys[:-1]
+        d[offs[1:-1] - 1] = True  # segment boundaries
+        ok = bool(d.all().item())
+    else:
+        ok = bool((keys[1:] >= keys[:-1]).all().item())
     if args.what == "pairs":
         same = keys[1:] == keys[:-1]
         ok = ok and bool(((work[1][1:] > work[1][:-1]) | ~same).all().item())

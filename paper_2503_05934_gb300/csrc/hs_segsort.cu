@@ -28,53 +28,62 @@ constexpr int SPLIT_CAP = 256;  // merge-level chunk boundaries searched per bat
 
 HS_DEV bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// The E smallest keys of A[0..ra) and B[0..rb) (windows of at most E keys each,
-// both sorted), ascending, as the lower half of a P-wide bitonic merge.
-template <int E, int P>
-HS_DEV void window_merge(const int32_t *A, int ra, const int32_t *B, int rb, int32_t (&o)[P]) {
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-        const int j = P - 1 - i;
-        const int32_t a = (i < E && i < ra) ? A[i] : kKeyMax;
-        const int32_t b = (j < E && j < rb) ? B[j] : kKeyMax;
-        o[i] = hs_min(a, b);
+// Merge-path split by one warp (32-ary search): the smallest i in [lo, hi]
+// with A[i] > B[diag - 1 - i] (hi when there is none), the number of A
+// elements among the first diag outputs of the stable merge.  Each round the
+// lanes test 32 evenly spaced candidates (two independent loads each) and the
+// range shrinks 32-fold, so a 65536-key range takes about four dependent load
+// rounds instead of sixteen.  The final round starts with fewer than 32
+// candidates left, so the last lane always tests a position >= hi and the
+// ballot is never empty.  Every lane returns the result.
+HS_DEV int64_t warp_merge_path(const int32_t *A, const int32_t *B, int64_t diag, int64_t lo,
+                               int64_t hi, int lane) {
+    while (hi - lo >= 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t q = lo + (int64_t)(lane + 1) * step;  // candidate; q >= hi counts as true
+        const bool t = q >= hi || A[q] > B[diag - 1 - q];
+        const unsigned m = __ballot_sync(0xffffffffu, t);
+        const int f = __ffs(m) - 1;  // some lane holds q >= hi, so m != 0
+        const int64_t nlo = f == 0 ? lo : lo + (int64_t)f * step + 1;
+        hi = hs_min(hi, lo + (int64_t)(f + 1) * step);
+        lo = nlo;
     }
-    bitonic_half_clean<P>(o);
+    const int64_t q = lo + lane;
+    const bool t = q >= hi || A[q] > B[diag - 1 - q];
+    const unsigned m = __ballot_sync(0xffffffffu, t);
+    return lo + (__ffs(m) - 1);
 }
 
 // One merge level over a single segment by one CTA: runs of w in src are
-// merged into runs of 2w in dst.  Output chunks of T keys; their merge-path
-// splits are searched in parallel (one thread per chunk boundary), then each
-// chunk is staged in shared memory and merged with per-thread windows.
+// merged into runs of 2w in dst.  Output chunks of T keys: their merge-path
+// splits are found by one warp per chunk boundary; each chunk is then staged
+// in shared memory, each thread merges exactly its own EO outputs (exact
+// window, end split from the next lane), and the outputs leave through shared
+// memory as coalesced stores.
 template <int NT, int L, int LV>
 HS_DEV void cta_merge_level(const int32_t *src, int32_t *dst, int64_t n, int64_t w, int32_t *s,
                             int64_t *split) {
     using C = BlockSort3<NT, L, LV>;
-    constexpr int T = C::T, E = C::EO, P = C::P;
+    constexpr int T = C::T, EO = C::EO, P = C::P;
     const int64_t span = 2 * w;
     const int64_t ngroups = (n + span - 1) / span;
     const int64_t tpg = (span + T - 1) / T;
     const int64_t last = n - (ngroups - 1) * span;
     const int64_t nchunks = (ngroups - 1) * tpg + (last + T - 1) / T;
-    const bool vec = aligned16(dst);
-
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int *wsplit = s + C::T + C::P + 32;
     for (int64_t c0 = 0; c0 < nchunks; c0 += SPLIT_CAP) {
         const int64_t c1 = std::min<int64_t>(nchunks, c0 + SPLIT_CAP);
         // Splits of boundaries c0 .. c1 (c1 may open the next batch).
-        for (int64_t c = c0 + threadIdx.x; c <= c1 && c < nchunks; c += NT) {
+        for (int64_t c = c0 + warp; c <= c1 && c < nchunks; c += NT / 32) {
             const int64_t g = c / tpg, t = c - g * tpg;
             const MergeGeom m = merge_geom(g, n, w);
             int64_t diag = t * T;
             if (diag > m.alen + m.blen) diag = m.alen + m.blen;
-            const int32_t *A = src + m.gs, *B = src + m.gs + w;
-            int64_t lo = diag > m.blen ? diag - m.blen : 0;
-            int64_t hi = diag < m.alen ? diag : m.alen;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
-                else hi = mid;
-            }
-            split[c - c0] = lo;
+            const int64_t lo = diag > m.blen ? diag - m.blen : 0;
+            const int64_t hi = diag < m.alen ? diag : m.alen;
+            const int64_t r = warp_merge_path(src + m.gs, src + m.gs + w, diag, lo, hi, lane);
+            if (lane == 0) split[c - c0] = r;
         }
         __syncthreads();
         for (int64_t c = c0; c < c1; ++c) {
@@ -87,35 +96,45 @@ HS_DEV void cta_merge_level(const int32_t *src, int32_t *dst, int64_t n, int64_t
             const int64_t a1 = (o1 == glen) ? m.alen : split[c + 1 - c0];
             const int na = (int)(a1 - a0);
             const int tot = (int)(o1 - o0);
-            const int32_t *A = src + m.gs + a0;
-            const int32_t *B = src + m.gs + w + (o0 - a0) - na;  // B[i - na] for i >= na
-            for (int i = threadIdx.x; i < tot; i += NT) s[i] = i < na ? A[i] : B[i];
+            const int nb = tot - na;
+            const int32_t *gA = src + m.gs + a0, *gB = src + m.gs + w + (o0 - a0);
+            for (int i = threadIdx.x; i < tot; i += NT) s[i] = i < na ? gA[i] : gB[i - na];
             __syncthreads();
-            const int diag = threadIdx.x * E;
-            if (diag < tot) {
-                const int nb = tot - na;
-                const int ai = merge_path2(s, na, s + na, nb, diag);
-                const int bi = diag - ai;
-                int32_t o[P];
-                window_merge<E, P>(s + ai, na - ai, s + na + bi, nb - bi, o);
-                int32_t *out = dst + m.gs + o0 + diag;
-                if constexpr (E % 4 == 0) {
-                    if (vec && diag + E <= tot) {
-#pragma unroll
-                        for (int q = 0; q < E / 4; ++q)
-                            *reinterpret_cast<int4 *>(out + 4 * q) =
-                                make_int4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < E; ++k)
-                            if (diag + k < tot) out[k] = o[k];
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < E; ++k)
-                        if (diag + k < tot) out[k] = o[k];
-                }
+            const int32_t *A = s, *B = s + na;
+            const int diag = threadIdx.x * EO;
+            const int dcl = diag < tot ? diag : tot;
+            int lo = dcl > nb ? dcl - nb : 0, hi = dcl < na ? dcl : na;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (A[mid] <= B[dcl - 1 - mid]) lo = mid + 1;
+                else hi = mid;
             }
+            int end = __shfl_down_sync(0xffffffffu, lo, 1);
+            if (lane == 0) wsplit[warp] = lo;
+            if (threadIdx.x == 0) wsplit[NT / 32] = na;
+            __syncthreads();
+            const int dend = (diag + EO) < tot ? (diag + EO) : tot;
+            if (lane == 31) end = wsplit[warp + 1];
+            if (dend == tot) end = na;
+            const int cnt = dend - dcl;
+            int32_t x[P];
+            if (cnt > 0) exact_window_merge<EO, P>(A, lo, B, dcl - lo, end - lo, cnt, x);
+            __syncthreads();
+            if (cnt > 0) {
+#pragma unroll
+                for (int k = 0; k < EO; ++k)
+                    if (k < cnt) s[diag + k] = x[k];
+            }
+            __syncthreads();
+            int32_t *out = dst + m.gs + o0;
+            // Plain (cached) stores: the next level reads these keys back from L2.
+            int start = 0;
+            if (aligned16(out)) {
+                for (int q = threadIdx.x; q < (tot >> 2); q += NT)
+                    reinterpret_cast<int4 *>(out)[q] = *reinterpret_cast<const int4 *>(s + 4 * q);
+                start = tot & ~3;
+            }
+            for (int i = start + threadIdx.x; i < tot; i += NT) out[i] = s[i];
             __syncthreads();
         }
     }
