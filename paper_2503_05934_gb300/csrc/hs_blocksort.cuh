@@ -108,10 +108,18 @@ HS_DEV void block_merge_levels(K *s, int *wsplit, K (&k)[EO], int cnt) {
     constexpr int T = NT * EO;
     const int my0 = threadIdx.x * EO;
     for (int w = EO; w < T && w < cnt; w *= 2) {
-        __syncthreads();
+        // While a group of two runs lies inside one warp's slots, the warp
+        // only reads what its own lanes wrote: a warp barrier suffices.  The
+        // first stores still wait for the whole block, because the caller may
+        // have staged the tile in this buffer in another layout (the pair
+        // sort reads int32 keys from slots the 64-bit words then overwrite).
+        const bool in_warp = 2 * w <= 32 * EO;
+        if (in_warp && w != EO) __syncwarp();
+        else __syncthreads();
 #pragma unroll
         for (int j = 0; j < EO; ++j) s[my0 + j] = k[j];
-        __syncthreads();
+        if (in_warp) __syncwarp();
+        else __syncthreads();
         const int gs = (my0 / (2 * w)) * (2 * w);
         const int diag = my0 - gs;
         const int alen = hs_min(w, T - gs);
