@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -204,6 +205,31 @@ def sort_passes(n: int, tile: int) -> int:
     return p
 
 
+def host_cpu_info() -> dict:
+    """The host the CPU baseline ran on: architecture, logical cores, model."""
+    model = None
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"machine": platform.machine(), "nproc": os.cpu_count(), "model": model}
+
+
+def library_sort_rate(sample: np.ndarray, seconds: float = 2.0) -> float:
+    """numpy's library sort on the same sample, one core: context for the
+    oracle's rate (a tuned library sort against the paper's algorithms)."""
+    done, t_total = 0, 0.0
+    while done == 0 or t_total < seconds:
+        t0 = time.perf_counter()
+        np.sort(sample)
+        t_total += time.perf_counter() - t0
+        done += sample.size
+    return done / t_total
+
+
 def cpu_oracle_rate(sample: np.ndarray, seconds: float, netset: str):
     import oracle
     done, t_total, reps = 0, 0.0, 0
@@ -346,6 +372,8 @@ def run_ours(args):
         "frac": achieved / peak if achieved else None, "traffic": traffic,
         "algorithmic_bytes_per_launch": alg_bytes,
         "launch_ms": avg_mk_s * 1e3 if avg_mk_s else None,
+        # ncu DRAM bytes over the live launch time: bandwidth actually drawn
+        "traffic_gbs": traffic / avg_mk_s / 1e9 if traffic and avg_mk_s else None,
     }
     tile = int(hs.lib().hs_keys_tile(hs.netset_mask(args.netset), n))
     passes = sort_passes(n, tile) if tile else None
@@ -411,7 +439,9 @@ def run_ours(args):
         line["cpu_baseline"] = {
             "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first 2^22 keys of the workload, oracle Algorithm 1 ({args.netset}), "
-                      f"{reps} full sorts on one host core"}
+                      f"{reps} full sorts on one host core",
+            "host": host_cpu_info(),
+            "library_sort_value": library_sort_rate(host[:sample_n].copy())}
 
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -630,7 +660,17 @@ def run_batched(hs, torch, dev, stream, args):
     plain_s = time.perf_counter() - t0
     assert torch.equal(work, batched), "per-array result differs from batched result"
     graph.destroy()
-    del work, pristine, batched, offs, d
+    # The seeded prefix of the same size sequence that first reaches 2^28
+    # keys (the total the workload's description names), same plan.
+    kp = int(np.searchsorted(off, 1 << 28))
+    np_keys = int(off[kp])
+    pw, po = work[:np_keys], offs[:kp + 1]
+    pgraph = hs.hs_segsort_capture(pw, po, plan)
+    pms = time_sorts(torch, stream, max(3, args.steps // 4), 2,
+                     lambda: pw.copy_(pristine[:np_keys]), lambda: pgraph.launch(stream))
+    pgraph.destroy()
+    assert torch.equal(pw, batched[:np_keys]), "prefix result differs from the full batch"
+    del work, pristine, batched, offs, d, pw, po
     # Roofline bytes: one read and one write per key per pass, 1 + the merge
     # levels above the plan's tile for each segment (two-way merges).
     pd = plan.as_dict()
@@ -646,6 +686,8 @@ def run_batched(hs, torch, dev, stream, args):
             "speedup_vs_plain": plain_s / (ms / 1e3), "keys": int(n), "segments": 200_000,
             "plan": plan.as_dict(), "autotune_best_ms": tune_ms,
             "gpu_launches_per_batch": launches / (max(3, args.steps // 4) + 2),
+            "prefix_2p28": {"segments": kp, "keys": np_keys, "ms_per_batch": pms,
+                            "value": np_keys / (pms / 1e3), "unit": "keys/s"},
             "workload": "200,000 int32 arrays, sizes log-uniform in [3, 65536], "
                         "1/3 random, 1/3 sorted, 1/3 nearly sorted; CUDA-graph replay of "
                         "one persistent launch; plain = one hs_sort_i32 per array"}

@@ -187,7 +187,11 @@ HS_DEV void block_sort_tile3(const int32_t *kin, int32_t *kout, int cnt, uint32_
         for (int q = threadIdx.x; q < T / 4; q += NT)
             *reinterpret_cast<int4 *>(s + 4 * q) = ld_stream(s4 + q);
     } else {
-        for (int i = threadIdx.x; i < T; i += NT) s[i] = i < cnt ? kin[i] : kKeyMax;
+        for (int i = threadIdx.x; i < T; i += NT) {
+            if (i < cnt) cp_async4(s + i, kin + i);
+            else s[i] = kKeyMax;
+        }
+        cp_async_wait_all();
     }
     __syncthreads();
 

@@ -154,6 +154,14 @@ HS_DEV void cp_async16(void *smem_dst, const void *gmem_src) {
                  "l"(gmem_src)
                  : "memory");
 }
+// Four-byte asynchronous copy (any 4-byte aligned address): a loop of these
+// keeps every load of a staged tile in flight at once, where a loop of plain
+// load-then-store waits out one memory latency per iteration.
+HS_DEV void cp_async4(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
 HS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------

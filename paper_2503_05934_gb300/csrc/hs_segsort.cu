@@ -98,7 +98,8 @@ HS_DEV void cta_merge_level(const int32_t *src, int32_t *dst, int64_t n, int64_t
             const int tot = (int)(o1 - o0);
             const int nb = tot - na;
             const int32_t *gA = src + m.gs + a0, *gB = src + m.gs + w + (o0 - a0);
-            for (int i = threadIdx.x; i < tot; i += NT) s[i] = i < na ? gA[i] : gB[i - na];
+            for (int i = threadIdx.x; i < tot; i += NT) cp_async4(s + i, i < na ? gA + i : gB + (i - na));
+            cp_async_wait_all();
             __syncthreads();
             const int32_t *A = s, *B = s + na;
             const int diag = threadIdx.x * EO;
@@ -170,18 +171,23 @@ HS_DEV void sort_segment(const SegDesc &d, uint32_t netset, int32_t *s, int64_t 
 }
 
 template <int NT, int L, int LV>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 2)
     k_seg_sort(const SegDesc *descs, int64_t ndesc, unsigned long long *head, uint32_t netset) {
     extern __shared__ __align__(16) int32_t smem[];
     __shared__ int64_t s_split[SPLIT_CAP + 1];
-    __shared__ unsigned long long s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(head, 1ull);
-        __syncthreads();
-        const unsigned long long item = s_item;
+    __shared__ unsigned long long s_item[2];
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(head, 1ull);
+    __syncthreads();
+    for (int it = 0;; it ^= 1) {
+        const unsigned long long item = s_item[it];
         if (item >= (unsigned long long)ndesc) break;
+        // The next item is claimed now; the atomic's round trip overlaps
+        // this segment's sort and its result is only consumed at the end.
+        unsigned long long next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(head, 1ull);
         const SegDesc d = descs[item];
         sort_segment<NT, L, LV>(d, netset, smem, s_split);
+        if (threadIdx.x == 0) s_item[it ^ 1] = next;
         __syncthreads();
     }
 }
