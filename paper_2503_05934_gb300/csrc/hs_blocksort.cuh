@@ -103,10 +103,16 @@ HS_DEV void sort_thread_leaves(K *k, int avail, uint32_t netset) {
 // unpadded.  NT need not be a power of two: the last group of a level may
 // hold a short B run or none (then its keys stay as they are).  On return k
 // holds the thread's EO keys of the sorted tile.
-template <int NT, int EO, int P, bool SKIP, class K>
+//
+// WARP: the tile belongs to one warp alone (NT = 32, s is that warp's own
+// buffer), every barrier is a warp barrier, and other warps of the block may
+// be sorting other tiles meanwhile.
+template <int NT, int EO, int P, bool SKIP, class K, bool WARP = false>
 HS_DEV void block_merge_levels(K *s, int *wsplit, K (&k)[EO], int cnt) {
+    static_assert(!WARP || NT == 32, "a warp-owned tile has 32 threads");
     constexpr int T = NT * EO;
-    const int my0 = threadIdx.x * EO;
+    const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    const int my0 = tid * EO;
     for (int w = EO; w < T && w < cnt; w *= 2) {
         // While a group of two runs lies inside one warp's slots, the warp
         // only reads what its own lanes wrote: a warp barrier suffices.  The
@@ -114,11 +120,11 @@ HS_DEV void block_merge_levels(K *s, int *wsplit, K (&k)[EO], int cnt) {
         // have staged the tile in this buffer in another layout (the pair
         // sort reads int32 keys from slots the 64-bit words then overwrite).
         const bool in_warp = 2 * w <= 32 * EO;
-        if (in_warp && w != EO) __syncwarp();
+        if (WARP || (in_warp && w != EO)) __syncwarp();
         else __syncthreads();
 #pragma unroll
         for (int j = 0; j < EO; ++j) s[my0 + j] = k[j];
-        if (in_warp) __syncwarp();
+        if (WARP || in_warp) __syncwarp();
         else __syncthreads();
         const int gs = (my0 / (2 * w)) * (2 * w);
         const int diag = my0 - gs;
@@ -142,7 +148,7 @@ HS_DEV void block_merge_levels(K *s, int *wsplit, K (&k)[EO], int cnt) {
         int end = __shfl_down_sync(0xffffffffu, lo, 1);
         const int dend = diag + EO;  // runs and groups are multiples of EO
         const bool last = dend == alen + blen;
-        if (2 * w > 32 * EO) {  // groups span warps: exchange warp-boundary splits
+        if (!WARP && 2 * w > 32 * EO) {  // groups span warps: exchange warp-boundary splits
             if ((threadIdx.x & 31) == 0) wsplit[threadIdx.x >> 5] = lo;
             __syncthreads();
             if ((threadIdx.x & 31) == 31 && !last) end = wsplit[(threadIdx.x >> 5) + 1];

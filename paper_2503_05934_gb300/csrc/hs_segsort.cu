@@ -170,45 +170,141 @@ HS_DEV void sort_segment(const SegDesc &d, uint32_t netset, int32_t *s, int64_t 
     }
 }
 
+// A segment of at most one warp tile (32 * EO keys) sorted by one warp alone:
+// the block sort's leaves and merge levels with warp barriers only, in the
+// warp's own part of shared memory, so a CTA keeps one small segment in
+// flight per warp instead of one per CTA.
+template <int L, int LV>
+HS_DEV void warp_sort_segment(int32_t *keys, int n, uint32_t netset, int32_t *s) {
+    using W = BlockSort3<32, L, LV>;
+    constexpr int EO = W::EO, P = W::P, T = W::T;
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < T; i += 32) {
+        if (i < n) cp_async4(s + i, keys + i);
+        else s[i] = kKeyMax;
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    const int my0 = lane * EO;
+    int32_t k[EO];
+#pragma unroll
+    for (int j = 0; j < EO; ++j) k[j] = s[my0 + j];
+    if (my0 < n) sort_thread_leaves<L, LV, P>(k, n - my0, netset);
+    block_merge_levels<32, EO, P, true, int32_t, true>(s, nullptr, k, n);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < EO; ++j) s[my0 + j] = k[j];
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) keys[i] = s[i];
+    __syncwarp();
+}
+
+// Queue counters of one launch (zeroed before the classify step):
+// [0] large-list head, [1] small-list head, [2] large count, [3] small count.
+constexpr int kCtrlWords = 4;
+
+// Dynamic shared memory of the batched kernel: the block tile, or one warp
+// tile per warp, whichever is larger.
+template <int NT, int L, int LV>
+constexpr int seg_smem_bytes() {
+    constexpr int blk = BlockSort3<NT, L, LV>::SMEM_BYTES;
+    constexpr int wrp = (NT / 32) * BlockSort3<32, L, LV>::SMEM_BYTES;
+    return blk > wrp ? blk : wrp;
+}
+
+// Persistent sort over the classified descriptors: CTAs first take the large
+// list (cdesc[0, nlarge), one segment per CTA), then each warp takes small
+// segments from the back of the array (cdesc[ndesc - 1 - j]) until both
+// lists are drained.  Large segments first also balances the load: the
+// short items fill the gaps at the end.
 template <int NT, int L, int LV>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 2)
-    k_seg_sort(const SegDesc *descs, int64_t ndesc, unsigned long long *head, uint32_t netset) {
+    k_seg_sort(const SegDesc *cdesc, int64_t ndesc, unsigned long long *ctrl, uint32_t netset) {
     extern __shared__ __align__(16) int32_t smem[];
     __shared__ int64_t s_split[SPLIT_CAP + 1];
     __shared__ unsigned long long s_item[2];
-    if (threadIdx.x == 0) s_item[0] = atomicAdd(head, 1ull);
+    const unsigned long long nlarge = ctrl[2], nsmall = ctrl[3];
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(&ctrl[0], 1ull);
     __syncthreads();
     for (int it = 0;; it ^= 1) {
         const unsigned long long item = s_item[it];
-        if (item >= (unsigned long long)ndesc) break;
+        if (item >= nlarge) break;
         // The next item is claimed now; the atomic's round trip overlaps
         // this segment's sort and its result is only consumed at the end.
         unsigned long long next = 0;
-        if (threadIdx.x == 0) next = atomicAdd(head, 1ull);
-        const SegDesc d = descs[item];
+        if (threadIdx.x == 0) next = atomicAdd(&ctrl[0], 1ull);
+        const SegDesc d = cdesc[item];
         sort_segment<NT, L, LV>(d, netset, smem, s_split);
         if (threadIdx.x == 0) s_item[it ^ 1] = next;
         __syncthreads();
     }
+    // Every thread left the loop after the same barrier: the block's shared
+    // memory is free for the warps' own tiles.
+    constexpr int WSZ = BlockSort3<32, L, LV>::SZ;
+    int32_t *ws = smem + (threadIdx.x >> 5) * WSZ;
+    for (;;) {
+        unsigned long long j = 0;
+        if ((threadIdx.x & 31) == 0) j = atomicAdd(&ctrl[1], 1ull);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= nsmall) break;
+        const SegDesc d = cdesc[ndesc - 1 - (int64_t)j];
+        warp_sort_segment<L, LV>(d.keys, (int)d.n, netset, ws);
+    }
 }
 
-// Descriptors for an offsets array: segment i is keys[off[i], off[i+1]); its
-// scratch is the same range of the workspace key area.  Malformed offsets
-// raise a status bit and leave the segment empty.
-__global__ void k_seg_descs(int32_t *keys, int64_t n_keys, const int64_t *off, int64_t nseg,
-                            int32_t *scratch, SegDesc *descs, unsigned *status) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nseg) return;
-    const int64_t b = off[i], e = off[i + 1];
-    SegDesc d{};
-    if (b < 0 || e < b || e > n_keys) {
-        atomicOr(status, kStatusBadOffsets);
-    } else {
-        d.keys = keys + b;
-        d.scratch = scratch + b;
-        d.n = e - b;
+// Files descriptor d (when valid) into the classified array: large segments
+// (more than small_max keys) from the front, small ones (2..small_max keys)
+// from the back; empty and one-key segments are already sorted and dropped.
+// One atomic per warp and class.  Every lane of the warp must call it.
+HS_DEV void classify_desc(const SegDesc &d, bool valid, int64_t ndesc, int64_t small_max,
+                          SegDesc *cdesc, unsigned long long *ctrl) {
+    const bool big = valid && d.n > small_max;
+    const bool sml = valid && d.n > 1 && d.n <= small_max;
+    const unsigned mb = __ballot_sync(0xffffffffu, big), ms = __ballot_sync(0xffffffffu, sml);
+    const int lane = threadIdx.x & 31;
+    unsigned long long bb = 0, sb = 0;
+    if (lane == 0) {
+        if (mb) bb = atomicAdd(&ctrl[2], (unsigned long long)__popc(mb));
+        if (ms) sb = atomicAdd(&ctrl[3], (unsigned long long)__popc(ms));
     }
-    descs[i] = d;
+    bb = __shfl_sync(0xffffffffu, bb, 0);
+    sb = __shfl_sync(0xffffffffu, sb, 0);
+    const unsigned below = (1u << lane) - 1u;
+    if (big) cdesc[bb + __popc(mb & below)] = d;
+    if (sml) cdesc[ndesc - 1 - (int64_t)(sb + __popc(ms & below))] = d;
+}
+
+// Classifies caller-built descriptors (the serving loop's batches).
+__global__ void k_seg_classify(const SegDesc *descs, int64_t ndesc, int64_t small_max,
+                               SegDesc *cdesc, unsigned long long *ctrl) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    SegDesc d{};
+    const bool valid = i < ndesc;
+    if (valid) d = descs[i];
+    classify_desc(d, valid, ndesc, small_max, cdesc, ctrl);
+}
+
+// Descriptors for an offsets array, classified as they are built: segment i
+// is keys[off[i], off[i+1]); its scratch is the same range of the workspace
+// key area.  Malformed offsets raise a status bit and drop the segment.
+__global__ void k_seg_descs(int32_t *keys, int64_t n_keys, const int64_t *off, int64_t nseg,
+                            int32_t *scratch, int64_t small_max, SegDesc *cdesc,
+                            unsigned long long *ctrl, unsigned *status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    SegDesc d{};
+    bool valid = false;
+    if (i < nseg) {
+        const int64_t b = off[i], e = off[i + 1];
+        if (b < 0 || e < b || e > n_keys) {
+            atomicOr(status, kStatusBadOffsets);
+        } else {
+            d.keys = keys + b;
+            d.scratch = scratch + b;
+            d.n = e - b;
+            valid = true;
+        }
+    }
+    classify_desc(d, valid, nseg, small_max, cdesc, ctrl);
 }
 
 // ------------------------------------------------------------------ host side
@@ -217,20 +313,22 @@ struct SegKernelInfo {
     const void *fn;
     int smem;
     int max_occ;
+    int64_t small_max;  // segments of up to this many keys are sorted by one warp
 };
 
 template <int NT, int L, int LV>
 static hs_status seg_kernel_info(SegKernelInfo *out) {
-    using C = BlockSort3<NT, L, LV>;
+    constexpr int SMEM = seg_smem_bytes<NT, L, LV>();
     auto kern = k_seg_sort<NT, L, LV>;
-    hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
+    hs_status r = ensure_smem((const void *)kern, SMEM);
     if (r != HS_OK) return r;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, C::SMEM_BYTES);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, SMEM);
     if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     out->fn = (const void *)kern;
-    out->smem = C::SMEM_BYTES;
+    out->smem = SMEM;
     out->max_occ = occ > 0 ? occ : 1;
+    out->small_max = BlockSort3<32, L, LV>::T;
     return HS_OK;
 }
 
@@ -283,26 +381,38 @@ hs_status check_plan(const hs_plan &p) {
     return HS_OK;
 }
 
-hs_status seg_launch_descs(const SegDesc *d_descs, int64_t ndesc, unsigned long long *d_head,
-                           const hs_plan &plan, cudaStream_t st) {
-    hs_status r = check_plan(plan);
-    if (r != HS_OK) return r;
-    if (ndesc <= 0) return HS_OK;
-    SegKernelInfo ki{};
-    if ((r = seg_kernel(plan.block_threads, leaf_size(plan.netset), &ki)) != HS_OK) return r;
+// The persistent sort over classified descriptors (ctrl already holds the
+// class counts and zeroed heads).
+static hs_status seg_launch_sort(const SegKernelInfo &ki, const SegDesc *d_cdesc, int64_t ndesc,
+                                 unsigned long long *d_ctrl, const hs_plan &plan, cudaStream_t st) {
     const int per_sm = plan.ctas_per_sm > 0 ? std::min(plan.ctas_per_sm, ki.max_occ) : ki.max_occ;
     const int64_t grid = std::min<int64_t>(ndesc, (int64_t)sm_count() * per_sm);
-    cudaError_t e = cudaMemsetAsync(d_head, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return fail_cuda(e, "segsort: queue reset");
     uint32_t netset = plan.netset;
-    void *args[] = {(void *)&d_descs, (void *)&ndesc, (void *)&d_head, (void *)&netset};
+    void *args[] = {(void *)&d_cdesc, (void *)&ndesc, (void *)&d_ctrl, (void *)&netset};
     LaunchToken t = launch_begin(K_SEG_SORT, st);
-    e = cudaLaunchKernel(ki.fn, dim3((unsigned)grid), dim3(plan.block_threads), args, ki.smem, st);
+    cudaError_t e = cudaLaunchKernel(ki.fn, dim3((unsigned)grid), dim3(plan.block_threads), args,
+                                     ki.smem, st);
     if (e != cudaSuccess) {
         launch_end(t);
         return fail_cuda(e, "segsort launch");
     }
     return launch_end(t);
+}
+
+hs_status seg_launch_descs(const SegDesc *d_descs, int64_t ndesc, SegDesc *d_cdesc,
+                           unsigned long long *d_ctrl, const hs_plan &plan, cudaStream_t st) {
+    hs_status r = check_plan(plan);
+    if (r != HS_OK) return r;
+    if (ndesc <= 0) return HS_OK;
+    SegKernelInfo ki{};
+    if ((r = seg_kernel(plan.block_threads, leaf_size(plan.netset), &ki)) != HS_OK) return r;
+    cudaError_t e = cudaMemsetAsync(d_ctrl, 0, kCtrlWords * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return fail_cuda(e, "segsort: queue reset");
+    LaunchToken t = launch_begin(K_SEG_CLASSIFY, st);
+    k_seg_classify<<<(unsigned)((ndesc + 255) / 256), 256, 0, st>>>(d_descs, ndesc, ki.small_max,
+                                                                    d_cdesc, d_ctrl);
+    if ((r = launch_end(t)) != HS_OK) return r;
+    return seg_launch_sort(ki, d_cdesc, ndesc, d_ctrl, plan, st);
 }
 
 struct SegLayout {
@@ -338,17 +448,22 @@ hs_status segsort(int32_t *d_keys, size_t n_keys, const int64_t *d_offsets, size
     if (!d_ws || ws_bytes < l.total)
         return fail(HS_ERR_INVALID_ARG, "hs_segsort_i32: workspace smaller than hs_segsort_workspace_bytes");
     if (!aligned(d_ws, 16)) return fail(HS_ERR_INVALID_ARG, "hs_segsort_i32: workspace not 16-byte aligned");
+    SegKernelInfo ki{};
+    if ((r = seg_kernel(plan.block_threads, leaf_size(plan.netset), &ki)) != HS_OK) return r;
     char *base = static_cast<char *>(d_ws);
     int32_t *scratch = reinterpret_cast<int32_t *>(base + l.keys);
-    SegDesc *descs = reinterpret_cast<SegDesc *>(base + l.descs);
-    unsigned long long *head = reinterpret_cast<unsigned long long *>(base + l.head);
+    SegDesc *cdesc = reinterpret_cast<SegDesc *>(base + l.descs);
+    unsigned long long *ctrl = reinterpret_cast<unsigned long long *>(base + l.head);
     unsigned *status = nullptr;
     if ((r = device_status(&status)) != HS_OK) return r;
+    cudaError_t e = cudaMemsetAsync(ctrl, 0, kCtrlWords * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return fail_cuda(e, "segsort: queue reset");
     LaunchToken t = launch_begin(K_SEG_CLASSIFY, st);
     k_seg_descs<<<(unsigned)((num_segs + 255) / 256), 256, 0, st>>>(
-        d_keys, (int64_t)n_keys, d_offsets, (int64_t)num_segs, scratch, descs, status);
+        d_keys, (int64_t)n_keys, d_offsets, (int64_t)num_segs, scratch, ki.small_max, cdesc, ctrl,
+        status);
     if ((r = launch_end(t)) != HS_OK) return r;
-    return seg_launch_descs(descs, (int64_t)num_segs, head, plan, st);
+    return seg_launch_sort(ki, cdesc, (int64_t)num_segs, ctrl, plan, st);
 }
 
 // -------------------------------------------------------------- graphs

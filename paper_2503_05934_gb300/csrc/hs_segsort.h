@@ -17,10 +17,12 @@ struct SegDesc {
 hs_plan default_seg_plan(hs_netset s);
 hs_status check_plan(const hs_plan &p);
 
-// Sorts ndesc arrays described by device descriptors with one persistent
-// launch; d_head is a device counter the launch resets first.
-hs_status seg_launch_descs(const SegDesc *d_descs, int64_t ndesc, unsigned long long *d_head,
-                           const hs_plan &plan, cudaStream_t st);
+// Sorts ndesc arrays described by device descriptors: a classify launch
+// files them into d_cdesc (ndesc entries; large segments from the front,
+// warp-sized ones from the back), then one persistent launch sorts them.
+// d_ctrl holds the launch's four queue counters (32 bytes, reset first).
+hs_status seg_launch_descs(const SegDesc *d_descs, int64_t ndesc, SegDesc *d_cdesc,
+                           unsigned long long *d_ctrl, const hs_plan &plan, cudaStream_t st);
 
 size_t segsort_workspace_bytes(size_t n_keys, size_t num_segs);
 hs_status segsort(int32_t *d_keys, size_t n_keys, const int64_t *d_offsets, size_t num_segs,

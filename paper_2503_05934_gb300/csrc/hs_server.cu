@@ -171,8 +171,8 @@ static void issue_slot(hs_server *srv, Slot &slot) {
                                         cudaMemcpyHostToDevice, slot.stream);
         if (e != cudaSuccess) st = fail_cuda(e, "server: descriptor copy");
         if (st == HS_OK)
-            st = seg_launch_descs(slot.d_desc, nb, slot.d_head, default_seg_plan(batch[0]->netset),
-                                  slot.stream);
+            st = seg_launch_descs(slot.d_desc, nb, slot.d_desc + kMaxBatch, slot.d_head,
+                                  default_seg_plan(batch[0]->netset), slot.stream);
         srv->batches.fetch_add(1);
         srv->batched_reqs.fetch_add(nb);
     }
@@ -278,7 +278,8 @@ hs_status hs_server_create(size_t budget_bytes, hs_server **out) {
         slot.srv = srv;
         e = cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaMallocHost(&slot.h_desc, kMaxBatch * sizeof(SegDesc));
-        if (e == cudaSuccess) e = cudaMalloc(&slot.d_desc, kMaxBatch * sizeof(SegDesc));
+        // The batch's descriptors, then their classified copy.
+        if (e == cudaSuccess) e = cudaMalloc(&slot.d_desc, 2 * kMaxBatch * sizeof(SegDesc));
         if (e == cudaSuccess) e = cudaMalloc(&slot.d_head, 256);
     }
     if (e != cudaSuccess) {

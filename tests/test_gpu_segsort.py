@@ -69,6 +69,27 @@ def test_every_plan_gives_the_same_bytes(hs, netset, threads, ctas):
     assert np.array_equal(gpu_segsort(hs, keys, off, plan=plan), want)
 
 
+LEAF = {"6To8": 8, "Odd": 7, "3To5": 5, "3To4": 4, "none": 1}
+
+
+@pytest.mark.parametrize("netset", ["6To8", "Odd", "3To5", "none"])
+@pytest.mark.parametrize("threads", [256, 512])
+def test_warp_tile_boundary(hs, netset, threads):
+    """Segments of up to one warp tile (32 threads x EO keys, EO = 4L-1 at
+    256 threads, 2L-1 at 512) are sorted by a single warp; one key more goes
+    to a whole CTA.  Many such segments keep every warp of a CTA busy on a
+    different one at once."""
+    L = LEAF[netset]
+    wt = 32 * ((4 if threads == 256 else 2) * L - 1)
+    rng = np.random.default_rng(wt + threads)
+    edge = [wt - 1, wt, wt + 1, 2, 3, 2 * wt, wt - 31, 33]
+    sizes = np.concatenate([edge, rng.integers(0, wt + 1, 600), edge]).astype(np.int64)
+    keys, off, _ = g.segmented(0, 5 + wt, sizes=sizes)
+    want = oracle.segsort(keys, off, "merge", "6To8")
+    plan = hs.make_plan(netset, threads, 0)
+    assert np.array_equal(gpu_segsort(hs, keys, off, plan=plan), want)
+
+
 def test_large_segments_and_many_merge_chunks(hs):
     # One segment long enough for more than 256 merge chunks per level
     # (several split batches), plus neighbours of odd sizes.
