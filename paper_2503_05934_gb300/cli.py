@@ -9,8 +9,9 @@ prints the time per sort.
 Keys are int32 from the seeded generators of ``hs_inputs`` (uniform over the
 int32 range, sorted, or nearly sorted); pairs carry keys from 2^16 distinct
 values and values = original index; batched runs sort --segments arrays of
-log-uniform sizes in [3, 65536] (mixed distributions) in one launch with the
-default plan.  Every run restores the input from a
+log-uniform sizes in [3, 65536] (mixed distributions), or with --seg-size S
+2^log2n keys in arrays of S keys each, in one launch with the default plan.
+Every run restores the input from a
 pristine device copy (untimed), times the sort with CUDA events on the
 sorting stream, and checks that the output is sorted (pairs: and stable).
 """
@@ -30,6 +31,9 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--what", choices=["keys", "quick", "pairs", "batched"], default="keys")
     ap.add_argument("--segments", type=int, default=20000)
+    ap.add_argument("--seg-size", type=int, default=0,
+                    help="batched: every segment this long, 2^log2n keys in all "
+                         "(default: --segments log-uniform sizes)")
     ap.add_argument("--log2n", type=int, default=24)
     ap.add_argument("--dist", choices=["uniform", "sorted", "nearly"], default="uniform")
     ap.add_argument("--netset", default="6To8")
@@ -38,6 +42,7 @@ def main(argv=None) -> int:
     ap.add_argument("--option", action="append", default=[], help="name=value for hs_set_option")
     args = ap.parse_args(argv)
 
+    import numpy as np
     import torch
 
     import hs_inputs
@@ -57,7 +62,11 @@ def main(argv=None) -> int:
         def run(bufs):
             hs.hs_sort_pairs_i32(bufs[0], bufs[1], "merge", args.netset, ws=ws, stream=st)
     elif args.what == "batched":
-        keys, off, _ = hs_inputs.segmented(args.segments, args.seed)
+        if args.seg_size > 0:
+            sizes = np.full(max(1, n // args.seg_size), args.seg_size, np.int64)
+            keys, off, _ = hs_inputs.segmented(0, args.seed, sizes=sizes)
+        else:
+            keys, off, _ = hs_inputs.segmented(args.segments, args.seed)
         n = keys.size
         src = [torch.from_numpy(keys).to(dev)]
         offs = torch.from_numpy(off).to(dev)

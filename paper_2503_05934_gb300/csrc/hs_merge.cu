@@ -76,9 +76,10 @@ static hs_status launch_blocksort_nt(int L, const int32_t *kin, int32_t *kout, i
     return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
 }
 
-hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
-                           int vec, cudaStream_t st, int32_t *samp) {
-    switch (shape_for(n, L)) {
+static hs_status blocksort_launch_shape(int shape, int L, const int32_t *kin, int32_t *kout,
+                                        int64_t n, hs_netset s, int vec, cudaStream_t st,
+                                        int32_t *samp) {
+    switch (shape) {
         case 1: return launch_blocksort_nt<1024, 2>(L, kin, kout, n, s, vec, samp, st);
         case 2: return launch_blocksort_nt<256, 4>(L, kin, kout, n, s, vec, samp, st);
         case 3: return launch_blocksort_nt<512, 4>(L, kin, kout, n, s, vec, samp, st);
@@ -86,6 +87,11 @@ hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, 
         case 5: return launch_blocksort_nt<576, 4>(L, kin, kout, n, s, vec, samp, st);
         default: return launch_blocksort_nt<512, 2>(L, kin, kout, n, s, vec, samp, st);
     }
+}
+
+hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
+                           int vec, cudaStream_t st, int32_t *samp) {
+    return blocksort_launch_shape(shape_for(n, L), L, kin, kout, n, s, vec, st, samp);
 }
 
 // Global levels: the tiled kernel (option "merge_kernel" 1, the default) for
@@ -177,20 +183,39 @@ hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, v
     return merge_sort_with(d_keys, n, s, m.kbuf, m.part, m.samp, st);
 }
 
-// Host buffer in, sorted host buffer out, with the input copy overlapped: the
-// keys travel in kChunks equal chunks on a copy stream; each chunk is merge-
-// sorted on `st` as soon as it has arrived (block sort and the levels inside
-// the chunk), while the next chunks are still in flight; global merge levels
-// of run width C, 2C, ... then merge the sorted chunks (the same levels a
-// whole-array sort runs), and the result is copied back.  d_keys is device
+// Chunk-local merge levels of the host-buffer sort: the most that keep one
+// chunk's sort (block sort + k levels) within the time its copy in takes, so
+// that sorting keeps pace with the copies.  Planning rates, measured on
+// GB300: host link 200 GB/s, block sort 130 Gkeys/s, a merge level 8 B/key at
+// 6.5 TB/s plus 30 us of partition and launch latency.
+static int host_local_levels(int64_t chunk, int max_levels) {
+    const double copy_s = 4.0 * chunk / 200e9;
+    const double sort_s = chunk / 130e9;
+    const double level_s = 8.0 * chunk / 6.5e12 + 30e-6;
+    int k = 0;
+    while (k < max_levels && sort_s + (k + 1) * level_s <= copy_s) ++k;
+    return k;
+}
+
+// Host-buffer merge sort.  The keys are copied in as about eight chunks on a
+// second stream; as each chunk lands it is block sorted and merged k levels
+// deep into runs of W = T << k keys (chunks are whole multiples of W, so these
+// are exactly the first k levels of the whole sort).  The remaining levels run
+// over the whole array, and the result is copied out.  d_keys is device
 // memory for n keys; d_ws the merge workspace for n keys.
 hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, hs_netset s,
                                   void *d_ws, cudaStream_t st) {
     constexpr int kChunks = 8;
     const int64_t n = (int64_t)n_;
-    // Chunk length: a multiple of 1024 keys (16-byte aligned chunk starts and
-    // sample positions that are multiples of 32).
-    const int64_t C = ((n + kChunks - 1) / kChunks + 1023) / 1024 * 1024;
+    const int L = leaf_size(s);
+    const int shape = shape_for(n, L);
+    const int64_t T = shape_tile(shape, L);
+    const int levels = global_levels(n, T);
+    const int k = host_local_levels((n + kChunks - 1) / kChunks, levels > 0 ? levels - 1 : 0);
+    const int64_t W = T << k;
+    // Chunk length: whole runs of W keys, so chunk starts are multiples of
+    // T (16-byte aligned, sample positions at multiples of 32).
+    const int64_t C = W * std::max<int64_t>(1, (n + kChunks * W - 1) / (kChunks * W));
     const int nch = (int)((n + C - 1) / C);
     const MergeScratch m = carve_merge_workspace(d_ws, n_);
     const int vec = aligned(d_keys, 16) ? 1 : 0;
@@ -213,10 +238,18 @@ hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, h
             r = fail_cuda(e, "host sort: wait for a chunk");
             break;
         }
-        r = merge_sort_with(d_keys + b, len, s, m.kbuf + b, m.part, samp ? samp + b / 32 : nullptr, st);
+        // The block sort writes where k ping-pong levels end in d_keys.
+        int32_t *cur = (k % 2 == 0) ? d_keys + b : m.kbuf + b;
+        int32_t *alt = (k % 2 == 0) ? m.kbuf + b : d_keys + b;
+        int32_t *csamp = samp ? samp + b / kSampleStride : nullptr;
+        r = blocksort_launch_shape(shape, L, d_keys + b, cur, len, s, vec, st, csamp);
+        for (int j = 0; j < k && r == HS_OK; ++j) {
+            r = launch_keys_level(cur, alt, len, T << j, m.part, csamp, vec, st);
+            std::swap(cur, alt);
+        }
     }
     int32_t *kcur = d_keys, *kalt = m.kbuf;
-    for (int64_t w = C; w < n && r == HS_OK; w *= 2) {
+    for (int64_t w = W; w < n && r == HS_OK; w *= 2) {
         r = launch_keys_level(kcur, kalt, n, w, m.part, samp, vec, st);
         std::swap(kcur, kalt);
     }

@@ -185,11 +185,15 @@ def test_host_buffer_entry(hs):
     assert np.array_equal(h.numpy(), oracle.merge_sort(a, "6To8"))
 
 
-@pytest.mark.parametrize("n", [1 << 22, (1 << 22) + 12_345, 5 * (1 << 22) + 2, 3 * (1 << 23)])
+@pytest.mark.parametrize("n", [1 << 22, (1 << 22) + 12_345, 5 * (1 << 22) + 2, 3 * (1 << 23),
+                               (1 << 26) + 4 * 12_345, 5 * (1 << 24) + 2])
 def test_host_buffer_entry_chunked(hs, n):
-    """Host sorts of 2^22 keys or more copy in by chunks and sort each chunk
-    on arrival, then merge the chunks: the result must equal the oracle's
-    order statistics and numpy's sort (pinned and pageable buffers)."""
+    """Host sorts of 2^22 keys or more copy in by chunks and block sort each
+    chunk on arrival, from 2^26 keys on also with its first merge levels
+    (chunks of whole runs), then run the remaining levels: the result must
+    equal the oracle's order statistics and numpy's sort (pinned and pageable
+    buffers; the last two sizes take chunk-local levels, aligned and not a
+    multiple of four)."""
     import torch
     a = g.random_i32(n, 40 + n)
     h = torch.from_numpy(a.copy()).pin_memory()
