@@ -21,12 +21,20 @@
 //   k_qs_fill      the listed = ranges, in the caller's array
 //   k_qs_small     block sort of each small child into the caller's array
 //   k_qs_chunkmap  chunk -> segment map of the next level
-// The host reads the level's counters back once, after k_qs_next, to size
-// the remaining launches exactly (one CTA per chunk, per small child, per
-// listed range, per next-level segment); the kernels also read their counts
-// on the device and skip work past them.  The order of the chunks' runs
-// inside a < or > range depends on timing; the sorted output does not.
+// The host does not wait for a level before launching the next one.  Each
+// level's counters reach it through mapped host memory (written by
+// k_qs_chunkmap), and it reads those of the level two back: launch sizes are
+// upper bounds derived from the last counters it has seen (segments at most
+// double per level, and the chunk count never exceeds the known chunks plus
+// one partial chunk per segment); every kernel reads its exact count on the
+// device and skips work past it.  The small-segment sorts and the long =
+// fills of a level (k_qs_leaves) run on a second stream, overlapped with the
+// following levels: their key ranges are final, so no later level touches
+// them.  Counters and lists rotate through QS_RING slots so a level's slot is
+// reused only after its leaves are done.  The order of the chunks' runs inside
+// a < or > range depends on timing; the sorted output does not.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "hs_internal.h"
@@ -60,11 +68,19 @@ struct QFill {
     int32_t value, pad;
 };
 
-// Level k uses counter slot k % 2: nseg and nchunks describe its segment list
-// (written by level k - 1); nsmall and nfill count the small children and
-// long = ranges that level k itself lists and consumes.
+// Level k uses counter slot k % QS_RING: nseg and nchunks describe its
+// segment list (written by level k - 1); nsmall and nfill count the small
+// children and long = ranges that level k itself lists, in its own slot of
+// the small and fill lists.
+constexpr int QS_RING = 4;
 struct QCounters {
     unsigned long long nseg, nchunks, nsmall, nfill;
+};
+
+// One level's counters as the host reads them (mapped host memory).
+struct QReadback {
+    QCounters cur, next;
+    unsigned long long status, pad;
 };
 
 struct QCaps {
@@ -95,7 +111,7 @@ __global__ void k_qs_init(QSeg *segs, int32_t *chunk_seg, int64_t n, int64_t nch
         s.pivot = median_of_three(X, 0, n);
         segs[0] = s;
         ctr[0] = QCounters{1ull, (unsigned long long)nchunks, 0ull, 0ull};
-        ctr[1] = QCounters{0ull, 0ull, 0ull, 0ull};
+        for (int i = 1; i < QS_RING; ++i) ctr[i] = QCounters{0ull, 0ull, 0ull, 0ull};
         *status = 0ull;
     }
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
@@ -272,16 +288,11 @@ __global__ void k_qs_next(const QSeg *segs, QCounters *cctr, QCounters *nctr, QC
     }
 }
 
-__global__ void k_qs_fill(const QFill *fill, const QCounters *cctr, QCaps caps, int32_t *X) {
-    const int64_t nfill = clamp_count(cctr->nfill, caps.fill);
-    for (int64_t f = blockIdx.x; f < nfill; f += gridDim.x) {
-        const QFill q = fill[f];
-        for (int64_t i = q.begin + threadIdx.x; i < q.end; i += blockDim.x) X[i] = q.value;
-    }
-}
-
-__global__ void k_qs_chunkmap(const QSeg *segs, const QCounters *nctr, QCaps caps,
-                              int32_t *chunk_seg) {
+// Chunk -> segment map of the next level.  Block 0 also publishes the
+// level's final counters and status to the host (mapped memory).
+__global__ void k_qs_chunkmap(const QSeg *segs, const QCounters *cctr, const QCounters *nctr,
+                              QCaps caps, int32_t *chunk_seg, const unsigned long long *status,
+                              QReadback *rb) {
     const int64_t nseg = clamp_count(nctr->nseg, caps.seg);
     for (int64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
         const QSeg &g = segs[s];
@@ -289,17 +300,36 @@ __global__ void k_qs_chunkmap(const QSeg *segs, const QCounters *nctr, QCaps cap
         for (int64_t c = threadIdx.x; c < nch; c += blockDim.x)
             if (g.chunk0 + c < caps.chunk) chunk_seg[g.chunk0 + c] = (int32_t)s;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        QReadback r{};
+        r.cur = *cctr;
+        r.next = *nctr;
+        r.status = *status;
+        *rb = r;
+        __threadfence_system();
+    }
 }
 
+// A level's leaves: item i < nsmall block-sorts small child i into the
+// caller's array; the next nfill items write the listed = ranges.
 template <int L>
 __global__ void __launch_bounds__(QS_BS_NT)
-    k_qs_small(const QSmall *small, const QCounters *cctr, QCaps caps, const int32_t *X,
-               const int32_t *Y, int32_t *Xw, uint32_t netset) {
+    k_qs_leaves(const QSmall *small, const QFill *fill, const QCounters *cctr, QCaps caps,
+                const int32_t *X, const int32_t *Y, int32_t *Xw, uint32_t netset) {
     extern __shared__ __align__(16) int32_t smem[];
-    if ((int64_t)blockIdx.x >= clamp_count(cctr->nsmall, caps.small)) return;
-    const QSmall s = small[blockIdx.x];
-    block_sort_tile3<QS_BS_NT, L, 4, true>(qs_src(s.buf, X, Y) + s.begin, Xw + s.begin,
-                                           (int)(s.end - s.begin), netset, false, smem);
+    const int64_t nsmall = clamp_count(cctr->nsmall, caps.small);
+    const int64_t nfill = clamp_count(cctr->nfill, caps.fill);
+    for (int64_t i = blockIdx.x; i < nsmall + nfill; i += gridDim.x) {
+        if (i < nsmall) {
+            const QSmall s = small[i];
+            block_sort_tile3<QS_BS_NT, L, 4, true>(qs_src(s.buf, X, Y) + s.begin, Xw + s.begin,
+                                                   (int)(s.end - s.begin), netset, false, smem);
+            __syncthreads();
+        } else {
+            const QFill q = fill[i - nsmall];
+            for (int64_t x = q.begin + threadIdx.x; x < q.end; x += blockDim.x) Xw[x] = q.value;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -319,6 +349,7 @@ static QLayout qs_layout(size_t n) {
     q.caps.chunk = (int64_t)(n / QS_C) + q.caps.seg + 2;
     q.caps.small = 2 * q.caps.seg + 2;
     q.caps.fill = q.caps.seg;
+    // Small and fill lists and counters: one slot per level in flight.
     size_t off = 0;
     q.y = off;
     off += align_up(n * sizeof(int32_t), 256);
@@ -333,11 +364,11 @@ static QLayout qs_layout(size_t n) {
     q.chunk_b = off;
     off += align_up((size_t)q.caps.chunk * sizeof(int32_t), 256);
     q.small = off;
-    off += align_up((size_t)q.caps.small * sizeof(QSmall), 256);
+    off += align_up(QS_RING * (size_t)q.caps.small * sizeof(QSmall), 256);
     q.fill = off;
-    off += align_up((size_t)q.caps.fill * sizeof(QFill), 256);
+    off += align_up(QS_RING * (size_t)q.caps.fill * sizeof(QFill), 256);
     q.ctr = off;
-    off += align_up(2 * sizeof(QCounters), 256);
+    off += align_up(QS_RING * sizeof(QCounters), 256);
     q.status = off;
     off += 256;
     q.total = off;
@@ -350,31 +381,89 @@ void quick_set_max_levels(int64_t v) { qs_option_max_levels = v; }
 void quick_set_two_way(int v) { g_qs_two_way = v; }
 
 template <int L>
-static hs_status launch_small_t(int64_t nsmall, const QSmall *small, const QCounters *cctr,
-                                const QCaps &caps, const int32_t *X, const int32_t *Y, int32_t *Xw,
-                                hs_netset s, cudaStream_t st) {
+static hs_status launch_leaves_t(int64_t grid, const QSmall *small, const QFill *fill,
+                                 const QCounters *cctr, const QCaps &caps, const int32_t *X,
+                                 const int32_t *Y, int32_t *Xw, hs_netset s, cudaStream_t st) {
     const int smem = BlockSort3<QS_BS_NT, L, 4>::SMEM_BYTES;
-    auto kern = k_qs_small<L>;
+    auto kern = k_qs_leaves<L>;
     hs_status r = ensure_smem((const void *)kern, smem);
     if (r != HS_OK) return r;
     LaunchToken t = launch_begin(K_QS_SMALL, st);
-    kern<<<(unsigned)nsmall, QS_BS_NT, smem, st>>>(small, cctr, caps, X, Y, Xw, s);
+    kern<<<(unsigned)grid, QS_BS_NT, smem, st>>>(small, fill, cctr, caps, X, Y, Xw, s);
     return launch_end(t);
 }
 
-static hs_status launch_small(int L, int64_t nsmall, const QSmall *small, const QCounters *cctr,
-                              const QCaps &caps, const int32_t *X, const int32_t *Y, int32_t *Xw,
-                              hs_netset s, cudaStream_t st) {
+static hs_status launch_leaves(int L, int64_t grid, const QSmall *small, const QFill *fill,
+                               const QCounters *cctr, const QCaps &caps, const int32_t *X,
+                               const int32_t *Y, int32_t *Xw, hs_netset s, cudaStream_t st) {
     switch (L) {
-        case 1: return launch_small_t<1>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
-        case 3: return launch_small_t<3>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
-        case 4: return launch_small_t<4>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
-        case 5: return launch_small_t<5>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
-        case 6: return launch_small_t<6>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
-        case 7: return launch_small_t<7>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
-        case 8: return launch_small_t<8>(nsmall, small, cctr, caps, X, Y, Xw, s, st);
+        case 1: return launch_leaves_t<1>(grid, small, fill, cctr, caps, X, Y, Xw, s, st);
+        case 3: return launch_leaves_t<3>(grid, small, fill, cctr, caps, X, Y, Xw, s, st);
+        case 4: return launch_leaves_t<4>(grid, small, fill, cctr, caps, X, Y, Xw, s, st);
+        case 5: return launch_leaves_t<5>(grid, small, fill, cctr, caps, X, Y, Xw, s, st);
+        case 6: return launch_leaves_t<6>(grid, small, fill, cctr, caps, X, Y, Xw, s, st);
+        case 7: return launch_leaves_t<7>(grid, small, fill, cctr, caps, X, Y, Xw, s, st);
+        case 8: return launch_leaves_t<8>(grid, small, fill, cctr, caps, X, Y, Xw, s, st);
     }
     return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
+}
+
+// Per host thread and device: the leaves stream, the events of the levels in
+// flight and the mapped readback slots.  Created on first use and kept for
+// the thread's lifetime.
+struct QuickCtx {
+    int device = -1;
+    cudaStream_t side = nullptr;
+    cudaEvent_t level_done[QS_RING] = {}, leaves_done[QS_RING] = {}, side_end = nullptr;
+    QReadback *h_rb = nullptr, *d_rb = nullptr;
+};
+
+// A level's published counters, once its completion event has been waited
+// for (the synchronising call orders the device's writes before this read).
+static QReadback read_back(const QuickCtx *qc, int64_t level) {
+    QReadback r;
+    std::memcpy(&r, &qc->h_rb[level % QS_RING], sizeof(r));
+    return r;
+}
+
+static hs_status quick_ctx(QuickCtx **out) {
+    static thread_local std::vector<QuickCtx *> ctxs;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e, "quick sort: current device");
+    for (QuickCtx *c : ctxs)
+        if (c->device == dev) {
+            *out = c;
+            return HS_OK;
+        }
+    QuickCtx *c = new (std::nothrow) QuickCtx();
+    if (!c) return fail(HS_ERR_NO_MEMORY, "quick sort: context");
+    c->device = dev;
+    e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    for (int i = 0; i < QS_RING && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&c->level_done[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->leaves_done[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->side_end, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void **>(&c->h_rb), QS_RING * sizeof(QReadback),
+                          cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->d_rb), c->h_rb, 0);
+    if (e != cudaSuccess) {
+        // Partly built contexts are released; errors on release are moot.
+        if (c->h_rb) cudaFreeHost(c->h_rb);
+        for (int i = 0; i < QS_RING; ++i) {
+            if (c->level_done[i]) cudaEventDestroy(c->level_done[i]);
+            if (c->leaves_done[i]) cudaEventDestroy(c->leaves_done[i]);
+        }
+        if (c->side_end) cudaEventDestroy(c->side_end);
+        if (c->side) cudaStreamDestroy(c->side);
+        delete c;
+        return fail_cuda(e, "quick sort: context");
+    }
+    ctxs.push_back(c);
+    *out = c;
+    return HS_OK;
 }
 
 // Depth guard: segments still live after the level cap (adversarial inputs
@@ -425,61 +514,114 @@ hs_status quick_sort(int32_t *d_keys, size_t n_, hs_netset s, void *d_ws, size_t
     QCounters *ctr = reinterpret_cast<QCounters *>(base + q.ctr);
     unsigned long long *status = reinterpret_cast<unsigned long long *>(base + q.status);
 
+    QuickCtx *qc = nullptr;
+    hs_status r = quick_ctx(&qc);
+    if (r != HS_OK) return r;
+
     const int64_t nchunks0 = (n + QS_C - 1) / QS_C;
     LaunchToken t = launch_begin(K_QS_PLAN, st);
     k_qs_init<<<(unsigned)std::min<int64_t>((nchunks0 + 255) / 256, 4096), 256, 0, st>>>(
         cur, ccur, n, nchunks0, X, ctr, status);
-    hs_status r = launch_end(t);
-    if (r != HS_OK) return r;
+    if ((r = launch_end(t)) != HS_OK) return r;
 
     int lg = 0;
     while ((int64_t(1) << lg) < n) ++lg;
     const int64_t max_levels = qs_option_max_levels >= 0 ? qs_option_max_levels : 4 * lg + 16;
-    QCounters h{1ull, (unsigned long long)nchunks0, 0ull, 0ull};
-    for (int64_t level = 0; h.nseg > 0; ++level) {
-        if (level >= max_levels)
-            return qs_fallback(X, Y, cur, (int64_t)h.nseg, s, base + q.y,
-                               merge_workspace_bytes(n_, 0), st);
-        QCounters *cc = ctr + (level & 1), *nc = ctr + ((level + 1) & 1);
-        cudaError_t e = cudaMemsetAsync(nc, 0, sizeof(QCounters), st);
-        if (e != cudaSuccess) return fail_cuda(e, "quick sort: counter reset");
-        t = launch_begin(K_QS_PARTITION, st);
-        if (g_qs_two_way)
-            k_qs_partition<true><<<(unsigned)h.nchunks, QS_NT, 0, st>>>(cur, ccur, cc, q.caps, X, Y, X, Y);
-        else
-            k_qs_partition<false><<<(unsigned)h.nchunks, QS_NT, 0, st>>>(cur, ccur, cc, q.caps, X, Y, X, Y);
+    // Levels launched ahead of the last counters read back.
+    constexpr int64_t kAhead = 2;
+    // The latest exact counts the host knows: those of level `known`.
+    int64_t known = 0;
+    int64_t known_nseg = 1, known_nchunks = nchunks0;
+    const QCaps &caps = q.caps;
+    cudaError_t e = cudaSuccess;
+    int64_t level = 0;
+    // Waits for everything launched so far (the leaves stream included).
+    auto drain = [&]() {
+        cudaEventRecord(qc->side_end, qc->side);
+        cudaStreamWaitEvent(st, qc->side_end, 0);
+        return cudaStreamSynchronize(st);
+    };
+    for (;; ++level) {
+        if (level >= kAhead) {
+            const int64_t j = level - kAhead;
+            if ((e = cudaEventSynchronize(qc->level_done[j % QS_RING])) != cudaSuccess)
+                return fail_cuda(e, "quick sort: waiting for a level");
+            const QReadback rb = read_back(qc, j);
+            if (rb.status) {
+                drain();
+                return fail(HS_ERR_CUDA, "quick sort: internal work-list overflow");
+            }
+            known = j + 1;
+            known_nseg = (int64_t)rb.next.nseg;
+            known_nchunks = (int64_t)rb.next.nchunks;
+            if (known_nseg == 0) break;  // the levels after j were launched empty
+        }
+        if (level >= max_levels) {
+            // Every level up to here has been launched: wait for all of them,
+            // then hand the segments still live to the merge path.
+            if ((e = drain()) != cudaSuccess) return fail_cuda(e, "quick sort: synchronize");
+            int64_t live = 1;  // level 0: the whole array
+            if (level > 0) {
+                const QReadback rb = read_back(qc, level - 1);
+                if (rb.status) return fail(HS_ERR_CUDA, "quick sort: internal work-list overflow");
+                live = (int64_t)rb.next.nseg;
+            }
+            if (live == 0) break;
+            return qs_fallback(X, Y, cur, live, s, base + q.y, merge_workspace_bytes(n_, 0), st);
+        }
+        // Launch sizes: exact for the level whose counts are known, else
+        // bounds (segments at most double per level; chunks are at most the
+        // known chunks plus one partial chunk per segment).
+        const int64_t lag = level - known;
+        const int64_t seg_b = lag == 0 ? known_nseg
+                                       : std::min<int64_t>(caps.seg, known_nseg << std::min<int64_t>(lag, 32));
+        const int64_t chunk_b = lag == 0 ? known_nchunks
+                                         : std::min<int64_t>(caps.chunk, known_nchunks + seg_b);
+        const int slot = (int)(level % QS_RING), nslot = (int)((level + 1) % QS_RING);
+        QCounters *cc = ctr + slot, *nc = ctr + nslot;
+        QSmall *small_l = small + (size_t)slot * caps.small;
+        QFill *fill_l = fill + (size_t)slot * caps.fill;
+        // Slot nslot last served level + 1 - QS_RING: its leaves must be done
+        // before its counters are reset.
+        if (level + 1 >= QS_RING && (e = cudaStreamWaitEvent(st, qc->leaves_done[nslot], 0)) != cudaSuccess)
+            return fail_cuda(e, "quick sort: ordering the leaves");
+        if ((e = cudaMemsetAsync(nc, 0, sizeof(QCounters), st)) != cudaSuccess)
+            return fail_cuda(e, "quick sort: counter reset");
+        if (chunk_b > 0) {
+            t = launch_begin(K_QS_PARTITION, st);
+            if (g_qs_two_way)
+                k_qs_partition<true><<<(unsigned)chunk_b, QS_NT, 0, st>>>(cur, ccur, cc, caps, X, Y, X, Y);
+            else
+                k_qs_partition<false><<<(unsigned)chunk_b, QS_NT, 0, st>>>(cur, ccur, cc, caps, X, Y, X, Y);
+            if ((r = launch_end(t)) != HS_OK) return r;
+        }
+        t = launch_begin(K_QS_PLAN, st);
+        k_qs_next<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((seg_b + 255) / 256, 4096)), 256, 0, st>>>(
+            cur, cc, nc, caps, tile, nxt, small_l, fill_l, X, Y, status);
         if ((r = launch_end(t)) != HS_OK) return r;
         t = launch_begin(K_QS_PLAN, st);
-        k_qs_next<<<(unsigned)((h.nseg + 255) / 256), 256, 0, st>>>(cur, cc, nc, q.caps, tile, nxt,
-                                                                    small, fill, X, Y, status);
+        k_qs_chunkmap<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(2 * seg_b, 4096)), 256, 0, st>>>(
+            nxt, cc, nc, caps, cnxt, status, qc->d_rb + slot);
         if ((r = launch_end(t)) != HS_OK) return r;
-
-        QCounters hc{}, hn{};
-        unsigned long long hst = 0;
-        e = cudaMemcpyAsync(&hc, cc, sizeof(hc), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&hn, nc, sizeof(hn), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, status, sizeof(hst), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return fail_cuda(e, "quick sort: reading level counters");
-        if (hst) return fail(HS_ERR_CUDA, "quick sort: internal work-list overflow");
-        if (hc.nfill > 0) {
-            t = launch_begin(K_QS_FILL, st);
-            k_qs_fill<<<(unsigned)std::min<unsigned long long>(hc.nfill, 4096), 256, 0, st>>>(
-                fill, cc, q.caps, X);
-            if ((r = launch_end(t)) != HS_OK) return r;
-        }
-        if (hc.nsmall > 0 &&
-            (r = launch_small(L, (int64_t)hc.nsmall, small, cc, q.caps, X, Y, X, s, st)) != HS_OK)
+        if ((e = cudaEventRecord(qc->level_done[slot], st)) != cudaSuccess)
+            return fail_cuda(e, "quick sort: level event");
+        // This level's small children and long = ranges, on the leaves stream.
+        if ((e = cudaStreamWaitEvent(qc->side, qc->level_done[slot], 0)) != cudaSuccess)
+            return fail_cuda(e, "quick sort: ordering the leaves");
+        const int64_t leaves_b = std::min<int64_t>(caps.small + caps.fill, 3 * seg_b);
+        if (leaves_b > 0 &&
+            (r = launch_leaves(L, std::min<int64_t>(leaves_b, 8192), small_l, fill_l, cc, caps, X, Y,
+                               X, s, qc->side)) != HS_OK)
             return r;
-        if (hn.nseg > 0) {
-            t = launch_begin(K_QS_PLAN, st);
-            k_qs_chunkmap<<<(unsigned)hn.nseg, 256, 0, st>>>(nxt, nc, q.caps, cnxt);
-            if ((r = launch_end(t)) != HS_OK) return r;
-        }
-        h = hn;
+        if ((e = cudaEventRecord(qc->leaves_done[slot], qc->side)) != cudaSuccess)
+            return fail_cuda(e, "quick sort: leaves event");
         std::swap(cur, nxt);
         std::swap(ccur, cnxt);
     }
+    // The sort ends on `st`: it waits for the leaves stream's last work.
+    if ((e = cudaEventRecord(qc->side_end, qc->side)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, qc->side_end, 0)) != cudaSuccess)
+        return fail_cuda(e, "quick sort: joining the leaves stream");
     return HS_OK;
 }
 
