@@ -97,9 +97,13 @@ HS_API size_t hs_sort_workspace_bytes(size_t n, int with_values, hs_algo a);
  *            vectorised paths); may be NULL only when n == 0.
  *   n        number of keys; 0 and 1 are no-ops.
  *   d_ws     device workspace of ws_bytes >= hs_sort_workspace_bytes(n, 0, a).
- * MERGE is fully asynchronous.  QUICK reads one small counter back to the
- * host per partition level, so it synchronises `stream` internally and cannot
- * be captured in a CUDA graph.
+ * MERGE is fully asynchronous.  QUICK learns each partition level's
+ * counters through mapped host memory and waits for the level two behind the
+ * one it launches, so the call returns only when all but the last levels have
+ * run, and it cannot be captured in a CUDA graph.  It also runs each level's
+ * leaf sorts on a library-owned second stream (one per host thread and
+ * device), joined back into `stream` before it returns; its work is complete
+ * when `stream` reaches that point.
  * Errors: HS_ERR_INVALID_ARG for a NULL/unaligned pointer with n > 0, an
  * unknown algo, netset bits outside 3..8 or a short workspace;
  * HS_ERR_CUDA if a launch fails. */
