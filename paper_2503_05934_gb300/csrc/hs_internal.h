@@ -18,9 +18,8 @@ enum KernelId {
     K_MERGE_KEYS,
     K_MERGE_PAIRS,
     K_QS_PLAN,
-    K_QS_FILL,
     K_QS_PARTITION,
-    K_QS_SMALL,
+    K_QS_LEAVES,
     K_SEG_CLASSIFY,
     K_SEG_SORT,
     K_COUNT

@@ -18,9 +18,10 @@
 //                  middle) is final; short ones are written here, long ones
 //                  listed; children go to the next level (> tile, with their
 //                  median-of-three pivots) or to the small list (<= tile)
-//   k_qs_fill      the listed = ranges, in the caller's array
-//   k_qs_small     block sort of each small child into the caller's array
-//   k_qs_chunkmap  chunk -> segment map of the next level
+//   k_qs_chunkmap  chunk -> segment map of the next level; publishes the
+//                  level's counters to the host
+//   k_qs_leaves    (second stream) block sort of each small child into the
+//                  caller's array, and the listed = ranges
 // The host does not wait for a level before launching the next one.  Each
 // level's counters reach it through mapped host memory (written by
 // k_qs_chunkmap), and it reads those of the level two back: launch sizes are
@@ -388,7 +389,7 @@ static hs_status launch_leaves_t(int64_t grid, const QSmall *small, const QFill 
     auto kern = k_qs_leaves<L>;
     hs_status r = ensure_smem((const void *)kern, smem);
     if (r != HS_OK) return r;
-    LaunchToken t = launch_begin(K_QS_SMALL, st);
+    LaunchToken t = launch_begin(K_QS_LEAVES, st);
     kern<<<(unsigned)grid, QS_BS_NT, smem, st>>>(small, fill, cctr, caps, X, Y, Xw, s);
     return launch_end(t);
 }

@@ -13,8 +13,8 @@ namespace hs {
 
 static const char *const kKernelNames[K_COUNT] = {
     "blocksort_keys", "blocksort_pairs", "merge_partition", "merge_keys",
-    "merge_pairs",    "qs_plan",         "qs_fill",
-    "qs_partition",   "qs_small",        "seg_classify",    "seg_sort"};
+    "merge_pairs",    "qs_plan",         "qs_partition",
+    "qs_leaves",      "seg_classify",    "seg_sort"};
 
 const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kKernelNames[id] : "?"; }
 
