@@ -541,7 +541,7 @@ def run_extras(hs, torch, dev, stream, args, rank, pristine):
     ms = time_sorts(torch, stream, max(3, args.steps // 4), 2, lambda: w64.copy_(a64),
                     lambda: hs.hs_sort_i64(w64, "merge", args.netset, ws=ws64, stream=stream))
     assert bool((w64[1:] >= w64[:-1]).all().item()), "int64 sort output not sorted"
-    p64 = sort_passes(n, 256 * (4 * 8 - 1))
+    p64 = sort_passes(n, int(hs.lib().hs_i64_tile(hs.netset_mask(args.netset), n)))
     out[f"merge_int64_2p{args.log2n - 1}"] = {
         "value": n / (ms / 1e3), "unit": "keys/s", "ms_per_sort": ms, "passes": p64,
         "frac_of_measured": min(p64, sort_passes(n, 8192)) * 16 * n / (ms / 1e3) / (peak * 1e9),

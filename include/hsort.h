@@ -347,6 +347,11 @@ HS_API size_t hs_keys_tile(hs_netset s, size_t n);
  * the current options; 0 for an invalid set. */
 HS_API size_t hs_pairs_tile(hs_netset s);
 
+/* Keys per block-sort tile of hs_sort_i64 for an n-key array and network set
+ * s (the global merge levels above it number ceil(log2(n / tile))); 0 for an
+ * invalid set. */
+HS_API size_t hs_i64_tile(hs_netset s, size_t n);
+
 /* --------------------------------------------------------- host checking */
 
 /* The device networks compiled for the host, for exhaustive CPU checks of

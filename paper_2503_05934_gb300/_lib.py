@@ -64,6 +64,7 @@ SIGNATURES = {
     "hs_device_check": (_int, [_vp]),
     "hs_keys_tile": (_sz, [_u32, _sz]),
     "hs_pairs_tile": (_sz, [_u32]),
+    "hs_i64_tile": (_sz, [_u32, _sz]),
     "hs_network_pairs": (_int, [_int, ctypes.POINTER(ctypes.c_int), _int]),
     "hs_network_apply": (_int, [_int, _c_i32p]),
 }

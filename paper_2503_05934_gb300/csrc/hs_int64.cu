@@ -210,10 +210,14 @@ __global__ void __launch_bounds__(NT)
 
 // ---------------------------------------------------------------- planner
 
-constexpr int B64_NT = 256;                  // block sort: 256 threads x four leaves
+// Block sort: 256 threads x four leaves (7936 keys for {6,7,8}).  A 288-thread
+// tile (8928 keys) would save a global level at powers of two, as it does for
+// int32 keys, but on 8-byte keys its block sort costs more than that level:
+// 3.05 against 2.37 ms at 2^27 keys, 8.63 against 8.35 ms for the whole sort.
+constexpr int B64_NT = 256;
 constexpr int M64_NT = 96, M64_EO = 31;      // merge level: 96 threads x 31 keys
 
-static int64_t tile64(int L) { return (int64_t)B64_NT * (4 * L - 1); }
+int64_t tile64(int L, int64_t) { return (int64_t)B64_NT * (4 * L - 1); }
 
 size_t merge_workspace_bytes_i64(size_t n) {
     return ws_align(n * sizeof(K64)) + merge_ws_part_bytes(n) + ws_align((n / 32 + 8) * sizeof(K64));
@@ -250,7 +254,7 @@ hs_status merge_sort_i64(int64_t *d_keys, size_t n_, hs_netset s, void *d_ws, si
                          cudaStream_t st) {
     const int64_t n = (int64_t)n_;
     const int L = leaf_size(s);
-    const int64_t T = tile64(L);
+    const int64_t T = tile64(L, n);
     int passes = 0;
     for (int64_t w = T; w < n; w *= 2) ++passes;
 

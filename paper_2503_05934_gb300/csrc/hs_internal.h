@@ -85,6 +85,7 @@ hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n, hs
                                   void *d_ws, cudaStream_t st);
 int64_t pairs_tile(int L);
 size_t merge_workspace_bytes_i64(size_t n);
+int64_t tile64(int L, int64_t n);  // int64 block-sort tile for n keys
 hs_status merge_sort_i64(int64_t *d_keys, size_t n, hs_netset s, void *d_ws, size_t ws_bytes,
                          cudaStream_t st);
 void pairs_set_blocksort(int v);

@@ -376,6 +376,11 @@ size_t hs_keys_tile(hs_netset s, size_t n) {
     return (size_t)keys_tile(leaf_size(s), (int64_t)n);
 }
 
+size_t hs_i64_tile(hs_netset s, size_t n) {
+    if (!netset_ok(s)) return 0;
+    return (size_t)tile64(leaf_size(s), (int64_t)n);
+}
+
 size_t hs_pairs_tile(hs_netset s) {
     if (!netset_ok(s)) return 0;
     return (size_t)pairs_tile(leaf_size(s));

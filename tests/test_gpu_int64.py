@@ -31,7 +31,9 @@ def gpu_sort64(hs, a, netset="6To8", offset=0):
 
 @pytest.mark.parametrize("netset", ["6To8", "3To8", "none", "Odd", "VarSort4"])
 def test_int64_sizes_and_distributions(hs, netset):
-    for n in [0, 1, 2, 7, 31, 2975, 2976, 2977, 7935, 7936, 7937, 25_000, 100_001, 1_000_000]:
+    # Tile edges (7936 keys for {6,7,8}) and sizes just above powers of two.
+    for n in [0, 1, 2, 7, 31, 2975, 2976, 2977, 7935, 7936, 7937, 8928, 8929, 16_384, 17_856,
+              25_000, 100_001, 1_000_000, 1 << 20, (1 << 20) + 3]:
         for dist in g.DISTS:
             a = g.keys_i64(n, dist, 3000 + n)
             assert np.array_equal(gpu_sort64(hs, a, netset), oracle.merge_sort_i64(a, netset)), (n, dist)
