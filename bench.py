@@ -40,6 +40,7 @@ SPEC_HBM_GBS = 8000.0
 # shape and its partition pass: the committed ncu traffic figure applies only
 # while these are unchanged.
 KERNEL_SOURCES = ["paper_2503_05934_gb300/csrc/hs_merge_tile.cuh",
+                  "paper_2503_05934_gb300/csrc/hs_bulk.cuh",
                   "paper_2503_05934_gb300/csrc/hs_merge_prims.cuh",
                   "paper_2503_05934_gb300/csrc/hs_common.cuh"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "merge_keys_2p28_uniform.md")

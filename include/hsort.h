@@ -303,8 +303,10 @@ HS_API hs_status hs_prof_read(const char *kernel, uint64_t *launches, double *to
  * status word.  Kernels never trap: a kernel that meets invalid device-side
  * input (segment offsets that decrease or run past the key count) raises
  * this word and skips that work.  Returns HS_ERR_INVALID_ARG for such input,
- * HS_ERR_TIMEOUT if a bounded device-side wait gave up, HS_ERR_CUDA on a
- * CUDA error, else HS_OK.  Synchronous. */
+ * HS_ERR_TIMEOUT if a bounded device-side wait gave up (such as a merge
+ * level's wait for its bulk tile copy), HS_ERR_CUDA on a CUDA error or when
+ * a kernel found bulk-copy addresses that are not 16-byte aligned (it then
+ * skipped its copies), else HS_OK.  Synchronous. */
 HS_API hs_status hs_device_check(hs_stream_t stream);
 
 /* Process-wide tuning knobs (set them while no sort is in flight).
@@ -323,9 +325,11 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *   "merge_kernel": 1 (default) tiled merge levels with asynchronous 16-byte
  *     staging and odd outputs per thread (used for keys when both buffers
  *     are 16-byte aligned and n % 4 == 0), 0 staged-load serial merges.
- *   "merge_tile": shape of the tiled keys level: 5 (default) 96 threads x
- *     31 keys with exact per-thread windows, 0 256 x 15 with two windows,
- *     1 64 x 31, 2 128 x 31, 3 64 x 63, 4 128 x 23, 6 192 x 31, 7 256 x 31.
+ *   "merge_tile": shape of the tiled keys level: 9 (default) 128 threads x
+ *     31 keys with exact per-thread windows, the tile moved in and out by
+ *     bulk copies (copy engine); 8 the same with 96 x 31, 10 with 192 x 31;
+ *     the cp.async-staged forms 5 96 x 31, 1 64 x 31, 2 128 x 31, 3 64 x 63,
+ *     4 128 x 23, 6 192 x 31, 7 256 x 31; 0 256 x 15 with two windows.
  *   "merge_samples": 1 (default) the tiled keys levels' partition searches
  *     start on every 32nd key of the level's input, written by the pass
  *     before; 0 plain searches in the keys.

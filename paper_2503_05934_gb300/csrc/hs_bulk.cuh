@@ -1,0 +1,100 @@
+// Bulk asynchronous copies (the TMA engine's untiled form, cp.async.bulk)
+// between global and shared memory, completed through an mbarrier (loads) or
+// a bulk group (stores).  One thread issues a whole tile's copy, so the
+// load/store units carry none of the tile's global traffic: they are left to
+// the merge's own shared-memory reads and writes.
+//
+// Rules of the untiled form: both addresses 16-byte aligned and the size a
+// multiple of 16 bytes.  Every wait here is bounded.
+#pragma once
+
+#include "hs_common.cuh"
+
+namespace hs {
+
+// Polls of a bounded mbarrier wait (each try_wait may also suspend the
+// thread for a while): far beyond any healthy copy, far below a hang.
+constexpr long kBulkSpinLimit = 1L << 22;
+
+HS_DEV void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+    // Make the initialised barrier visible to the async proxy (the copy engine).
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+HS_DEV void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// True once the barrier's phase `parity` has completed; false after
+// kBulkSpinLimit polls.
+HS_DEV bool mbar_wait(uint64_t *bar, unsigned parity) {
+    const uint32_t a = smem_addr(bar);
+    for (long i = 0; i < kBulkSpinLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// L2 policy for streamed data: evict first, so that small reused arrays (the
+// partition samples) stay resident while whole passes stream through.
+HS_DEV uint64_t l2_evict_first_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Global -> shared, `bytes` (multiple of 16, both ends 16-byte aligned),
+// completing `bytes` of transaction count on `bar`.
+HS_DEV void bulk_load(void *sdst, const void *gsrc, unsigned bytes, uint64_t *bar,
+                      uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
+// Shared -> global in the calling thread's bulk group.
+HS_DEV void bulk_store(void *gdst, const void *ssrc, unsigned bytes, uint64_t policy) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;"
+                 ::"l"(gdst), "r"(smem_addr(ssrc)), "r"(bytes), "l"(policy)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Waits until the calling thread's bulk stores have read their shared source
+// (the CTA's shared memory must outlive those reads).
+HS_DEV void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Orders this thread's generic shared-memory writes before later bulk copies
+// (async proxy) that read them.
+HS_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// x[k] for a run-time k in [0, P) without local memory: a select tree on k's bits.
+template <int P, class K>
+HS_DEV K select_dyn(const K (&x)[P], int k) {
+    K v[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) v[i] = x[i];
+#pragma unroll
+    for (int h = P / 2; h >= 1; h /= 2) {
+        const bool up = (k & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) v[i] = up ? v[i + h] : v[i];
+    }
+    return v[0];
+}
+
+}  // namespace hs

@@ -66,5 +66,6 @@ HS_DEV uint32_t smem_addr(const void *p) {
 // Device status bits raised by kernels instead of trapping.
 constexpr unsigned kStatusTimeout = 1u;  // a bounded device-side wait gave up
 constexpr unsigned kStatusBadOffsets = 2u;
+constexpr unsigned kStatusMisaligned = 4u;  // a bulk copy's addresses were not 16-byte aligned
 
 }  // namespace hs

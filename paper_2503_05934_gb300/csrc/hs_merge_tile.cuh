@@ -5,12 +5,14 @@
 //
 // One CTA per output tile of TO = NT*EO keys (the partition pass gives its
 // merge-path split), many CTAs per SM for latency hiding.  The tile's A and B
-// ranges are staged in shared memory by 16-byte asynchronous copies
-// (cp.async) of their 16-byte-aligned covers; each thread then forms its EO
-// outputs by a bitonic merge of its windows, the outputs are staged in shared
-// memory (odd stride EO: conflict-free) and leave as 16-byte streaming stores.
+// ranges are staged in shared memory as their 16-byte-aligned covers (by
+// bulk copies in the default form, by 16-byte cp.async in the others); each
+// thread then forms its EO outputs by a bitonic merge of its windows, the
+// outputs are staged in shared memory (odd stride EO: conflict-free) and
+// leave as one bulk store (default) or 16-byte streaming stores.
 #pragma once
 
+#include "hs_bulk.cuh"
 #include "hs_internal.h"
 #include "hs_merge_prims.cuh"
 
@@ -175,6 +177,122 @@ __global__ void __launch_bounds__(NT)
     store_tile_out<NT>(dst, sA, tot, samp, m.gs + o0);
 }
 
+// Bulk-copy form of the exact-window level: one thread issues the two cover
+// copies (cp.async.bulk, completion counted on an mbarrier) and, once the
+// tile is merged, one bulk store of the whole output tile; each thread writes
+// the samples that fall among its own outputs straight from registers.  The
+// load/store units then carry only the merge's own shared-memory traffic
+// (the staging, read-back and global stores of k_merge_tile2 go to the copy
+// engine).  Same results as k_merge_tile2.
+template <int NT, int EO>
+__global__ void __launch_bounds__(NT)
+    k_merge_tile_bulk(const int32_t *in, int32_t *out, int64_t n, int64_t w, const int64_t *part,
+                      int tpg, int32_t *samp, unsigned *status) {
+    using C = TileMerge2<NT, EO>;
+    constexpr int TO = C::TO, P = C::P;
+    static_assert(kSampleStride == 32, "sample positions are multiples of 32");
+    extern __shared__ __align__(16) int32_t smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int wsplit[NT / 32 + 1];
+    const int64_t g = blockIdx.x / tpg;
+    const int t = blockIdx.x - (int)(g * tpg);
+    const MergeGeom m = merge_geom(g, n, w);
+    const int64_t glen = m.alen + m.blen;
+    const int64_t o0 = (int64_t)t * TO;
+    const int64_t o1 = (o0 + TO) < glen ? (o0 + TO) : glen;
+    const int64_t a0 = part[blockIdx.x];
+    const int64_t a1 = (o1 == glen) ? m.alen : part[blockIdx.x + 1];
+    const int na = (int)(a1 - a0);
+    const int tot = (int)(o1 - o0);
+    const int nb = tot - na;
+    const int64_t ga = m.gs + a0, gb = m.gs + w + (o0 - a0);
+    const int64_t ca = ga & ~int64_t(3), cb = gb & ~int64_t(3);
+    const int nca = (int)(((ga + na + 3) & ~int64_t(3)) - ca) / 4;
+    const int ncb = (int)(((gb + nb + 3) & ~int64_t(3)) - cb) / 4;
+    int32_t *sA = smem, *sB = smem + 4 * nca;
+    const uint64_t pol = l2_evict_first_policy();
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    // Bulk copies need 16-byte aligned ends: the covers are whole 16-byte
+    // words of 16-byte aligned arrays, and this re-checks it before issuing.
+    const bool aligned16 = ((smem_addr(sA) | smem_addr(sB)) & 15u) == 0 &&
+                           ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+    if (threadIdx.x == 0 && aligned16) {
+        mbar_arrive_expect_tx(&bar, (unsigned)(nca + ncb) * 16u);
+        if (nca > 0) bulk_load(sA, in + ca, (unsigned)nca * 16u, &bar, pol);
+        if (ncb > 0) bulk_load(sB, in + cb, (unsigned)ncb * 16u, &bar, pol);
+    }
+    if (!aligned16) {  // uniform across the CTA: nothing was issued
+        if (threadIdx.x == 0) atomicOr(status, kStatusMisaligned);
+        return;
+    }
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {  // a copy never landed: report, drain, leave
+        if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+        if (!ok) mbar_wait(&bar, 0);
+        return;
+    }
+    const int32_t *A = sA + (int)(ga - ca), *B = sB + (int)(gb - cb);
+
+    const int diag = threadIdx.x * EO;
+    const int lane = threadIdx.x & 31;
+    const int dcl = diag < tot ? diag : tot;
+    int lo = dcl > nb ? dcl - nb : 0, hi = dcl < na ? dcl : na;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] <= B[dcl - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    int end = __shfl_down_sync(0xffffffffu, lo, 1);
+    if (lane == 0) wsplit[threadIdx.x >> 5] = lo;
+    if (threadIdx.x == 0) wsplit[NT / 32] = na;
+    __syncthreads();
+    const int dend = (diag + EO) < tot ? (diag + EO) : tot;
+    if (lane == 31) end = wsplit[(threadIdx.x >> 5) + 1];
+    if (dend == tot) end = na;
+    int32_t x[P];
+    const int cnt = dend - dcl;
+    if (cnt > 0) exact_window_merge<EO, P>(A, lo, B, dcl - lo, end - lo, cnt, x);
+    __syncthreads();
+    if (cnt > 0) {
+#pragma unroll
+        for (int k = 0; k < EO; ++k)
+            if (k < cnt) sA[diag + k] = x[k];
+        fence_proxy_async_smem();
+        if (samp) {
+            // Output positions m.gs + o0 + diag + k; m.gs + o0 is a multiple of 32.
+#pragma unroll
+            for (int j = 0; j < (EO + 31) / 32; ++j) {
+                const int k = ((-diag) & 31) + 32 * j;
+                if (k < cnt) samp[(m.gs + o0 + diag + k) / kSampleStride] = select_dyn(x, k);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // 16-byte aligned: m.gs + o0 and tot are multiples of 4 keys.
+        bulk_store(out + m.gs + o0, sA, (unsigned)tot * 4u, pol);
+        bulk_wait_read();
+    }
+}
+
+// Partition pass + one tiled merge launch for one level.  With samp (samples
+// of kin at stride kSampleStride) the partition searches the samples first,
+// and the merge writes the samples of kout for the next level.
+// Partition pass of one tiled level: part[b] = A keys before output tile b.
+static hs_status launch_partition(const int32_t *kin, int64_t n, int64_t w, int to,
+                                  const LevelTiles &lt, int64_t *part, const int32_t *samp,
+                                  cudaStream_t st) {
+    LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
+    const unsigned pgrid = (unsigned)((lt.nblocks + 255) / 256);
+    if (samp)
+        k_merge_partition_sampled<<<pgrid, 256, 0, st>>>(kin, samp, n, w, to, (int)lt.tpg,
+                                                          lt.nblocks, part);
+    else
+        k_merge_partition<<<pgrid, 256, 0, st>>>(kin, n, w, to, (int)lt.tpg, lt.nblocks, part);
+    return launch_end(t);
+}
+
 // Partition pass + one tiled merge launch for one level.  With samp (samples
 // of kin at stride kSampleStride) the partition searches the samples first,
 // and the merge writes the samples of kout for the next level.
@@ -183,29 +301,43 @@ static hs_status launch_tile(const int32_t *kin, int32_t *kout, int64_t n, int64
                              int64_t *part, int32_t *samp, cudaStream_t st) {
     static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
     const LevelTiles lt = level_tiles(n, w, C::TO);
-    LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
-    const unsigned pgrid = (unsigned)((lt.nblocks + 255) / 256);
-    if (samp)
-        k_merge_partition_sampled<<<pgrid, 256, 0, st>>>(kin, samp, n, w, C::TO, (int)lt.tpg,
-                                                          lt.nblocks, part);
-    else
-        k_merge_partition<<<pgrid, 256, 0, st>>>(kin, n, w, C::TO, (int)lt.tpg, lt.nblocks, part);
-    hs_status r = launch_end(t);
+    hs_status r = launch_partition(kin, n, w, C::TO, lt, part, samp, st);
     if (r != HS_OK) return r;
     if ((r = ensure_smem((const void *)KERN, C::SMEM_BYTES)) != HS_OK) return r;
     constexpr int NTH = C::TO / C::EOUT;
-    t = launch_begin(K_MERGE_KEYS, st);
+    LaunchToken t = launch_begin(K_MERGE_KEYS, st);
     KERN<<<(unsigned)lt.nblocks, NTH, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, (int)lt.tpg, samp);
     return launch_end(t);
 }
 
-constexpr int kDefaultMergeTile = 5;
+// The same with the bulk-copy kernel (k_merge_tile_bulk), which also takes
+// the device status word for its bounded copy wait.
+template <int NT, int EO>
+static hs_status launch_tile_bulk(const int32_t *kin, int32_t *kout, int64_t n, int64_t w,
+                                  int64_t *part, int32_t *samp, cudaStream_t st) {
+    using C = TileMerge2<NT, EO>;
+    static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
+    unsigned *status = nullptr;
+    hs_status r = device_status(&status);
+    if (r != HS_OK) return r;
+    const LevelTiles lt = level_tiles(n, w, C::TO);
+    if ((r = launch_partition(kin, n, w, C::TO, lt, part, samp, st)) != HS_OK) return r;
+    auto kern = k_merge_tile_bulk<NT, EO>;
+    if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
+    LaunchToken t = launch_begin(K_MERGE_KEYS, st);
+    kern<<<(unsigned)lt.nblocks, NT, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, (int)lt.tpg, samp,
+                                                          status);
+    return launch_end(t);
+}
 
-// One tiled keys level; `shape` is the option "merge_tile": 5 (the default,
-// 96 threads x 31 keys, exact windows: small CTAs, many per SM, so loads,
-// merges and stores of neighbouring CTAs overlap), 0 (window form, 256 x 15),
-// and the exact-window variants 1 (64 x 31), 2 (128 x 31), 3 (64 x 63),
-// 4 (128 x 23), 6 (192 x 31), 7 (256 x 31).
+constexpr int kDefaultMergeTile = 9;
+
+// One tiled keys level; `shape` is the option "merge_tile": 9 (the default,
+// bulk-copy form k_merge_tile_bulk, 128 threads x 31 keys: the copy engine
+// moves the tile in and out, small CTAs keep many tiles in flight per SM),
+// 8 (bulk, 96 x 31), 10 (bulk, 192 x 31); the cp.async exact-window forms
+// 5 (96 x 31), 1 (64 x 31), 2 (128 x 31), 3 (64 x 63), 4 (128 x 23),
+// 6 (192 x 31), 7 (256 x 31); and 0 (window form, 256 x 15).
 static hs_status launch_keys_tile_level(int shape, const int32_t *kin, int32_t *kout, int64_t n,
                                         int64_t w, int64_t *part, int32_t *samp, cudaStream_t st) {
     switch (shape) {
@@ -214,9 +346,12 @@ static hs_status launch_keys_tile_level(int shape, const int32_t *kin, int32_t *
         case 2: return launch_tile<k_merge_tile2<128, 31>, TileMerge2<128, 31>>(kin, kout, n, w, part, samp, st);
         case 3: return launch_tile<k_merge_tile2<64, 63>, TileMerge2<64, 63>>(kin, kout, n, w, part, samp, st);
         case 4: return launch_tile<k_merge_tile2<128, 23>, TileMerge2<128, 23>>(kin, kout, n, w, part, samp, st);
+        case 5: return launch_tile<k_merge_tile2<96, 31>, TileMerge2<96, 31>>(kin, kout, n, w, part, samp, st);
         case 6: return launch_tile<k_merge_tile2<192, 31>, TileMerge2<192, 31>>(kin, kout, n, w, part, samp, st);
         case 7: return launch_tile<k_merge_tile2<256, 31>, TileMerge2<256, 31>>(kin, kout, n, w, part, samp, st);
-        default: return launch_tile<k_merge_tile2<96, 31>, TileMerge2<96, 31>>(kin, kout, n, w, part, samp, st);
+        case 8: return launch_tile_bulk<96, 31>(kin, kout, n, w, part, samp, st);
+        case 10: return launch_tile_bulk<192, 31>(kin, kout, n, w, part, samp, st);
+        default: return launch_tile_bulk<128, 31>(kin, kout, n, w, part, samp, st);
     }
 }
 

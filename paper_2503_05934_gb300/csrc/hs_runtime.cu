@@ -134,6 +134,8 @@ hs_status device_check(cudaStream_t st) {
             return fail_cuda(e, "hs_device_check: clear status");
         if (v & kStatusTimeout)
             return fail(HS_ERR_TIMEOUT, "a kernel gave up on a bounded wait");
+        if (v & kStatusMisaligned)
+            return fail(HS_ERR_CUDA, "a kernel found bulk-copy addresses that are not 16-byte aligned");
         return fail(HS_ERR_INVALID_ARG, "a kernel found malformed segment offsets");
     }
     return HS_OK;
@@ -333,8 +335,8 @@ hs_status hs_set_option(const char *name, int64_t value) {
         return HS_OK;
     }
     if (std::strcmp(name, "merge_tile") == 0) {
-        if (value < 0 || value > 7)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_tile must be 0..7");
+        if (value < 0 || value > 10)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_tile must be 0..10");
         merge_set_tile((int)value);
         return HS_OK;
     }

@@ -242,7 +242,7 @@ def test_many_duplicates_and_runs(hs):
         assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), mod
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("samples", [0, 1])
 def test_merge_tile_shapes_and_samples(hs, tile, samples):
     """Every tiled merge-level shape, with and without sampled partition
@@ -259,7 +259,7 @@ def test_merge_tile_shapes_and_samples(hs, tile, samples):
                     a = g.keys(n, "nearly", n + tile)
                 assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), (n, kind)
     finally:
-        hs.hs_set_option("merge_tile", 5)
+        hs.hs_set_option("merge_tile", 9)
         hs.hs_set_option("merge_samples", 1)
 
 
