@@ -336,8 +336,16 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *   "pairs_blocksort": pair block-sort shape, 0 (default) 256 threads x 4
  *     leaves, 1: 512 x 2, 2: 512 x 4, 3: 288 x 4.
  *   "pairs_merge": tiled pair levels (16-byte aligned keys and values,
- *     n % 4 == 0) with 1 (default) 128 threads x 31 pairs or 2 96 x 31,
- *     both with sampled partition searches; 0 staged-load serial merges.
+ *     n % 4 == 0) with 3 (default) 128 threads x 31 pairs moved in and out
+ *     by bulk copies, 1 the same staged by cp.async, 2 96 x 31 staged by
+ *     cp.async, all with sampled partition searches; 0 staged-load serial
+ *     merges.
+ *   "blocksort_bulk": keys block sort of the merge path with 1 (default)
+ *     each full tile moved in and out by one bulk copy when the array is
+ *     16-byte aligned, 0 tiles staged by the threads.
+ *   "i64_merge": int64 merge levels (hs_sort_i64) with 1 (default) tiles
+ *     moved in and out by bulk copies when both buffers are 16-byte aligned
+ *     and n is even, 0 tiles staged by cp.async.
  *     Every option gives identical results.
  * Unknown names or values return HS_ERR_INVALID_ARG. */
 HS_API hs_status hs_set_option(const char *name, int64_t value);

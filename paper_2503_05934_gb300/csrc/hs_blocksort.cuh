@@ -11,6 +11,7 @@
 //    memory and are gathered once, by position, at the end.
 #pragma once
 
+#include "hs_bulk.cuh"
 #include "hs_merge_prims.cuh"
 #include "hs_networks.cuh"
 
@@ -240,6 +241,74 @@ __global__ void __launch_bounds__(NT, blocksort_min_ctas(NT))
     const int cnt = (int)((n - base) < T ? (n - base) : T);
     block_sort_tile3<NT, L, LEAVES>(kin + base, kout + base, cnt, netset, vec != 0, smem, samp,
                                     base);
+}
+
+// Bulk-copy form for 16-byte aligned arrays: a full tile arrives by one bulk
+// copy (completion counted on an mbarrier) and leaves by one bulk store, and
+// each thread writes the samples among its own keys from registers, so the
+// load/store units carry only the merge levels' shared-memory traffic.  A
+// partial last tile takes block_sort_tile3's plain path.  Same results as
+// k_blocksort3.
+template <int NT, int L, int LEAVES = 2>
+__global__ void __launch_bounds__(NT, blocksort_min_ctas(NT))
+    k_blocksort3_bulk(const int32_t *kin, int32_t *kout, int64_t n, uint32_t netset,
+                      int32_t *samp, unsigned *status) {
+    using C = BlockSort3<NT, L, LEAVES>;
+    constexpr int EO = C::EO, P = C::P, T = C::T;
+    static_assert(T % kSampleStride == 0 && kSampleStride == 32, "tiles start on sample positions");
+    extern __shared__ __align__(16) int32_t smem[];
+    __shared__ __align__(8) uint64_t bar;
+    const int64_t base = (int64_t)blockIdx.x * T;
+    const int cnt = (int)((n - base) < T ? (n - base) : T);
+    if (cnt < T) {  // uniform across the CTA
+        block_sort_tile3<NT, L, LEAVES>(kin + base, kout + base, cnt, netset, true, smem, samp,
+                                        base);
+        return;
+    }
+    int *wsplit = smem + T + P + 32;
+    const uint64_t pol = l2_evict_first_policy();
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    // T % 4 == 0 and the arrays are 16-byte aligned: both ends of each copy are.
+    const bool aligned16 = (smem_addr(smem) & 15u) == 0 &&
+                           ((reinterpret_cast<uintptr_t>(kin + base) |
+                             reinterpret_cast<uintptr_t>(kout + base)) & 15u) == 0;
+    if (!aligned16) {  // uniform across the CTA: nothing was issued
+        if (threadIdx.x == 0) atomicOr(status, kStatusMisaligned);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, (unsigned)T * 4u);
+        bulk_load(smem, kin + base, (unsigned)T * 4u, &bar, pol);
+    }
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {  // the copy never landed: report, drain, leave
+        if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+        if (!ok) mbar_wait(&bar, 0);
+        return;
+    }
+    const int my0 = threadIdx.x * EO;
+    int32_t k[EO];
+#pragma unroll
+    for (int j = 0; j < EO; ++j) k[j] = smem[my0 + j];
+    sort_thread_leaves<L, LEAVES, P>(k, T - my0, netset);
+    block_merge_levels<NT, EO, P, false>(smem, wsplit, k, T);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < EO; ++j) smem[my0 + j] = k[j];
+    fence_proxy_async_smem();
+    if (samp) {
+#pragma unroll
+        for (int j = 0; j < (EO + 31) / 32; ++j) {
+            const int q = ((-my0) & 31) + 32 * j;
+            if (q < EO) samp[(base + my0 + q) / kSampleStride] = select_dyn(k, q);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bulk_store(kout + base, smem, (unsigned)T * 4u, pol);
+        bulk_wait_read();
+    }
 }
 
 // ---------------------------------------------------------------------------

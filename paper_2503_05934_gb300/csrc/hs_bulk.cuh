@@ -82,12 +82,14 @@ HS_DEV void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" :
 // (async proxy) that read them.
 HS_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// x[k] for a run-time k in [0, P) without local memory: a select tree on k's bits.
-template <int P, class K>
-HS_DEV K select_dyn(const K (&x)[P], int k) {
+// x[k] for a run-time k in [0, N) without local memory: a select tree on k's bits.
+template <int N, class K>
+HS_DEV K select_dyn(const K (&x)[N], int k) {
+    constexpr int P = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : N <= 32 ? 32 : 64;
+    static_assert(N <= P, "select_dyn covers arrays of up to 64 entries");
     K v[P];
 #pragma unroll
-    for (int i = 0; i < P; ++i) v[i] = x[i];
+    for (int i = 0; i < P; ++i) v[i] = x[i < N ? i : 0];
 #pragma unroll
     for (int h = P / 2; h >= 1; h /= 2) {
         const bool up = (k & h) != 0;

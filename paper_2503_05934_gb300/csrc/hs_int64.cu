@@ -10,6 +10,7 @@
 // aligned array works.
 #include <algorithm>
 
+#include "hs_bulk.cuh"
 #include "hs_internal.h"
 #include "hs_blocksort.cuh"
 
@@ -208,6 +209,101 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
+// Bulk-copy form for 16-byte aligned buffers with n even: one thread issues
+// the two cover copies (cp.async.bulk, completion counted on an mbarrier)
+// and, once the tile is merged, one bulk store of the output tile; each
+// thread writes the samples among its own outputs from registers.  Same
+// merge and results as k_merge_tile64.
+template <int NT, int EO>
+__global__ void __launch_bounds__(NT)
+    k_merge_tile64_bulk(const K64 *in, K64 *out, int64_t n, int64_t w, const int64_t *part,
+                        int tpg, K64 *samp, unsigned *status) {
+    using C = TileMerge64<NT, EO>;
+    constexpr int TO = C::TO, P = C::P;
+    static_assert(kSampleStride == 32, "sample positions are multiples of 32");
+    extern __shared__ __align__(16) K64 s64[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int wsplit[NT / 32 + 1];
+    const int64_t g = blockIdx.x / tpg;
+    const int t = blockIdx.x - (int)(g * tpg);
+    const MergeGeom m = merge_geom(g, n, w);
+    const int64_t glen = m.alen + m.blen;
+    const int64_t o0 = (int64_t)t * TO;
+    const int64_t o1 = (o0 + TO) < glen ? (o0 + TO) : glen;
+    const int64_t a0 = part[blockIdx.x];
+    const int64_t a1 = (o1 == glen) ? m.alen : part[blockIdx.x + 1];
+    const int na = (int)(a1 - a0);
+    const int tot = (int)(o1 - o0);
+    const int nb = tot - na;
+    const int64_t ga = m.gs + a0, gb = m.gs + w + (o0 - a0);
+    const int64_t ca = ga & ~int64_t(1), cb = gb & ~int64_t(1);
+    const int nca = (int)(((ga + na + 1) & ~int64_t(1)) - ca) / 2;  // 16-byte words
+    const int ncb = (int)(((gb + nb + 1) & ~int64_t(1)) - cb) / 2;
+    const uint64_t pol = l2_evict_first_policy();
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool aligned16 = (smem_addr(s64) & 15u) == 0 &&
+                           ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+    if (!aligned16) {  // uniform across the CTA: nothing was issued
+        if (threadIdx.x == 0) atomicOr(status, kStatusMisaligned);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, (unsigned)(nca + ncb) * 16u);
+        if (nca > 0) bulk_load(s64, in + ca, (unsigned)nca * 16u, &bar, pol);
+        if (ncb > 0) bulk_load(s64 + 2 * nca, in + cb, (unsigned)ncb * 16u, &bar, pol);
+    }
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {  // a copy never landed: report, drain, leave
+        if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+        if (!ok) mbar_wait(&bar, 0);
+        return;
+    }
+    const K64 *A = s64 + (int)(ga - ca);
+    const K64 *B = s64 + 2 * nca + (int)(gb - cb);
+
+    const int diag = threadIdx.x * EO;
+    const int lane = threadIdx.x & 31;
+    const int dcl = diag < tot ? diag : tot;
+    int lo = dcl > nb ? dcl - nb : 0, hi = dcl < na ? dcl : na;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] <= B[dcl - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    int end = __shfl_down_sync(0xffffffffu, lo, 1);
+    if (lane == 0) wsplit[threadIdx.x >> 5] = lo;
+    if (threadIdx.x == 0) wsplit[NT / 32] = na;
+    __syncthreads();
+    const int dend = (diag + EO) < tot ? (diag + EO) : tot;
+    if (lane == 31) end = wsplit[(threadIdx.x >> 5) + 1];
+    if (dend == tot) end = na;
+    K64 x[P];
+    const int cnt = dend - dcl;
+    if (cnt > 0) exact_window_merge<EO, P>(A, lo, B, dcl - lo, end - lo, cnt, x);
+    __syncthreads();
+    if (cnt > 0) {
+#pragma unroll
+        for (int k = 0; k < EO; ++k)
+            if (k < cnt) s64[diag + k] = x[k];
+        fence_proxy_async_smem();
+        if (samp) {
+            // Output positions m.gs + o0 + diag + k; m.gs + o0 is a multiple of 32.
+#pragma unroll
+            for (int j = 0; j < (EO + 31) / 32; ++j) {
+                const int k = ((-diag) & 31) + 32 * j;
+                if (k < cnt) samp[(m.gs + o0 + diag + k) / kSampleStride] = select_dyn(x, k);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // 16-byte aligned: m.gs + o0 and tot are even.
+        bulk_store(out + m.gs + o0, s64, (unsigned)tot * 8u, pol);
+        bulk_wait_read();
+    }
+}
+
 // ---------------------------------------------------------------- planner
 
 // Block sort: 256 threads x four leaves (7936 keys for {6,7,8}).  A 288-thread
@@ -218,6 +314,11 @@ constexpr int B64_NT = 256;
 constexpr int M64_NT = 96, M64_EO = 31;      // merge level: 96 threads x 31 keys
 
 int64_t tile64(int L, int64_t) { return (int64_t)B64_NT * (4 * L - 1); }
+
+// Merge level form (option "i64_merge"): 1 (default) k_merge_tile64_bulk when
+// the buffers are 16-byte aligned and n is even, 0 the cp.async-staged form.
+static int g_i64_bulk = 1;
+void i64_set_bulk(int v) { g_i64_bulk = v; }
 
 size_t merge_workspace_bytes_i64(size_t n) {
     return ws_align(n * sizeof(K64)) + merge_ws_part_bytes(n) + ws_align((n / 32 + 8) * sizeof(K64));
@@ -277,17 +378,26 @@ hs_status merge_sort_i64(int64_t *d_keys, size_t n_, hs_netset s, void *d_ws, si
     using C = TileMerge64<M64_NT, M64_EO>;
     static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
     const bool vec = aligned(d_keys, 16) && (!kbuf || aligned(kbuf, 16)) && (n % 2) == 0;
+    const bool bulk = vec && g_i64_bulk;
     auto kern = vec ? k_merge_tile64<M64_NT, M64_EO, true> : k_merge_tile64<M64_NT, M64_EO, false>;
+    auto kern_bulk = k_merge_tile64_bulk<M64_NT, M64_EO>;
+    unsigned *status = nullptr;
+    if (bulk && passes > 0 && (r = device_status(&status)) != HS_OK) return r;
     for (int64_t w = T; w < n; w *= 2) {
         const LevelTiles lt = level_tiles(n, w, C::TO);
         LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
         k_merge_partition_sampled64<<<(unsigned)((lt.nblocks + 255) / 256), 256, 0, st>>>(
             kcur, samp, n, w, C::TO, (int)lt.tpg, lt.nblocks, part);
         if ((r = launch_end(t)) != HS_OK) return r;
-        if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
+        if ((r = ensure_smem(bulk ? (const void *)kern_bulk : (const void *)kern, C::SMEM_BYTES)) != HS_OK)
+            return r;
         t = launch_begin(K_MERGE_KEYS, st);
-        kern<<<(unsigned)lt.nblocks, M64_NT, C::SMEM_BYTES, st>>>(kcur, kalt, n, w, part, (int)lt.tpg,
-                                                                  samp);
+        if (bulk)
+            kern_bulk<<<(unsigned)lt.nblocks, M64_NT, C::SMEM_BYTES, st>>>(kcur, kalt, n, w, part,
+                                                                           (int)lt.tpg, samp, status);
+        else
+            kern<<<(unsigned)lt.nblocks, M64_NT, C::SMEM_BYTES, st>>>(kcur, kalt, n, w, part,
+                                                                      (int)lt.tpg, samp);
         if ((r = launch_end(t)) != HS_OK) return r;
         std::swap(kcur, kalt);
     }

@@ -48,14 +48,28 @@ int64_t keys_tile(int L, int64_t n) { return shape_tile(shape_for(n, L), L); }
 void merge_set_blocksort_threads(int nt) { g_bs_shape = (nt == 1024) ? 1 : 0; }
 void merge_set_blocksort_shape(int v) { g_bs_shape = v; }
 
+// Option "blocksort_bulk": 1 (default) 16-byte aligned arrays use the
+// bulk-copy form (k_blocksort3_bulk), 0 the thread-staged form.
+static int g_bs_bulk = 1;
+void merge_set_blocksort_bulk(int v) { g_bs_bulk = v; }
+
 template <int NT, int L, int LEAVES>
 static hs_status launch_blocksort_t(const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
                                     int vec, int32_t *samp, cudaStream_t st) {
     using C = BlockSort3<NT, L, LEAVES>;
-    auto kern = k_blocksort3<NT, L, LEAVES>;
-    hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
-    if (r != HS_OK) return r;
     const int64_t grid = (n + C::T - 1) / C::T;
+    hs_status r;
+    if (vec && g_bs_bulk) {
+        unsigned *status = nullptr;
+        if ((r = device_status(&status)) != HS_OK) return r;
+        auto kern = k_blocksort3_bulk<NT, L, LEAVES>;
+        if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
+        LaunchToken t = launch_begin(K_BLOCKSORT_KEYS, st);
+        kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, samp, status);
+        return launch_end(t);
+    }
+    auto kern = k_blocksort3<NT, L, LEAVES>;
+    if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
     LaunchToken t = launch_begin(K_BLOCKSORT_KEYS, st);
     kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, vec, samp);
     return launch_end(t);

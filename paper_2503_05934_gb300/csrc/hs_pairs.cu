@@ -4,6 +4,7 @@
 // reads and writes both once.
 #include <algorithm>
 
+#include "hs_bulk.cuh"
 #include "hs_internal.h"
 #include "hs_blocksort.cuh"
 
@@ -114,6 +115,133 @@ __global__ void __launch_bounds__(NT)
     store_tile_out<NT>(dv, sV, tot, nullptr, 0);
 }
 
+// Bulk-copy form of the tiled pairs level: one thread issues the four cover
+// copies (keys and values of A and B, cp.async.bulk, completion counted on an
+// mbarrier) and, once the tile is merged, one bulk store each of the output
+// keys and values; each thread writes the samples among its own outputs from
+// registers.  Same merge and results as k_merge_tile_pairs.
+template <int NT, int EO>
+__global__ void __launch_bounds__(NT)
+    k_merge_tile_pairs_bulk(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
+                            int64_t n, int64_t w, const int64_t *part, int tpg, int32_t *samp,
+                            unsigned *status) {
+    using C = TileMergePairs<NT, EO>;
+    constexpr int TO = C::TO;
+    static_assert(kSampleStride == 32, "sample positions are multiples of 32");
+    extern __shared__ __align__(16) int32_t smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int wsplit[NT / 32 + 1];
+    int32_t *sK = smem, *sV = smem + C::REG;
+    const int64_t g = blockIdx.x / tpg;
+    const int t = blockIdx.x - (int)(g * tpg);
+    const MergeGeom m = merge_geom(g, n, w);
+    const int64_t glen = m.alen + m.blen;
+    const int64_t o0 = (int64_t)t * TO;
+    const int64_t o1 = (o0 + TO) < glen ? (o0 + TO) : glen;
+    const int64_t a0 = part[blockIdx.x];
+    const int64_t a1 = (o1 == glen) ? m.alen : part[blockIdx.x + 1];
+    const int na = (int)(a1 - a0);
+    const int tot = (int)(o1 - o0);
+    const int nb = tot - na;
+    const int64_t ga = m.gs + a0, gb = m.gs + w + (o0 - a0);
+    const int64_t ca = ga & ~int64_t(3), cb = gb & ~int64_t(3);
+    const int nca = (int)(((ga + na + 3) & ~int64_t(3)) - ca) / 4;
+    const int ncb = (int)(((gb + nb + 3) & ~int64_t(3)) - cb) / 4;
+    const uint64_t pol = l2_evict_first_policy();
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    // C::REG is a multiple of 4 words, so sV and both B covers start on 16 bytes.
+    const bool aligned16 = ((smem_addr(sK) | smem_addr(sV)) & 15u) == 0 &&
+                           ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(kout) |
+                             reinterpret_cast<uintptr_t>(vin) | reinterpret_cast<uintptr_t>(vout)) & 15u) == 0;
+    if (!aligned16) {  // uniform across the CTA: nothing was issued
+        if (threadIdx.x == 0) atomicOr(status, kStatusMisaligned);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, (unsigned)(nca + ncb) * 32u);
+        if (nca > 0) {
+            bulk_load(sK, kin + ca, (unsigned)nca * 16u, &bar, pol);
+            bulk_load(sV, vin + ca, (unsigned)nca * 16u, &bar, pol);
+        }
+        if (ncb > 0) {
+            bulk_load(sK + 4 * nca, kin + cb, (unsigned)ncb * 16u, &bar, pol);
+            bulk_load(sV + 4 * nca, vin + cb, (unsigned)ncb * 16u, &bar, pol);
+        }
+    }
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {  // a copy never landed: report, drain, leave
+        if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+        if (!ok) mbar_wait(&bar, 0);
+        return;
+    }
+    const int offA = (int)(ga - ca), offB = 4 * nca + (int)(gb - cb);
+    const int32_t *A = sK + offA, *B = sK + offB;
+    const int32_t *VA = sV + offA, *VB = sV + offB;
+
+    const int diag = threadIdx.x * EO;
+    const int lane = threadIdx.x & 31;
+    const int dcl = diag < tot ? diag : tot;
+    int lo = dcl > nb ? dcl - nb : 0, hi = dcl < na ? dcl : na;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] <= B[dcl - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    int end = __shfl_down_sync(0xffffffffu, lo, 1);
+    if (lane == 0) wsplit[threadIdx.x >> 5] = lo;
+    if (threadIdx.x == 0) wsplit[NT / 32] = na;
+    __syncthreads();
+    const int dend = (diag + EO) < tot ? (diag + EO) : tot;
+    if (lane == 31) end = wsplit[(threadIdx.x >> 5) + 1];
+    if (dend == tot) end = na;
+    const int cnt = dend - dcl;
+
+    // Serial stable merge, as in k_merge_tile_pairs.
+    int32_t ok_[EO], ov[EO];
+    {
+        int ia = lo, ib = dcl - lo;
+        const int eb = ib + cnt - (end - lo);
+        int32_t ka = A[ia], kb = B[ib];
+#pragma unroll
+        for (int k = 0; k < EO; ++k) {
+            const bool take_b = (ib < eb) && ((ia >= end) || (kb < ka));
+            ok_[k] = take_b ? kb : ka;
+            ov[k] = take_b ? VB[ib] : VA[ia];
+            ib += take_b;
+            ia += !take_b;
+            const int32_t nx = take_b ? B[ib] : A[ia];
+            kb = take_b ? nx : kb;
+            ka = take_b ? ka : nx;
+        }
+    }
+    __syncthreads();
+    if (cnt > 0) {
+#pragma unroll
+        for (int k = 0; k < EO; ++k) {
+            if (k < cnt) {
+                sK[diag + k] = ok_[k];
+                sV[diag + k] = ov[k];
+            }
+        }
+        fence_proxy_async_smem();
+        if (samp) {
+#pragma unroll
+            for (int j = 0; j < (EO + 31) / 32; ++j) {
+                const int k = ((-diag) & 31) + 32 * j;
+                if (k < cnt) samp[(m.gs + o0 + diag + k) / kSampleStride] = select_dyn(ok_, k);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // 16-byte aligned: m.gs + o0 and tot are multiples of 4 pairs.
+        bulk_store(kout + m.gs + o0, sK, (unsigned)tot * 4u, pol);
+        bulk_store(vout + m.gs + o0, sV, (unsigned)tot * 4u, pol);
+        bulk_wait_read();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Planner.
 
@@ -122,10 +250,11 @@ __global__ void __launch_bounds__(NT)
 // leaves (one CTA per SM), 3 = 288 x 4 leaves (tiles of at least 8192 pairs
 // for the {6,7,8} set).
 static int g_pairs_bs = 0;
-// Merge level (option "pairs_merge"): 1 = tiled, 128 threads x 31 pairs (the
-// default when aligned), 2 = tiled, 96 x 31, 0 = the generic
-// serial-merge pass.  The tiled levels use sampled partition searches.
-static int g_pairs_merge = 1;
+// Merge level (option "pairs_merge"): 3 = tiled, 128 threads x 31 pairs moved
+// by bulk copies (the default when aligned), 1 = tiled, 128 x 31 staged by
+// cp.async, 2 = the same with 96 x 31, 0 = the generic serial-merge pass.
+// The tiled levels use sampled partition searches.
+static int g_pairs_merge = 3;
 
 void pairs_set_blocksort(int v) { g_pairs_bs = v; }
 void pairs_set_merge(int v) { g_pairs_merge = v; }
@@ -171,7 +300,7 @@ static hs_status launch_pairs_blocksort_nt(int L, const int32_t *kin, int32_t *k
 
 constexpr int PG_NT = 256, PG_E = 8;  // generic level
 
-template <int NT, int EO>
+template <int NT, int EO, bool BULK>
 static hs_status launch_pairs_tile(const int32_t *kin, int32_t *kout, const int32_t *vin,
                                    int32_t *vout, int64_t n, int64_t w, int64_t *part,
                                    int32_t *samp, cudaStream_t st) {
@@ -183,6 +312,16 @@ static hs_status launch_pairs_tile(const int32_t *kin, int32_t *kout, const int3
         kin, samp, n, w, C::TO, (int)lt.tpg, lt.nblocks, part);
     hs_status r = launch_end(t);
     if (r != HS_OK) return r;
+    if constexpr (BULK) {
+        unsigned *status = nullptr;
+        if ((r = device_status(&status)) != HS_OK) return r;
+        auto kern = k_merge_tile_pairs_bulk<NT, EO>;
+        if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
+        t = launch_begin(K_MERGE_PAIRS, st);
+        kern<<<(unsigned)lt.nblocks, NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, w, part,
+                                                              (int)lt.tpg, samp, status);
+        return launch_end(t);
+    }
     auto kern = k_merge_tile_pairs<NT, EO>;
     if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
     t = launch_begin(K_MERGE_PAIRS, st);
@@ -197,9 +336,11 @@ static hs_status launch_pairs_level(const int32_t *kin, int32_t *kout, const int
                                     int32_t *vout, int64_t n, int64_t w, int64_t *part,
                                     int32_t *samp, int vec, cudaStream_t st) {
     if (pairs_tiled(n, vec)) {
-        return g_pairs_merge == 1
-                   ? launch_pairs_tile<128, 31>(kin, kout, vin, vout, n, w, part, samp, st)
-                   : launch_pairs_tile<96, 31>(kin, kout, vin, vout, n, w, part, samp, st);
+        switch (g_pairs_merge) {
+            case 1: return launch_pairs_tile<128, 31, false>(kin, kout, vin, vout, n, w, part, samp, st);
+            case 2: return launch_pairs_tile<96, 31, false>(kin, kout, vin, vout, n, w, part, samp, st);
+            default: return launch_pairs_tile<128, 31, true>(kin, kout, vin, vout, n, w, part, samp, st);
+        }
     }
     const LevelTiles lt = level_tiles(n, w, PG_NT * PG_E);
     LaunchToken t = launch_begin(K_MERGE_PARTITION, st);

@@ -364,9 +364,21 @@ hs_status hs_set_option(const char *name, int64_t value) {
         pairs_set_blocksort((int)value);
         return HS_OK;
     }
+    if (std::strcmp(name, "blocksort_bulk") == 0) {
+        if (value != 0 && value != 1)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_bulk must be 0 or 1");
+        merge_set_blocksort_bulk((int)value);
+        return HS_OK;
+    }
+    if (std::strcmp(name, "i64_merge") == 0) {
+        if (value != 0 && value != 1)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: i64_merge must be 0 or 1");
+        i64_set_bulk((int)value);
+        return HS_OK;
+    }
     if (std::strcmp(name, "pairs_merge") == 0) {
-        if (value < 0 || value > 2)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: pairs_merge must be 0..2");
+        if (value < 0 || value > 3)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: pairs_merge must be 0..3");
         pairs_set_merge((int)value);
         return HS_OK;
     }

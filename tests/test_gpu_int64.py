@@ -39,6 +39,23 @@ def test_int64_sizes_and_distributions(hs, netset):
             assert np.array_equal(gpu_sort64(hs, a, netset), oracle.merge_sort_i64(a, netset)), (n, dist)
 
 
+@pytest.mark.parametrize("form", [0, 1])
+def test_int64_merge_level_forms(hs, form):
+    """Both int64 merge-level forms (tiles staged by cp.async, or moved by
+    bulk copies) give the oracle's result: tile edges of the 2976-key merge
+    tile, odd multiples of the block-sort tile, few distinct keys."""
+    hs.hs_set_option("i64_merge", form)
+    try:
+        for n in [3 * 2976 + 2, 2 * 7936, 3 * 7936, 100_002, 1 << 20, (1 << 20) + 2]:
+            for dist in g.DISTS:
+                a = g.keys_i64(n, dist, 5000 + n + form)
+                assert np.array_equal(gpu_sort64(hs, a), oracle.merge_sort_i64(a, "6To8")), (n, dist)
+        few = (g.keys_i64(400_002, "random", 6) % 3).astype(np.int64)
+        assert np.array_equal(gpu_sort64(hs, few), oracle.merge_sort_i64(few, "6To8"))
+    finally:
+        hs.hs_set_option("i64_merge", 1)
+
+
 def test_int64_extremes_duplicates_and_unaligned(hs):
     ext = np.array([2**63 - 1, -2**63, 0, -1, 1] * 20_001, np.int64)
     assert np.array_equal(gpu_sort64(hs, ext), np.sort(ext))

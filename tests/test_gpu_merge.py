@@ -135,7 +135,7 @@ def test_pairs_unaligned(hs):
 
 
 @pytest.mark.parametrize("bs", [0, 1, 2, 3])
-@pytest.mark.parametrize("merge", [0, 1, 2])
+@pytest.mark.parametrize("merge", [0, 1, 2, 3])
 def test_pairs_options_keep_results(hs, bs, merge):
     """Every pair block-sort shape and merge-level kernel gives the oracle's
     stable order: sizes around the tiles (7936 / 7680 / 15872 / 8928 pairs
@@ -161,7 +161,7 @@ def test_pairs_options_keep_results(hs, bs, merge):
                     assert np.array_equal(vo, ev), (n, kinds, off)
     finally:
         hs.hs_set_option("pairs_blocksort", 0)
-        hs.hs_set_option("pairs_merge", 1)
+        hs.hs_set_option("pairs_merge", 3)
 
 
 @pytest.mark.parametrize("netset", ["none", "3To5", "Odd", "3To4", "6To8", "3", "PowerOf2"])
@@ -265,10 +265,13 @@ def test_merge_tile_shapes_and_samples(hs, tile, samples):
 
 @pytest.mark.parametrize("shape", [-1, 0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("kernel", [0, 1])
-def test_tuning_options_keep_results(hs, shape, kernel):
-    """Block-sort shape and merge-level kernel change speed, not bytes."""
+@pytest.mark.parametrize("bulk", [0, 1])
+def test_tuning_options_keep_results(hs, shape, kernel, bulk):
+    """Block-sort shape, its bulk-copy form and the merge-level kernel
+    change speed, not bytes."""
     hs.hs_set_option("blocksort_shape", shape)
     hs.hs_set_option("merge_kernel", kernel)
+    hs.hs_set_option("blocksort_bulk", bulk)
     try:
         for netset in ["6To8", "3To5", "none", "Odd"]:
             for n in [1, 7, 8191, 8928, 8929, 16385, 17856, 17857, 100_003, 1 << 20]:
@@ -277,6 +280,7 @@ def test_tuning_options_keep_results(hs, shape, kernel):
     finally:
         hs.hs_set_option("blocksort_shape", -1)
         hs.hs_set_option("merge_kernel", 1)
+        hs.hs_set_option("blocksort_bulk", 1)
 
 
 def test_profiling_counters(hs):
