@@ -343,9 +343,13 @@ HS_API hs_status hs_device_check(hs_stream_t stream);
  *   "blocksort_bulk": keys block sort of the merge path with 1 (default)
  *     each full tile moved in and out by one bulk copy when the array is
  *     16-byte aligned, 0 tiles staged by the threads.
- *   "i64_merge": int64 merge levels (hs_sort_i64) with 1 (default) tiles
- *     moved in and out by bulk copies when both buffers are 16-byte aligned
- *     and n is even, 0 tiles staged by cp.async.
+ *   "pairs_blocksort_bulk": pair block sort with 1 (default) each full tile's
+ *     keys and values moved in and out by bulk copies when all four arrays
+ *     are 16-byte aligned, 0 tiles staged by the threads.
+ *   "i64_merge": int64 sorts (hs_sort_i64) with 1 (default) block-sort and
+ *     merge-level tiles moved in and out by bulk copies when the buffers are
+ *     16-byte aligned (levels: and n is even), 0 tiles staged by the threads
+ *     (block sort) and by cp.async (levels).
  *     Every option gives identical results.
  * Unknown names or values return HS_ERR_INVALID_ARG. */
 HS_API hs_status hs_set_option(const char *name, int64_t value);

@@ -324,6 +324,8 @@ struct BlockSortPairs {
     static constexpr int T = NT * EO;
     static constexpr int W_WORDS = T + P + 32;
     static constexpr int SMEM_BYTES = W_WORDS * 8 + T * 4 + (NT / 32 + 1) * 4;
+    // The bulk-copy form needs 16-byte aligned key, value and output regions.
+    static constexpr bool BULK_OK = T % 4 == 0 && W_WORDS % 2 == 0;
 };
 
 template <int NT, int L, int LEAVES = 2>
@@ -394,6 +396,83 @@ __global__ void __launch_bounds__(NT)
     const int cnt = (int)((n - base) < T ? (n - base) : T);
     block_sort_pairs_tile<NT, L, LEAVES>(kin + base, kout + base, vin + base, vout + base, cnt,
                                          netset, vec != 0, smem64, samp, base);
+}
+
+// Bulk-copy form of the pair block sort for 16-byte aligned arrays: a full
+// tile's keys and values arrive by two bulk copies (completion counted on an
+// mbarrier) and the sorted keys and gathered values leave by two bulk stores;
+// each thread writes the samples among its own keys from registers.  A
+// partial last tile takes block_sort_pairs_tile's plain path.  Same results
+// as k_blocksort_pairs.
+template <int NT, int L, int LEAVES = 2>
+__global__ void __launch_bounds__(NT)
+    k_blocksort_pairs_bulk(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
+                           int64_t n, uint32_t netset, int32_t *samp, unsigned *status) {
+    using C = BlockSortPairs<NT, L, LEAVES>;
+    constexpr int EO = C::EO, P = C::P, T = C::T;
+    static_assert(T % kSampleStride == 0 && kSampleStride == 32, "tiles start on sample positions");
+    static_assert(C::BULK_OK, "16-byte aligned key, value and output regions");
+    extern __shared__ __align__(16) int64_t smem64[];
+    __shared__ __align__(8) uint64_t bar;
+    const int64_t base = (int64_t)blockIdx.x * T;
+    const int cnt = (int)((n - base) < T ? (n - base) : T);
+    if (cnt < T) {  // uniform across the CTA
+        block_sort_pairs_tile<NT, L, LEAVES>(kin + base, kout + base, vin + base, vout + base, cnt,
+                                             netset, true, smem64, samp, base);
+        return;
+    }
+    int32_t *s32 = reinterpret_cast<int32_t *>(smem64);  // keys in, then output keys and values
+    int32_t *sv = reinterpret_cast<int32_t *>(smem64 + C::W_WORDS);  // input values
+    int *wsplit = sv + T;
+    const uint64_t pol = l2_evict_first_policy();
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool aligned16 = ((smem_addr(s32) | smem_addr(sv)) & 15u) == 0 &&
+                           ((reinterpret_cast<uintptr_t>(kin + base) |
+                             reinterpret_cast<uintptr_t>(kout + base) |
+                             reinterpret_cast<uintptr_t>(vin + base) |
+                             reinterpret_cast<uintptr_t>(vout + base)) & 15u) == 0;
+    if (!aligned16) {  // uniform across the CTA: nothing was issued
+        if (threadIdx.x == 0) atomicOr(status, kStatusMisaligned);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, (unsigned)T * 8u);
+        bulk_load(s32, kin + base, (unsigned)T * 4u, &bar, pol);
+        bulk_load(sv, vin + base, (unsigned)T * 4u, &bar, pol);
+    }
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {  // a copy never landed: report, drain, leave
+        if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+        if (!ok) mbar_wait(&bar, 0);
+        return;
+    }
+    const int my0 = threadIdx.x * EO;
+    int64_t k[EO];
+#pragma unroll
+    for (int j = 0; j < EO; ++j) k[j] = pack_word(s32[my0 + j], (uint32_t)(my0 + j));
+    sort_thread_leaves<L, LEAVES, P>(k, T - my0, netset);
+    block_merge_levels<NT, EO, P, false>(smem64, wsplit, k, T);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < EO; ++j) {
+        s32[my0 + j] = word_key(k[j]);
+        s32[T + my0 + j] = sv[word_tag(k[j])];
+    }
+    fence_proxy_async_smem();
+    if (samp) {
+#pragma unroll
+        for (int j = 0; j < (EO + 31) / 32; ++j) {
+            const int q = ((-my0) & 31) + 32 * j;
+            if (q < EO) samp[(base + my0 + q) / kSampleStride] = word_key(select_dyn(k, q));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bulk_store(kout + base, s32, (unsigned)T * 4u, pol);
+        bulk_store(vout + base, s32 + T, (unsigned)T * 4u, pol);
+        bulk_wait_read();
+    }
 }
 
 }  // namespace hs

@@ -62,6 +62,81 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
+// Bulk-copy form for 16-byte aligned arrays: a full tile arrives by one bulk
+// copy and leaves by one bulk store; each thread writes the samples among its
+// own keys from registers.  A partial last tile takes k_blocksort64's plain
+// path (the same code with vec = 0 below).  Same results as k_blocksort64.
+template <int NT, int L>
+__global__ void __launch_bounds__(NT)
+    k_blocksort64_bulk(const K64 *kin, K64 *kout, int64_t n, uint32_t netset, K64 *samp,
+                       unsigned *status) {
+    using C = BlockSort64<NT, L>;
+    constexpr int EO = C::EO, P = C::P, T = C::T;
+    static_assert(T % kSampleStride == 0 && kSampleStride == 32, "tiles start on sample positions");
+    static_assert(T % 2 == 0, "16-byte aligned tiles");
+    extern __shared__ __align__(16) K64 s64[];
+    __shared__ __align__(8) uint64_t bar;
+    int *wsplit = reinterpret_cast<int *>(s64 + T + P + 32);
+    const int64_t base = (int64_t)blockIdx.x * T;
+    const int cnt = (int)((n - base) < T ? (n - base) : T);
+    if (cnt < T) {  // uniform across the CTA: element-wise staging as in k_blocksort64
+        for (int i = threadIdx.x; i < T; i += NT) s64[i] = i < cnt ? ld_stream(kin + base + i) : word_max<K64>();
+        __syncthreads();
+    } else {
+        const uint64_t pol = l2_evict_first_policy();
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        const bool aligned16 = (smem_addr(s64) & 15u) == 0 &&
+                               ((reinterpret_cast<uintptr_t>(kin + base) |
+                                 reinterpret_cast<uintptr_t>(kout + base)) & 15u) == 0;
+        if (!aligned16) {  // uniform across the CTA: nothing was issued
+            if (threadIdx.x == 0) atomicOr(status, kStatusMisaligned);
+            return;
+        }
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(&bar, (unsigned)T * 8u);
+            bulk_load(s64, kin + base, (unsigned)T * 8u, &bar, pol);
+        }
+        const bool ok = mbar_wait(&bar, 0);
+        if (__syncthreads_or(!ok)) {  // the copy never landed: report, drain, leave
+            if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+            if (!ok) mbar_wait(&bar, 0);
+            return;
+        }
+    }
+    const int my0 = threadIdx.x * EO;
+    K64 k[EO];
+#pragma unroll
+    for (int j = 0; j < EO; ++j) k[j] = s64[my0 + j];
+    sort_thread_leaves<L, 4, P>(k, cnt - my0, netset);
+    block_merge_levels<NT, EO, P, false>(s64, wsplit, k, cnt);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < EO; ++j) s64[my0 + j] = k[j];
+    if (cnt < T) {
+        __syncthreads();
+        K64 *dst = kout + base;
+        for (int i = threadIdx.x; i < cnt; i += NT) {
+            st_stream(dst + i, s64[i]);
+            if (samp && i % kSampleStride == 0) samp[(base + i) / kSampleStride] = s64[i];
+        }
+        return;
+    }
+    fence_proxy_async_smem();
+    if (samp) {
+#pragma unroll
+        for (int j = 0; j < (EO + 31) / 32; ++j) {
+            const int q = ((-my0) & 31) + 32 * j;
+            if (q < EO) samp[(base + my0 + q) / kSampleStride] = select_dyn(k, q);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bulk_store(kout + base, s64, (unsigned)T * 8u, l2_evict_first_policy());
+        bulk_wait_read();
+    }
+}
+
 // Sampled merge-path partition (the int32 form's search on 8-byte keys).
 static __global__ void k_merge_partition_sampled64(const K64 *in, const K64 *samp, int64_t n,
                                                    int64_t w, int to, int tpg, int64_t nblocks,
@@ -315,8 +390,10 @@ constexpr int M64_NT = 96, M64_EO = 31;      // merge level: 96 threads x 31 key
 
 int64_t tile64(int L, int64_t) { return (int64_t)B64_NT * (4 * L - 1); }
 
-// Merge level form (option "i64_merge"): 1 (default) k_merge_tile64_bulk when
-// the buffers are 16-byte aligned and n is even, 0 the cp.async-staged form.
+// Tile copies (option "i64_merge"): 1 (default) the bulk-copy forms
+// (k_blocksort64_bulk for 16-byte aligned arrays, k_merge_tile64_bulk when
+// the buffers are 16-byte aligned and n is even), 0 the thread-staged block
+// sort and the cp.async-staged levels.
 static int g_i64_bulk = 1;
 void i64_set_bulk(int v) { g_i64_bulk = v; }
 
@@ -329,11 +406,21 @@ static hs_status launch_blocksort64_t(const K64 *kin, K64 *kout, int64_t n, hs_n
                                       cudaStream_t st) {
     const int vec = aligned(kin, 16) ? 1 : 0;
     using C = BlockSort64<B64_NT, L>;
+    const unsigned grid = (unsigned)((n + C::T - 1) / C::T);
+    hs_status r;
+    if (vec && aligned(kout, 16) && g_i64_bulk) {
+        unsigned *status = nullptr;
+        if ((r = device_status(&status)) != HS_OK) return r;
+        auto kern = k_blocksort64_bulk<B64_NT, L>;
+        if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
+        LaunchToken t = launch_begin(K_BLOCKSORT_KEYS, st);
+        kern<<<grid, B64_NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, samp, status);
+        return launch_end(t);
+    }
     auto kern = k_blocksort64<B64_NT, L>;
-    hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
-    if (r != HS_OK) return r;
+    if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
     LaunchToken t = launch_begin(K_BLOCKSORT_KEYS, st);
-    kern<<<(unsigned)((n + C::T - 1) / C::T), B64_NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, samp, vec);
+    kern<<<grid, B64_NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, samp, vec);
     return launch_end(t);
 }
 

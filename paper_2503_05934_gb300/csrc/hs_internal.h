@@ -100,6 +100,7 @@ void merge_set_kernel(int k);
 void merge_set_tile(int v);
 void i64_set_bulk(int v);
 void merge_set_blocksort_bulk(int v);
+void pairs_set_blocksort_bulk(int v);
 void merge_set_samples(int v);
 
 // Block sort of [0, n) in tiles of keys_tile(L) keys (the merge path's first pass;

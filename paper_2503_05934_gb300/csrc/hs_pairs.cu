@@ -268,15 +268,31 @@ int64_t pairs_tile(int L) {
     }
 }
 
+// Option "pairs_blocksort_bulk": 1 (default) 16-byte aligned arrays use the
+// bulk-copy form (k_blocksort_pairs_bulk), 0 the thread-staged form.
+static int g_pairs_bs_bulk = 1;
+void pairs_set_blocksort_bulk(int v) { g_pairs_bs_bulk = v; }
+
 template <int NT, int L, int LEAVES>
 static hs_status launch_pairs_blocksort_t(const int32_t *kin, int32_t *kout, const int32_t *vin,
                                           int32_t *vout, int64_t n, hs_netset s, int vec,
                                           int32_t *samp, cudaStream_t st) {
     using C = BlockSortPairs<NT, L, LEAVES>;
-    auto kern = k_blocksort_pairs<NT, L, LEAVES>;
-    hs_status r = ensure_smem((const void *)kern, C::SMEM_BYTES);
-    if (r != HS_OK) return r;
     const int64_t grid = (n + C::T - 1) / C::T;
+    hs_status r;
+    if constexpr (C::BULK_OK) {
+        if (vec && g_pairs_bs_bulk) {
+            unsigned *status = nullptr;
+            if ((r = device_status(&status)) != HS_OK) return r;
+            auto kern = k_blocksort_pairs_bulk<NT, L, LEAVES>;
+            if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
+            LaunchToken t = launch_begin(K_BLOCKSORT_PAIRS, st);
+            kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, s, samp, status);
+            return launch_end(t);
+        }
+    }
+    auto kern = k_blocksort_pairs<NT, L, LEAVES>;
+    if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
     LaunchToken t = launch_begin(K_BLOCKSORT_PAIRS, st);
     kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, s, vec, samp);
     return launch_end(t);

@@ -370,6 +370,12 @@ hs_status hs_set_option(const char *name, int64_t value) {
         merge_set_blocksort_bulk((int)value);
         return HS_OK;
     }
+    if (std::strcmp(name, "pairs_blocksort_bulk") == 0) {
+        if (value != 0 && value != 1)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: pairs_blocksort_bulk must be 0 or 1");
+        pairs_set_blocksort_bulk((int)value);
+        return HS_OK;
+    }
     if (std::strcmp(name, "i64_merge") == 0) {
         if (value != 0 && value != 1)
             return fail(HS_ERR_INVALID_ARG, "hs_set_option: i64_merge must be 0 or 1");

@@ -164,6 +164,30 @@ def test_pairs_options_keep_results(hs, bs, merge):
         hs.hs_set_option("pairs_merge", 3)
 
 
+@pytest.mark.parametrize("bs", [0, 3])
+@pytest.mark.parametrize("bulk", [0, 1])
+def test_pairs_blocksort_copy_forms(hs, bs, bulk):
+    """The pair block sort with its tiles moved by bulk copies or staged by
+    the threads gives the oracle's stable order: whole tiles, partial last
+    tiles and single partial tiles, few distinct keys and arbitrary values."""
+    hs.hs_set_option("pairs_blocksort", bs)
+    hs.hs_set_option("pairs_blocksort_bulk", bulk)
+    try:
+        rng = np.random.default_rng(70 + 2 * bs + bulk)
+        for n in [7936, 7940, 8928, 8932, 2 * 7936, 3 * 8928, 100_004, 1 << 20]:
+            for kinds in ["few", "wide"]:
+                hi = 5 if kinds == "few" else 1 << 31
+                k = rng.integers(-hi if kinds == "wide" else 0, hi, n, dtype=np.int64).astype(np.int32)
+                v = rng.integers(-(1 << 31), 1 << 31, n, dtype=np.int64).astype(np.int32)
+                ek, ev = oracle.merge_sort_pairs(k, v, "6To8")
+                ko, vo = gpu_sort_pairs(hs, k, v, "6To8")
+                assert np.array_equal(ko, ek), (n, kinds)
+                assert np.array_equal(vo, ev), (n, kinds)
+    finally:
+        hs.hs_set_option("pairs_blocksort", 0)
+        hs.hs_set_option("pairs_blocksort_bulk", 1)
+
+
 @pytest.mark.parametrize("netset", ["none", "3To5", "Odd", "3To4", "6To8", "3", "PowerOf2"])
 def test_pairs_all_netsets_small_words(hs, netset):
     """Every word over {0, 1, 2} of length 1..8, concatenated (ties
