@@ -309,6 +309,18 @@ HS_API hs_status hs_prof_read(const char *kernel, uint64_t *launches, double *to
  * skipped its copies), else HS_OK.  Synchronous. */
 HS_API hs_status hs_device_check(hs_stream_t stream);
 
+/* Diagnostic of the bounded waits (no counterpart in the paper: the paper's
+ * sorts run on one CPU thread).  The bulk-copy kernels wait on an mbarrier
+ * for their tile copies with a limit of 2^22 polls, after which they raise
+ * the status word and return instead of hanging.  This call launches one
+ * CTA on `stream` that arms such a barrier for 16 bytes, issues no copy and
+ * waits with a limit of `polls` polls, so its wait always gives up; a
+ * following hs_device_check(stream) returns HS_ERR_TIMEOUT (and clears the
+ * word).  Nothing is left in flight and the context stays usable.
+ *   polls  1 .. 4194304, else HS_ERR_INVALID_ARG (no launch).
+ * Asynchronous; HS_ERR_CUDA if the launch fails. */
+HS_API hs_status hs_bulk_wait_selftest(uint32_t polls, hs_stream_t stream);
+
 /* Process-wide tuning knobs (set them while no sort is in flight).
  *   "quick_max_levels": partition levels the quick path runs before its depth
  *     guard merge-sorts the segments still open (default -1 = automatic,

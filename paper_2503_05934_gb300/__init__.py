@@ -29,7 +29,8 @@ __all__ = [
     "hs_sort_i64_workspace_bytes",
     "hs_sort_host_workspace_bytes", "hs_sort_i32_host", "hs_launch_count",
     "hs_prof_enable", "hs_prof_select", "hs_prof_reset", "hs_prof_read", "hs_version", "hs_set_option",
-    "hs_sort_i32_noalloc", "NOALLOC_MAX_KEYS", "hs_device_check", "Plan", "make_plan",
+    "hs_sort_i32_noalloc", "NOALLOC_MAX_KEYS", "hs_device_check", "hs_bulk_wait_selftest",
+    "Plan", "make_plan",
     "hs_segsort_workspace_bytes", "hs_segsort_i32", "hs_sort_i32_many", "Graph",
     "hs_segsort_capture", "hs_segsort_autotune", "hs_tune_cache_save", "hs_tune_cache_load",
     "Server",
@@ -326,6 +327,12 @@ def hs_prof_read(kernel: str) -> tuple[int, float]:
 def hs_device_check(stream=None) -> None:
     """Waits for the stream and raises if a kernel reported a timed-out wait."""
     check(lib().hs_device_check(_stream_ptr(stream)))
+
+
+def hs_bulk_wait_selftest(polls: int, stream=None) -> None:
+    """Launches the bounded-wait diagnostic (a bulk-copy wait that can never
+    complete, limited to `polls` polls); hs_device_check then reports it."""
+    check(lib().hs_bulk_wait_selftest(int(polls), _stream_ptr(stream)))
 
 
 def hs_set_option(name: str, value: int) -> None:

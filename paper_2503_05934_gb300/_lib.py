@@ -62,6 +62,7 @@ SIGNATURES = {
                             ctypes.POINTER(ctypes.c_double)]),
     "hs_set_option": (_int, [ctypes.c_char_p, ctypes.c_int64]),
     "hs_device_check": (_int, [_vp]),
+    "hs_bulk_wait_selftest": (_int, [_u32, _vp]),
     "hs_keys_tile": (_sz, [_u32, _sz]),
     "hs_pairs_tile": (_sz, [_u32]),
     "hs_i64_tile": (_sz, [_u32, _sz]),

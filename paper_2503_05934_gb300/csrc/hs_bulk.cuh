@@ -29,11 +29,11 @@ HS_DEV void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
                  : "memory");
 }
 
-// True once the barrier's phase `parity` has completed; false after
-// kBulkSpinLimit polls.
-HS_DEV bool mbar_wait(uint64_t *bar, unsigned parity) {
+// True once the barrier's phase `parity` has completed; false after `limit`
+// polls.
+HS_DEV bool mbar_wait(uint64_t *bar, unsigned parity, long limit = kBulkSpinLimit) {
     const uint32_t a = smem_addr(bar);
-    for (long i = 0; i < kBulkSpinLimit; ++i) {
+    for (long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

@@ -22,6 +22,7 @@ enum KernelId {
     K_QS_LEAVES,
     K_SEG_CLASSIFY,
     K_SEG_SORT,
+    K_SELFTEST,
     K_COUNT
 };
 const char *kernel_name(int id);

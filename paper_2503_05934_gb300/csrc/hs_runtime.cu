@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "hs_internal.h"
+#include "hs_bulk.cuh"
 #include "hs_common.cuh"
 #include "hs_networks.cuh"
 
@@ -14,7 +15,8 @@ namespace hs {
 static const char *const kKernelNames[K_COUNT] = {
     "blocksort_keys", "blocksort_pairs", "merge_partition", "merge_keys",
     "merge_pairs",    "qs_plan",         "qs_partition",
-    "qs_leaves",      "seg_classify",    "seg_sort"};
+    "qs_leaves",      "seg_classify",    "seg_sort",
+    "selftest"};
 
 const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kKernelNames[id] : "?"; }
 
@@ -117,6 +119,22 @@ hs_status device_status(unsigned **out) {
     }
     *out = addr[dev];
     return HS_OK;
+}
+
+// Diagnostic kernel of hs_bulk_wait_selftest: one CTA arms an mbarrier for
+// 16 bytes of bulk-copy transactions, issues no copy, and waits as the
+// bulk-copy kernels do, with `polls` polls.  The wait gives up, the CTA
+// raises the status word and returns; nothing is left in flight.
+static __global__ void k_bulk_wait_selftest(long polls, unsigned *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16u);
+    const bool ok = mbar_wait(&bar, 0, polls);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+        return;
+    }
 }
 
 hs_status device_check(cudaStream_t st) {
@@ -308,6 +326,18 @@ hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, vo
     e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) return fail_cuda(e, "hs_sort_i32_host: stream synchronize");
     return HS_OK;
+}
+
+hs_status hs_bulk_wait_selftest(uint32_t polls, hs_stream_t stream) {
+    clear_error();
+    if (polls < 1 || polls > (uint32_t)kBulkSpinLimit)
+        return fail(HS_ERR_INVALID_ARG, "hs_bulk_wait_selftest: polls must be in [1, 2^22]");
+    unsigned *status = nullptr;
+    hs_status r = device_status(&status);
+    if (r != HS_OK) return r;
+    LaunchToken t = launch_begin(K_SELFTEST, (cudaStream_t)stream);
+    k_bulk_wait_selftest<<<1, 64, 0, (cudaStream_t)stream>>>((long)polls, status);
+    return launch_end(t);
 }
 
 hs_status hs_device_check(hs_stream_t stream) {

@@ -229,6 +229,20 @@ def test_host_buffer_entry_chunked(hs, n):
     assert np.array_equal(p.numpy(), want)
 
 
+def test_bulk_copy_wait_gives_up_with_a_status(hs):
+    """A bulk-copy wait that can never complete (an mbarrier armed for bytes
+    no copy delivers) ends after its poll limit with HS_ERR_TIMEOUT from
+    hs_device_check, not a hang; the context stays usable and the status word
+    is clear afterwards."""
+    hs.hs_bulk_wait_selftest(1000)
+    with pytest.raises(hs.HsortError) as err:
+        hs.hs_device_check()
+    assert err.value.status == 5  # HS_ERR_TIMEOUT
+    hs.hs_device_check()  # cleared
+    a = g.random_i32(100_000, 17)
+    assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a))
+
+
 def test_workspace_reuse_and_launch_count(hs):
     import torch
     n = 1 << 20

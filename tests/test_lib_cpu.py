@@ -123,3 +123,9 @@ def test_prof_select_names(hs):
     assert hs.hs_prof_select(None) == 0
     assert hs.hs_prof_select(b"no_such_kernel") == 1
     assert b"unknown kernel" in hs.hs_last_error()
+
+
+def test_bulk_wait_selftest_rejects_bad_poll_limits(hs):
+    """Argument errors return before any launch, so they need no GPU."""
+    assert hs.hs_bulk_wait_selftest(0, None) == 1
+    assert hs.hs_bulk_wait_selftest((1 << 22) + 1, None) == 1
