@@ -355,6 +355,11 @@ HS_API hs_status hs_bulk_wait_selftest(uint32_t polls, hs_stream_t stream);
  *   "blocksort_bulk": keys block sort of the merge path with 1 (default)
  *     each full tile moved in and out by one bulk copy when the array is
  *     16-byte aligned, 0 tiles staged by the threads.
+ *   "segsort_bulk": batched form (hs_segsort_i32, the server) with 1
+ *     (default) the tiles and merge chunks of segments longer than one warp
+ *     tile moved in and out of shared memory by bulk copies of their 16-byte
+ *     aligned interiors (at most three keys at each end by plain loads and
+ *     stores); 0 staged by the threads.
  *   "pairs_blocksort_bulk": pair block sort with 1 (default) each full tile's
  *     keys and values moved in and out by bulk copies when all four arrays
  *     are 16-byte aligned, 0 tiles staged by the threads.

@@ -55,6 +55,14 @@ HS_DEV uint64_t l2_evict_first_policy() {
     return p;
 }
 
+// L2 policy for data read again soon (a segment's merge levels in the
+// batched form): the normal eviction priority.
+HS_DEV uint64_t l2_evict_normal_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // Global -> shared, `bytes` (multiple of 16, both ends 16-byte aligned),
 // completing `bytes` of transaction count on `bar`.
 HS_DEV void bulk_load(void *sdst, const void *gsrc, unsigned bytes, uint64_t *bar,
@@ -77,6 +85,15 @@ HS_DEV void bulk_store(void *gdst, const void *ssrc, unsigned bytes, uint64_t po
 // Waits until the calling thread's bulk stores have read their shared source
 // (the CTA's shared memory must outlive those reads).
 HS_DEV void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Waits until the calling thread's bulk stores have completed their writes
+// (for kernels that read back what they stored).
+HS_DEV void bulk_wait_writes() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Orders this thread's global-memory accesses by the generic proxy (plain
+// loads and stores) with those of the async proxy (bulk copies) on either
+// side of it; a barrier after it extends the order to the rest of the CTA.
+HS_DEV void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // Orders this thread's generic shared-memory writes before later bulk copies
 // (async proxy) that read them.

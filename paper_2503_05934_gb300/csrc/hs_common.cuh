@@ -67,5 +67,6 @@ HS_DEV uint32_t smem_addr(const void *p) {
 constexpr unsigned kStatusTimeout = 1u;  // a bounded device-side wait gave up
 constexpr unsigned kStatusBadOffsets = 2u;
 constexpr unsigned kStatusMisaligned = 4u;  // a bulk copy's addresses were not 16-byte aligned
+constexpr unsigned kStatusInconsistent = 8u;  // merge splits that would stage outside a buffer
 
 }  // namespace hs

@@ -102,6 +102,7 @@ void merge_set_tile(int v);
 void i64_set_bulk(int v);
 void merge_set_blocksort_bulk(int v);
 void pairs_set_blocksort_bulk(int v);
+void segsort_set_bulk(int v);
 void merge_set_samples(int v);
 
 // Block sort of [0, n) in tiles of keys_tile(L) keys (the merge path's first pass;

@@ -154,6 +154,8 @@ hs_status device_check(cudaStream_t st) {
             return fail(HS_ERR_TIMEOUT, "a kernel gave up on a bounded wait");
         if (v & kStatusMisaligned)
             return fail(HS_ERR_CUDA, "a kernel found bulk-copy addresses that are not 16-byte aligned");
+        if (v & kStatusInconsistent)
+            return fail(HS_ERR_CUDA, "a kernel found merge splits that would stage outside its buffer");
         return fail(HS_ERR_INVALID_ARG, "a kernel found malformed segment offsets");
     }
     return HS_OK;
@@ -398,6 +400,12 @@ hs_status hs_set_option(const char *name, int64_t value) {
         if (value != 0 && value != 1)
             return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_bulk must be 0 or 1");
         merge_set_blocksort_bulk((int)value);
+        return HS_OK;
+    }
+    if (std::strcmp(name, "segsort_bulk") == 0) {
+        if (value != 0 && value != 1)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: segsort_bulk must be 0 or 1");
+        segsort_set_bulk((int)value);
         return HS_OK;
     }
     if (std::strcmp(name, "pairs_blocksort_bulk") == 0) {

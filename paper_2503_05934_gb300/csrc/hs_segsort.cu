@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "hs_bulk.cuh"
 #include "hs_internal.h"
 #include "hs_blocksort.cuh"
 #include "hs_segsort.h"
@@ -27,6 +28,81 @@ namespace hs {
 constexpr int SPLIT_CAP = 256;  // merge-level chunk boundaries searched per batch
 
 HS_DEV bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Bulk-copy staging of the batched form.  Segments start anywhere, so a run
+// g[0, cnt) of keys is placed at s[0, cnt) with s congruent to g modulo 16
+// bytes (s = a 16-byte aligned base + (g mod 16) / 4 words): its 16-byte
+// aligned interior then moves as one bulk copy, and at most three keys at
+// each end move by plain loads and stores.  The copies never touch a word
+// outside the run.
+struct StageCut {
+    int head, body;  // keys before the first 16-byte boundary, then whole 16-byte words (keys)
+};
+HS_DEV StageCut stage_cut(const int32_t *g, int cnt) {
+    const int h = (int)(((16u - (uint32_t)(reinterpret_cast<uintptr_t>(g) & 15u)) & 15u) >> 2);
+    StageCut c;
+    c.head = h < cnt ? h : cnt;
+    c.body = ((cnt - c.head) >> 2) << 2;
+    return c;
+}
+HS_DEV int32_t *congruent(int32_t *sbase, const int32_t *g) {
+    return sbase + ((reinterpret_cast<uintptr_t>(g) & 15u) >> 2);
+}
+// Thread 0: the interior copy (its bytes are counted by the caller's expect_tx).
+HS_DEV void stage_issue(int32_t *s, const int32_t *g, const StageCut &c, uint64_t *bar,
+                        uint64_t pol) {
+    if (c.body > 0) bulk_load(s + c.head, g + c.head, (unsigned)c.body * 4u, bar, pol);
+}
+template <int NT>
+HS_DEV void stage_edges(int32_t *s, const int32_t *g, int cnt, const StageCut &c) {
+    for (int i = threadIdx.x; i < c.head; i += NT) s[i] = g[i];
+    for (int i = c.head + c.body + threadIdx.x; i < cnt; i += NT) s[i] = g[i];
+}
+// Writes s[0, cnt) back to g (congruent as above).  The caller has made every
+// thread's writes to s visible to the copy engine (fence_proxy_async_smem and
+// a barrier); thread 0 waits until the bulk store has read s, so s may be
+// reused after the caller's next barrier.
+template <int NT>
+HS_DEV void unstage(const int32_t *s, int32_t *g, int cnt, uint64_t pol) {
+    const StageCut c = stage_cut(g, cnt);
+    if (threadIdx.x == 0 && c.body > 0) {
+        bulk_store(g + c.head, s + c.head, (unsigned)c.body * 4u, pol);
+        bulk_wait_read();
+    }
+    for (int i = threadIdx.x; i < c.head; i += NT) g[i] = s[i];
+    for (int i = c.head + c.body + threadIdx.x; i < cnt; i += NT) g[i] = s[i];
+}
+
+// Makes everything the CTA stored so far (thread 0's bulk stores, every
+// thread's plain stores) visible to the CTA's later reads by either proxy.
+HS_DEV void stores_done() {
+    if (threadIdx.x == 0) bulk_wait_writes();
+    fence_proxy_async_global();
+    __syncthreads();
+}
+
+// Per-CTA state of the bulk-copy staging: one mbarrier, its phase parity,
+// the L2 policy and the status word for a wait that gives up.
+struct Stager {
+    uint64_t *bar;
+    unsigned phase;
+    uint64_t pol;
+    unsigned *status;
+    // Every thread calls it after the interior copies were issued; false if
+    // the wait gave up (the status word is raised, and the copies in flight
+    // get one more bounded wait).  Callers separate consecutive waits by a
+    // barrier, so no thread lags a phase behind; after a false the CTA stops
+    // using the barrier.
+    HS_DEV bool wait() {
+        const bool ok = mbar_wait(bar, phase);
+        if (!ok) {
+            atomicOr(status, kStatusTimeout);
+            mbar_wait(bar, phase);
+        }
+        phase ^= 1u;
+        return ok;
+    }
+};
 
 // Merge-path split by one warp (32-ary search): the smallest i in [lo, hi]
 // with A[i] > B[diag - 1 - i] (hi when there is none), the number of A
@@ -141,21 +217,188 @@ HS_DEV void cta_merge_level(const int32_t *src, int32_t *dst, int64_t n, int64_t
     }
 }
 
+// cta_merge_level with bulk-copy staging: each chunk's A and B ranges are
+// placed congruent to their global addresses in two regions of the buffer
+// (A first, B from the next 16-byte boundary after it), and the merged chunk
+// leaves from a congruent copy.  src and dst are congruent modulo 16 bytes.
+// False if a copy wait gave up.
 template <int NT, int L, int LV>
-HS_DEV void sort_segment(const SegDesc &d, uint32_t netset, int32_t *s, int64_t *split) {
+HS_DEV bool cta_merge_level_staged(const int32_t *src, int32_t *dst, int64_t n, int64_t w,
+                                   int32_t *sbase, int64_t *split, Stager &sg) {
+    using C = BlockSort3<NT, L, LV>;
+    constexpr int T = C::T, EO = C::EO, P = C::P;
+    const int64_t span = 2 * w;
+    const int64_t ngroups = (n + span - 1) / span;
+    const int64_t tpg = (span + T - 1) / T;
+    const int64_t last = n - (ngroups - 1) * span;
+    const int64_t nchunks = (ngroups - 1) * tpg + (last + T - 1) / T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Past the A and B regions (at most T + 9 + P words with the window slack).
+    int *wsplit = sbase + C::T + C::P + 32;
+    for (int64_t c0 = 0; c0 < nchunks; c0 += SPLIT_CAP) {
+        const int64_t c1 = std::min<int64_t>(nchunks, c0 + SPLIT_CAP);
+        for (int64_t c = c0 + warp; c <= c1 && c < nchunks; c += NT / 32) {
+            const int64_t g = c / tpg, t = c - g * tpg;
+            const MergeGeom m = merge_geom(g, n, w);
+            int64_t diag = t * T;
+            if (diag > m.alen + m.blen) diag = m.alen + m.blen;
+            const int64_t lo = diag > m.blen ? diag - m.blen : 0;
+            const int64_t hi = diag < m.alen ? diag : m.alen;
+            const int64_t r = warp_merge_path(src + m.gs, src + m.gs + w, diag, lo, hi, lane);
+            if (lane == 0) split[c - c0] = r;
+        }
+        __syncthreads();
+        for (int64_t c = c0; c < c1; ++c) {
+            const int64_t g = c / tpg, t = c - g * tpg;
+            const MergeGeom m = merge_geom(g, n, w);
+            const int64_t glen = m.alen + m.blen;
+            const int64_t o0 = t * T;
+            const int64_t o1 = std::min<int64_t>(o0 + T, glen);
+            const int64_t a0 = split[c - c0];
+            const int64_t a1 = (o1 == glen) ? m.alen : split[c + 1 - c0];
+            const int na = (int)(a1 - a0);
+            const int tot = (int)(o1 - o0);
+            const int nb = tot - na;
+            // Consistent splits give 0 <= na, nb <= tot <= T; anything else would
+            // stage outside the buffer, so it is reported and the segment dropped
+            // (the values are the same in every thread: uniform).
+            if (na < 0 || nb < 0 || tot > T) {
+                if (threadIdx.x == 0) atomicOr(sg.status, kStatusInconsistent);
+                return false;
+            }
+            const int32_t *gA = src + m.gs + a0, *gB = src + m.gs + w + (o0 - a0);
+            int32_t *sA = congruent(sbase, gA);
+            int32_t *sB = congruent(sbase + ((int)(sA - sbase) + na + 3) / 4 * 4, gB);
+            fence_proxy_async_smem();  // earlier generic writes to the buffer before the copies
+            __syncthreads();
+            const StageCut ca = stage_cut(gA, na), cb = stage_cut(gB, nb);
+            if (threadIdx.x == 0) {
+                mbar_arrive_expect_tx(sg.bar, (unsigned)(ca.body + cb.body) * 4u);
+                stage_issue(sA, gA, ca, sg.bar, sg.pol);
+                stage_issue(sB, gB, cb, sg.bar, sg.pol);
+            }
+            stage_edges<NT>(sA, gA, na, ca);
+            stage_edges<NT>(sB, gB, nb, cb);
+            const bool ok = sg.wait();
+            if (__syncthreads_or(!ok)) return false;
+            const int32_t *A = sA, *B = sB;
+            const int diag = threadIdx.x * EO;
+            const int dcl = diag < tot ? diag : tot;
+            int lo = dcl > nb ? dcl - nb : 0, hi = dcl < na ? dcl : na;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (A[mid] <= B[dcl - 1 - mid]) lo = mid + 1;
+                else hi = mid;
+            }
+            int end = __shfl_down_sync(0xffffffffu, lo, 1);
+            if (lane == 0) wsplit[warp] = lo;
+            if (threadIdx.x == 0) wsplit[NT / 32] = na;
+            __syncthreads();
+            const int dend = (diag + EO) < tot ? (diag + EO) : tot;
+            if (lane == 31) end = wsplit[warp + 1];
+            if (dend == tot) end = na;
+            const int cnt = dend - dcl;
+            int32_t x[P];
+            if (cnt > 0) exact_window_merge<EO, P>(A, lo, B, dcl - lo, end - lo, cnt, x);
+            __syncthreads();
+            int32_t *out = dst + m.gs + o0;
+            int32_t *so = congruent(sbase, out);
+            if (cnt > 0) {
+#pragma unroll
+                for (int k = 0; k < EO; ++k)
+                    if (k < cnt) so[diag + k] = x[k];
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            unstage<NT>(so, out, tot, sg.pol);
+            __syncthreads();
+        }
+    }
+    // The next level reads this one's output back: its bulk stores must be
+    // done, and both the bulk stores and the threads' plain stores of the
+    // chunk ends must be ordered before the next reads of either proxy.
+    stores_done();
+    return true;
+}
+
+// One block-sort tile of a segment through bulk-copy staging: keys src[0,
+// cnt) sorted into dst[0, cnt).  The tile is placed congruent to src; when
+// dst is congruent to src too (in place, or the same offset of a congruent
+// scratch area) it leaves by a bulk store, else by plain stores.  Slots past
+// cnt hold +infinity sentinels.  False if a copy wait gave up.
+template <int NT, int L, int LV, bool SKIP>
+HS_DEV bool sort_tile_staged(int32_t *sbase, const int32_t *src, int32_t *dst, int cnt,
+                             uint32_t netset, Stager &sg) {
+    using C = BlockSort3<NT, L, LV>;
+    constexpr int T = C::T, EO = C::EO, P = C::P;
+    int32_t *s = congruent(sbase, src);
+    int *wsplit = s + T + P + 32;
+    fence_proxy_async_smem();  // earlier generic writes to the buffer before the copy
+    __syncthreads();
+    const StageCut c = stage_cut(src, cnt);
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(sg.bar, (unsigned)c.body * 4u);
+        stage_issue(s, src, c, sg.bar, sg.pol);
+    }
+    stage_edges<NT>(s, src, cnt, c);
+    for (int i = cnt + threadIdx.x; i < T; i += NT) s[i] = kKeyMax;
+    const bool ok = sg.wait();
+    if (__syncthreads_or(!ok)) return false;
+    const int my0 = threadIdx.x * EO;
+    int32_t k[EO];
+#pragma unroll
+    for (int j = 0; j < EO; ++j) k[j] = s[my0 + j];
+    if (!SKIP || my0 < cnt) sort_thread_leaves<L, LV, P>(k, cnt - my0, netset);
+    block_merge_levels<NT, EO, P, SKIP>(s, wsplit, k, cnt);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < EO; ++j) s[my0 + j] = k[j];
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (((reinterpret_cast<uintptr_t>(src) ^ reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+        unstage<NT>(s, dst, cnt, sg.pol);
+    } else {
+        for (int i = threadIdx.x; i < cnt; i += NT) dst[i] = s[i];
+    }
+    __syncthreads();
+    return true;
+}
+
+// BULK: every tile and merge chunk moves by bulk copies (sg); otherwise the
+// threads stage them.  False (uniform across the CTA) if a copy wait gave up.
+template <int NT, int L, int LV, bool BULK>
+HS_DEV bool sort_segment(const SegDesc &d, uint32_t netset, int32_t *s, int64_t *split,
+                         Stager &sg) {
     using C = BlockSort3<NT, L, LV>;
     constexpr int T = C::T;
     const int64_t n = d.n;
-    if (n <= 1) return;
+    if (n <= 1) return true;
     if (n <= T) {
+        if constexpr (BULK) return sort_tile_staged<NT, L, LV, true>(s, d.keys, d.keys, (int)n, netset, sg);
         block_sort_tile3<NT, L, LV, true>(d.keys, d.keys, (int)n, netset, aligned16(d.keys), s);
-        return;
+        return true;
     }
     int levels = 0;
     for (int64_t w = T; w < n; w *= 2) ++levels;
     // Ping-pong so that the last level lands in d.keys.
     int32_t *cur = (levels % 2 == 0) ? d.keys : d.scratch;
     int32_t *alt = (levels % 2 == 0) ? d.scratch : d.keys;
+    if constexpr (BULK) {
+        for (int64_t base = 0; base < n; base += T) {
+            const int cnt = (int)std::min<int64_t>(T, n - base);
+            if (!sort_tile_staged<NT, L, LV, false>(s, d.keys + base, cur + base, cnt, netset, sg))
+                return false;
+        }
+        // The merge levels read the tiles back.
+        stores_done();
+        for (int64_t w = T; w < n; w *= 2) {
+            if (!cta_merge_level_staged<NT, L, LV>(cur, alt, n, w, s, split, sg)) return false;
+            int32_t *tmp = cur;
+            cur = alt;
+            alt = tmp;
+        }
+        return true;
+    }
     const bool vec = aligned16(d.keys) && aligned16(cur);
     for (int64_t base = 0; base < n; base += T) {
         const int cnt = (int)std::min<int64_t>(T, n - base);
@@ -168,6 +411,7 @@ HS_DEV void sort_segment(const SegDesc &d, uint32_t netset, int32_t *s, int64_t 
         cur = alt;
         alt = tmp;
     }
+    return true;
 }
 
 // A segment of at most one warp tile (32 * EO keys) sorted by one warp alone:
@@ -207,7 +451,7 @@ constexpr int kCtrlWords = 4;
 // tile per warp, whichever is larger.
 template <int NT, int L, int LV>
 constexpr int seg_smem_bytes() {
-    constexpr int blk = BlockSort3<NT, L, LV>::SMEM_BYTES;
+    constexpr int blk = BlockSort3<NT, L, LV>::SMEM_BYTES + 16;  // + a congruent shift of up to 3 words
     constexpr int wrp = (NT / 32) * BlockSort3<32, L, LV>::SMEM_BYTES;
     return blk > wrp ? blk : wrp;
 }
@@ -217,12 +461,23 @@ constexpr int seg_smem_bytes() {
 // segments from the back of the array (cdesc[ndesc - 1 - j]) until both
 // lists are drained.  Large segments first also balances the load: the
 // short items fill the gaps at the end.
-template <int NT, int L, int LV>
+template <int NT, int L, int LV, bool BULK>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 2)
-    k_seg_sort(const SegDesc *cdesc, int64_t ndesc, unsigned long long *ctrl, uint32_t netset) {
+    k_seg_sort(const SegDesc *cdesc, int64_t ndesc, unsigned long long *ctrl, uint32_t netset,
+               unsigned *status) {
     extern __shared__ __align__(16) int32_t smem[];
     __shared__ int64_t s_split[SPLIT_CAP + 1];
     __shared__ unsigned long long s_item[2];
+    __shared__ __align__(8) uint64_t s_bar;
+    Stager sg{&s_bar, 0u, BULK ? l2_evict_normal_policy() : 0ull, status};
+    if (BULK) {
+        // The congruent staging relies on a 16-byte aligned dynamic buffer.
+        if ((smem_addr(smem) & 15u) != 0) {
+            if (threadIdx.x == 0) atomicOr(status, kStatusMisaligned);
+            return;
+        }
+        if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    }
     const unsigned long long nlarge = ctrl[2], nsmall = ctrl[3];
     if (threadIdx.x == 0) s_item[0] = atomicAdd(&ctrl[0], 1ull);
     __syncthreads();
@@ -234,7 +489,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 2)
         unsigned long long next = 0;
         if (threadIdx.x == 0) next = atomicAdd(&ctrl[0], 1ull);
         const SegDesc d = cdesc[item];
-        sort_segment<NT, L, LV>(d, netset, smem, s_split);
+        // A copy wait that gave up (status raised) ends this CTA's work.
+        if (!sort_segment<NT, L, LV, BULK>(d, netset, smem, s_split, sg)) return;
         if (threadIdx.x == 0) s_item[it ^ 1] = next;
         __syncthreads();
     }
@@ -316,10 +572,15 @@ struct SegKernelInfo {
     int64_t small_max;  // segments of up to this many keys are sorted by one warp
 };
 
+// Option "segsort_bulk": 1 (default) large segments move tiles and merge
+// chunks by bulk copies (k_seg_sort<..., true>), 0 the threads stage them.
+static int g_seg_bulk = 1;
+void segsort_set_bulk(int v) { g_seg_bulk = v; }
+
 template <int NT, int L, int LV>
 static hs_status seg_kernel_info(SegKernelInfo *out) {
     constexpr int SMEM = seg_smem_bytes<NT, L, LV>();
-    auto kern = k_seg_sort<NT, L, LV>;
+    auto kern = g_seg_bulk ? k_seg_sort<NT, L, LV, true> : k_seg_sort<NT, L, LV, false>;
     hs_status r = ensure_smem((const void *)kern, SMEM);
     if (r != HS_OK) return r;
     int occ = 0;
@@ -388,7 +649,11 @@ static hs_status seg_launch_sort(const SegKernelInfo &ki, const SegDesc *d_cdesc
     const int per_sm = plan.ctas_per_sm > 0 ? std::min(plan.ctas_per_sm, ki.max_occ) : ki.max_occ;
     const int64_t grid = std::min<int64_t>(ndesc, (int64_t)sm_count() * per_sm);
     uint32_t netset = plan.netset;
-    void *args[] = {(void *)&d_cdesc, (void *)&ndesc, (void *)&d_ctrl, (void *)&netset};
+    unsigned *status = nullptr;
+    hs_status r = device_status(&status);
+    if (r != HS_OK) return r;
+    void *args[] = {(void *)&d_cdesc, (void *)&ndesc, (void *)&d_ctrl, (void *)&netset,
+                    (void *)&status};
     LaunchToken t = launch_begin(K_SEG_SORT, st);
     cudaError_t e = cudaLaunchKernel(ki.fn, dim3((unsigned)grid), dim3(plan.block_threads), args,
                                      ki.smem, st);
