@@ -304,9 +304,11 @@ HS_API hs_status hs_prof_read(const char *kernel, uint64_t *launches, double *to
  * input (segment offsets that decrease or run past the key count) raises
  * this word and skips that work.  Returns HS_ERR_INVALID_ARG for such input,
  * HS_ERR_TIMEOUT if a bounded device-side wait gave up (such as a merge
- * level's wait for its bulk tile copy), HS_ERR_CUDA on a CUDA error or when
- * a kernel found bulk-copy addresses that are not 16-byte aligned (it then
- * skipped its copies), else HS_OK.  Synchronous. */
+ * level's wait for its bulk tile copy), HS_ERR_CUDA on a CUDA error, when a
+ * kernel found bulk-copy addresses that are not 16-byte aligned (it then
+ * skipped its copies) or when the batched form found merge splits that would
+ * stage outside its buffer (it then dropped that segment), else HS_OK.
+ * Synchronous. */
 HS_API hs_status hs_device_check(hs_stream_t stream);
 
 /* Diagnostic of the bounded waits (no counterpart in the paper: the paper's
@@ -334,9 +336,9 @@ HS_API hs_status hs_bulk_wait_selftest(uint32_t polls, hs_stream_t stream);
  *     leaves as leaf, ..., leaf, leaf-1 keys, so the first merge tile holds
  *     (leaves * leaf - 1) * threads keys.
  *   "blocksort_threads": 512 or 1024: shape 0 or 1.
- *   "merge_kernel": 1 (default) tiled merge levels with asynchronous 16-byte
- *     staging and odd outputs per thread (used for keys when both buffers
- *     are 16-byte aligned and n % 4 == 0), 0 staged-load serial merges.
+ *   "merge_kernel": 1 (default) tiled merge levels in the "merge_tile" shape,
+ *     odd outputs per thread (used for keys when both buffers are 16-byte
+ *     aligned and n % 4 == 0), 0 staged-load serial merges.
  *   "merge_tile": shape of the tiled keys level: 9 (default) 128 threads x
  *     31 keys with exact per-thread windows, the tile moved in and out by
  *     bulk copies (copy engine); 8 the same with 96 x 31, 10 with 192 x 31;
@@ -363,10 +365,10 @@ HS_API hs_status hs_bulk_wait_selftest(uint32_t polls, hs_stream_t stream);
  *   "pairs_blocksort_bulk": pair block sort with 1 (default) each full tile's
  *     keys and values moved in and out by bulk copies when all four arrays
  *     are 16-byte aligned, 0 tiles staged by the threads.
- *   "i64_merge": int64 sorts (hs_sort_i64) with 1 (default) block-sort and
- *     merge-level tiles moved in and out by bulk copies when the buffers are
- *     16-byte aligned (levels: and n is even), 0 tiles staged by the threads
- *     (block sort) and by cp.async (levels).
+ *   "i64_merge": int64 sorts (hs_sort_i64) with 1 (default) tiles moved in
+ *     and out by bulk copies: block-sort tiles when the arrays are 16-byte
+ *     aligned, merge-level tiles when they are and n is even; 0 block-sort
+ *     tiles staged by the threads and merge-level tiles by cp.async.
  *     Every option gives identical results.
  * Unknown names or values return HS_ERR_INVALID_ARG. */
 HS_API hs_status hs_set_option(const char *name, int64_t value);
