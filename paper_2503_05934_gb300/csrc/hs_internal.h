@@ -32,8 +32,17 @@ hs_status fail(hs_status st, const std::string &msg);
 hs_status fail_cuda(cudaError_t e, const char *what);
 void clear_error();
 
-// Brackets one launch: counts it and, when timing is on, records events on
-// `stream` around it.  Usage: auto t = launch_begin(id, s); <<<...>>>;
+// An NVTX range over one public call (pushed on construction, popped on
+// destruction), for profilers that select work by range.
+struct ApiRange {
+    explicit ApiRange(const char *name);
+    ~ApiRange();
+    ApiRange(const ApiRange &) = delete;
+    ApiRange &operator=(const ApiRange &) = delete;
+};
+
+// Brackets one launch: counts it, marks it with an NVTX range named for the
+// kernel and, when timing is on, records events on `stream` around it.  Usage: auto t = launch_begin(id, s); <<<...>>>;
 // st = launch_end(t).
 struct LaunchToken {
     int id;

@@ -5,12 +5,21 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hs_internal.h"
 #include "hs_bulk.cuh"
 #include "hs_common.cuh"
 #include "hs_networks.cuh"
 
 namespace hs {
+
+// NVTX range names of the launches ("hs:" + the kernel name), so that a
+// profiler can select one kernel's launches (ncu --nvtx --nvtx-include).
+static const char *const kRangeNames[K_COUNT] = {
+    "hs:blocksort_keys", "hs:blocksort_pairs", "hs:merge_partition", "hs:merge_keys",
+    "hs:merge_pairs",    "hs:qs_plan",         "hs:qs_partition",    "hs:qs_leaves",
+    "hs:seg_classify",   "hs:seg_sort",        "hs:selftest"};
 
 static const char *const kKernelNames[K_COUNT] = {
     "blocksort_keys", "blocksort_pairs", "merge_partition", "merge_keys",
@@ -50,7 +59,11 @@ static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_event_pool;
 static uint64_t g_prof_count[K_COUNT];
 static double g_prof_ms[K_COUNT];
 
+ApiRange::ApiRange(const char *name) { nvtxRangePushA(name); }
+ApiRange::~ApiRange() { nvtxRangePop(); }
+
 LaunchToken launch_begin(int id, cudaStream_t stream) {
+    nvtxRangePushA(kRangeNames[id]);  // popped by launch_end
     LaunchToken t{id, stream, nullptr, nullptr};
     const int only = g_prof_only.load(std::memory_order_relaxed);
     if (g_prof_on.load(std::memory_order_relaxed) && (only < 0 || only == id)) {
@@ -72,6 +85,7 @@ LaunchToken launch_begin(int id, cudaStream_t stream) {
 }
 
 hs_status launch_end(const LaunchToken &t) {
+    nvtxRangePop();
     cudaError_t e = cudaGetLastError();
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (t.ev_a) {
@@ -260,6 +274,7 @@ static hs_status check_common(const void *d_keys, size_t n, hs_algo a, hs_netset
 
 hs_status hs_sort_i32(int32_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
                       size_t ws_bytes, hs_stream_t stream) {
+    const ApiRange range("hs_sort_i32");
     clear_error();
     hs_status st = check_common(d_keys, n, a, s, "hs_sort_i32");
     if (st != HS_OK) return st;
@@ -270,6 +285,7 @@ hs_status hs_sort_i32(int32_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d
 
 hs_status hs_sort_pairs_i32(int32_t *d_keys, int32_t *d_vals, size_t n, hs_algo a, hs_netset s,
                             void *d_ws, size_t ws_bytes, hs_stream_t stream) {
+    const ApiRange range("hs_sort_pairs_i32");
     clear_error();
     hs_status st = check_common(d_keys, n, a, s, "hs_sort_pairs_i32");
     if (st != HS_OK) return st;
@@ -285,6 +301,7 @@ size_t hs_sort_i64_workspace_bytes(size_t n) { return merge_workspace_bytes_i64(
 
 hs_status hs_sort_i64(int64_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
                       size_t ws_bytes, hs_stream_t stream) {
+    const ApiRange range("hs_sort_i64");
     clear_error();
     if (a != HS_ALGO_MERGE && a != HS_ALGO_QUICK)
         return fail(HS_ERR_INVALID_ARG, "hs_sort_i64: unknown algorithm");
@@ -305,6 +322,7 @@ size_t hs_sort_host_workspace_bytes(size_t n, hs_algo a) {
 
 hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
                            size_t ws_bytes, hs_stream_t stream) {
+    const ApiRange range("hs_sort_i32_host");
     clear_error();
     hs_status st = check_common(h_keys, n, a, s, "hs_sort_i32_host");
     if (st != HS_OK) return st;

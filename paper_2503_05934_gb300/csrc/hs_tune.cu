@@ -264,6 +264,7 @@ static hs_status plan_from(const hs_plan *plan, hs_netset s, hs_plan *out) {
 hs_status hs_segsort_i32(int32_t *d_keys, size_t n_keys, const int64_t *d_offsets, size_t num_segs,
                          hs_algo a, hs_netset s, const hs_plan *plan, void *d_ws, size_t ws_bytes,
                          hs_stream_t stream) {
+    const ApiRange range("hs_segsort_i32");
     clear_error();
     if (a == HS_ALGO_QUICK)
         return fail(HS_ERR_UNSUPPORTED, "hs_segsort_i32: the batched form runs the merge path only");
