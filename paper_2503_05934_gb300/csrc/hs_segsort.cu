@@ -220,8 +220,9 @@ HS_DEV void cta_merge_level(const int32_t *src, int32_t *dst, int64_t n, int64_t
 // cta_merge_level with bulk-copy staging: each chunk's A and B ranges are
 // placed congruent to their global addresses in two regions of the buffer
 // (A first, B from the next 16-byte boundary after it), and the merged chunk
-// leaves from a congruent copy.  src and dst are congruent modulo 16 bytes.
-// False if a copy wait gave up.
+// leaves from a copy congruent to its destination (src and dst need not be
+// congruent to each other).  False if a copy wait gave up or the chunk's
+// split sizes do not fit the buffer.
 template <int NT, int L, int LV>
 HS_DEV bool cta_merge_level_staged(const int32_t *src, int32_t *dst, int64_t n, int64_t w,
                                    int32_t *sbase, int64_t *split, Stager &sg) {
