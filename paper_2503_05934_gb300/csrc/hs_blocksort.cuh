@@ -108,20 +108,67 @@ HS_DEV void sort_thread_leaves(K *k, int avail, uint32_t netset) {
 // WARP: the tile belongs to one warp alone (NT = 32, s is that warp's own
 // buffer), every barrier is a warp barrier, and other warps of the block may
 // be sorting other tiles meanwhile.
+// First merge level in registers: lanes 2j and 2j+1 merge their EO-key runs
+// (A = the even lane's, B = the odd lane's) without shared memory.  Each lane
+// gets the other's run by shuffles and applies the first half-cleaner of the
+// bitonic merge of A and reversed B (both padded to P with +infinity): the
+// even lane keeps the minima, the odd lane the maxima (in reverse order,
+// still bitonic), and each sorts its P words with the remaining half-cleaner
+// stages.  The even lane's P smallest words are the P smallest of the pair;
+// it keeps EO of them and hands the other P - EO to the odd lane, whose EO
+// outputs are those followed by the real words of its maxima.
+template <int EO, int P, class K>
+HS_DEV void shuffle_first_level(K (&k)[EO], bool odd) {
+    constexpr int X = P - EO;  // words the even lane hands to the odd lane
+    K z[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) z[i] = i < EO ? k[i < EO ? i : 0] : word_max<K>();
+    // Slots i and P-1-i meet the partner's P-1-i and i: both are updated in
+    // one step, so only the P-word array stays live (no copy of the partner's
+    // run).  Padding slots hold +infinity on both lanes and need no shuffle.
+#pragma unroll
+    for (int i = 0; i < P / 2; ++i) {
+        const int j = P - 1 - i;
+        const K a = z[i], b = z[j];
+        const K pb = j < EO ? __shfl_xor_sync(0xffffffffu, b, 1) : word_max<K>();  // partner's z[j]
+        const K pa = i < EO ? __shfl_xor_sync(0xffffffffu, a, 1) : word_max<K>();  // partner's z[i]
+        z[i] = odd ? hs_max(a, pb) : hs_min(a, pb);
+        z[j] = odd ? hs_max(b, pa) : hs_min(b, pa);
+    }
+    if constexpr (P == 1) z[0] = odd ? hs_max(z[0], __shfl_xor_sync(0xffffffffu, z[0], 1))
+                                    : hs_min(z[0], __shfl_xor_sync(0xffffffffu, z[0], 1));
+    bitonic_half_clean<P>(z);
+    if constexpr (X > 0) {
+        K e[X];
+#pragma unroll
+        for (int q = 0; q < X; ++q) e[q] = __shfl_xor_sync(0xffffffffu, z[EO + q], 1);
+#pragma unroll
+        for (int q = 0; q < EO; ++q) k[q] = odd ? (q < X ? e[q < X ? q : 0] : z[q - X < 0 ? 0 : q - X]) : z[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < EO; ++q) k[q] = z[q];
+    }
+}
+
 template <int NT, int EO, int P, bool SKIP, class K, bool WARP = false>
 HS_DEV void block_merge_levels(K *s, int *wsplit, K (&k)[EO], int cnt) {
     static_assert(!WARP || NT == 32, "a warp-owned tile has 32 threads");
     constexpr int T = NT * EO;
     const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
     const int my0 = tid * EO;
-    for (int w = EO; w < T && w < cnt; w *= 2) {
+    // Runs of EO -> 2EO in registers (pairs of adjacent lanes), then the
+    // shared-memory levels from 2EO on.  cnt is uniform, so every lane of a
+    // warp takes the same branch.
+    if (EO < T && EO < cnt) shuffle_first_level<EO, P>(k, (tid & 1) != 0);
+    constexpr int W0 = 2 * EO;
+    for (int w = W0; w < T && w < cnt; w *= 2) {
         // While a group of two runs lies inside one warp's slots, the warp
         // only reads what its own lanes wrote: a warp barrier suffices.  The
         // first stores still wait for the whole block, because the caller may
         // have staged the tile in this buffer in another layout (the pair
         // sort reads int32 keys from slots the 64-bit words then overwrite).
         const bool in_warp = 2 * w <= 32 * EO;
-        if (WARP || (in_warp && w != EO)) __syncwarp();
+        if (WARP || (in_warp && w != W0)) __syncwarp();
         else __syncthreads();
 #pragma unroll
         for (int j = 0; j < EO; ++j) s[my0 + j] = k[j];
