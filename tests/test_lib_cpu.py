@@ -129,3 +129,34 @@ def test_bulk_wait_selftest_rejects_bad_poll_limits(hs):
     """Argument errors return before any launch, so they need no GPU."""
     assert hs.hs_bulk_wait_selftest(0, None) == 1
     assert hs.hs_bulk_wait_selftest((1 << 22) + 1, None) == 1
+
+
+# Every tuning option with its default, a valid alternative and invalid values
+# (hs_set_option validates on the host, so no GPU is needed).
+OPTIONS = [
+    ("merge_tile", 9, 5, [-1, 11]),
+    ("merge_kernel", 1, 0, [2]),
+    ("merge_samples", 1, 0, [2]),
+    ("blocksort_shape", -1, 4, [-2, 6]),
+    ("blocksort_bulk", 1, 0, [2, -1]),
+    ("pairs_blocksort", 0, 3, [4]),
+    ("pairs_merge", 3, 1, [4, -1]),
+    ("pairs_blocksort_bulk", 1, 0, [2]),
+    ("i64_merge", 1, 0, [2]),
+    ("segsort_bulk", 1, 0, [2]),
+    ("quick_partition", 3, 2, [1, 4]),
+]
+
+
+@pytest.mark.parametrize("name,default,other,bad", OPTIONS)
+def test_option_values_are_validated(hs, name, default, other, bad):
+    try:
+        assert hs.hs_set_option(name.encode(), other) == 0
+        for v in bad:
+            assert hs.hs_set_option(name.encode(), v) == 1, (name, v)
+    finally:
+        assert hs.hs_set_option(name.encode(), default) == 0
+
+
+def test_unknown_option_is_rejected(hs):
+    assert hs.hs_set_option(b"no_such_option", 1) == 1
