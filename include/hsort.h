@@ -290,7 +290,11 @@ HS_API uint64_t hs_launch_count(void);
  * each launch while enabled (off by default; it adds two event records per
  * launch).  hs_prof_read waits for the recorded events, then returns the
  * launches and summed milliseconds of the kernel named `kernel` since the
- * last reset; unknown names give 0 launches. */
+ * last reset; unknown names give 0 launches.  Names: "blocksort_keys",
+ * "blocksort_pairs", "merge_partition" (binary and four-way partitions),
+ * "merge_keys" (binary keys levels, and int64 levels), "merge4_keys"
+ * (four-way keys levels), "merge_pairs", "qs_plan", "qs_partition",
+ * "qs_leaves", "seg_classify", "seg_sort", "selftest". */
 HS_API void hs_prof_enable(int on);
 /* Restricts the timing to launches of the kernel named `kernel` (the names
  * hs_prof_read accepts), so that the other launches carry no extra events;
@@ -344,6 +348,11 @@ HS_API hs_status hs_bulk_wait_selftest(uint32_t polls, hs_stream_t stream);
  *     bulk copies (copy engine); 8 the same with 96 x 31, 10 with 192 x 31;
  *     the cp.async-staged forms 5 96 x 31, 1 64 x 31, 2 128 x 31, 3 64 x 63,
  *     4 128 x 23, 6 192 x 31, 7 256 x 31; 0 256 x 15 with two windows.
+ *   "merge_fanin": 4 (default) the tiled keys levels merge four runs per
+ *     pass: a four-way merge-path split per output tile, then two stages of
+ *     binary merges in shared memory, one read and one write of every key for
+ *     two of Algorithm 1's merge levels (a binary level first when the number
+ *     of levels is odd); 2 binary levels only.
  *   "merge_samples": 1 (default) the tiled keys levels' partition searches
  *     start on every 32nd key of the level's input, written by the pass
  *     before; 0 plain searches in the keys.
@@ -395,6 +404,19 @@ HS_API size_t hs_i64_tile(hs_netset s, size_t n);
  * (-1 if m is outside 2..8); hs_network_apply sorts a[0..m-1] with it. */
 HS_API int hs_network_pairs(int m, int *pairs, int cap);
 HS_API int hs_network_apply(int m, int32_t *a);
+
+/* The K-way merge-path split of the four-way merge levels (two levels of
+ * Algorithm 1's Merge per pass), compiled for the host.  Run i is
+ * keys[starts[i] .. starts[i] + lens[i]), sorted ascending; the runs are
+ * merged stably (equal keys in run order, run 0 first).  For output rank
+ * `rank` (0 <= rank <= sum of lens), a[i] receives the number of elements of
+ * run i among the first `rank` outputs of that merge.  samp, when not NULL,
+ * holds keys[32 j] at samp[j] (the merge levels' sample array) and every start
+ * must be a multiple of 32; the search then reads positions that are
+ * multiples of 32 from it.  k_runs is 2, 4 or 8.  Returns 0, or -1 for
+ * invalid arguments (nothing written).  Host memory only; no GPU needed. */
+HS_API int hs_merge_split(const int32_t *keys, const int32_t *samp, const int64_t *starts,
+                          const int64_t *lens, int k_runs, int64_t rank, int64_t *a);
 
 #ifdef __cplusplus
 }

@@ -33,7 +33,7 @@ __all__ = [
     "Plan", "make_plan",
     "hs_segsort_workspace_bytes", "hs_segsort_i32", "hs_sort_i32_many", "Graph",
     "hs_segsort_capture", "hs_segsort_autotune", "hs_tune_cache_save", "hs_tune_cache_load",
-    "Server",
+    "Server", "hs_merge_split",
 ]
 
 
@@ -333,6 +333,29 @@ def hs_bulk_wait_selftest(polls: int, stream=None) -> None:
     """Launches the bounded-wait diagnostic (a bulk-copy wait that can never
     complete, limited to `polls` polls); hs_device_check then reports it."""
     check(lib().hs_bulk_wait_selftest(int(polls), _stream_ptr(stream)))
+
+
+def hs_merge_split(keys, starts, lens, rank: int, samp=None):
+    """Host build of the four-way levels' K-way merge-path split: for output
+    rank ``rank`` of the stable merge of runs ``keys[starts[i]:starts[i]+lens[i]]``
+    (numpy int32, K = 2, 4 or 8 runs), the number of elements each run
+    contributes to the first ``rank`` outputs.  ``samp`` (every 32nd key)
+    makes the search read positions that are multiples of 32 from it."""
+    import numpy as np
+    keys = np.ascontiguousarray(keys, dtype=np.int32)
+    st = np.ascontiguousarray(starts, dtype=np.int64)
+    ln = np.ascontiguousarray(lens, dtype=np.int64)
+    if st.size != ln.size:
+        raise ValueError("starts and lens differ in length")
+    sp = None if samp is None else np.ascontiguousarray(samp, dtype=np.int32)
+    out = np.zeros(ln.size, dtype=np.int64)
+    rc = lib().hs_merge_split(keys.ctypes.data if keys.size else None,
+                              sp.ctypes.data if sp is not None else None,
+                              st.ctypes.data, ln.ctypes.data, int(ln.size), int(rank),
+                              out.ctypes.data)
+    if rc != 0:
+        raise ValueError("hs_merge_split: invalid arguments")
+    return out
 
 
 def hs_set_option(name: str, value: int) -> None:

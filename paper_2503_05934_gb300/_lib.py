@@ -68,6 +68,7 @@ SIGNATURES = {
     "hs_i64_tile": (_sz, [_u32, _sz]),
     "hs_network_pairs": (_int, [_int, ctypes.POINTER(ctypes.c_int), _int]),
     "hs_network_apply": (_int, [_int, _c_i32p]),
+    "hs_merge_split": (_int, [_vp, _vp, _vp, _vp, _int, ctypes.c_int64, _vp]),
 }
 
 

@@ -127,7 +127,7 @@ def main(argv=None) -> int:
         torch.cuda.synchronize()
         hs.hs_prof_enable(False)
         out["kernels"] = {}
-        for name in ("blocksort_keys", "blocksort_pairs", "merge_partition", "merge_keys",
+        for name in ("blocksort_keys", "blocksort_pairs", "merge_partition", "merge_keys", "merge4_keys",
                      "merge_pairs", "qs_plan", "qs_partition", "qs_leaves", "seg_classify",
                      "seg_sort"):
             launches, ms = hs.hs_prof_read(name)

@@ -101,7 +101,7 @@ HS_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::c
 
 // x[k] for a run-time k in [0, N) without local memory: a select tree on k's bits.
 template <int N, class K>
-HS_DEV K select_dyn(const K (&x)[N], int k) {
+HS_HD K select_dyn(const K (&x)[N], int k) {
     constexpr int P = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : N <= 32 ? 32 : 64;
     static_assert(N <= P, "select_dyn covers arrays of up to 64 entries");
     K v[P];

@@ -23,6 +23,7 @@ enum KernelId {
     K_SEG_CLASSIFY,
     K_SEG_SORT,
     K_SELFTEST,
+    K_MERGE4_KEYS,
     K_COUNT
 };
 const char *kernel_name(int id);
@@ -73,12 +74,15 @@ hs_status ensure_smem(const void *func, int bytes);
 // sorts keys, or stable pairs when d_vals is non-null (pairs_sort).
 //
 // Workspace layout (each part 256-byte aligned): the keys ping-pong copy,
-// the values copy (pairs), the merge partition indices (n/1024 + 8 int64:
-// more than the output tiles of any level, whose tiles hold at least 1984
-// keys), and the keys' samples (every 32nd key, n/32 + 8 int32).
+// the values copy (pairs), the merge partition indices (n/256 + 64 int64:
+// one per output tile of a binary level, whose tiles hold at least 1984
+// keys, or four per tile boundary of a four-way level, whose tiles hold 3936
+// keys over groups of at least four block-sort tiles of 768 keys), and the
+// keys' samples (every 32nd key, n/32 + 8 int32).
 constexpr size_t ws_align(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t merge_ws_keys_bytes(size_t n) { return ws_align(n * sizeof(int32_t)); }
-constexpr size_t merge_ws_part_bytes(size_t n) { return ws_align((n / 1024 + 8) * sizeof(int64_t)); }
+constexpr size_t merge_ws_part_entries(size_t n) { return n / 256 + 64; }
+constexpr size_t merge_ws_part_bytes(size_t n) { return ws_align(merge_ws_part_entries(n) * sizeof(int64_t)); }
 constexpr size_t merge_ws_samp_bytes(size_t n) { return ws_align((n / 32 + 8) * sizeof(int32_t)); }
 constexpr size_t merge_workspace_size(size_t n, int with_values) {
     return merge_ws_keys_bytes(n) * (with_values ? 2 : 1) + merge_ws_part_bytes(n) +
@@ -113,6 +117,7 @@ void merge_set_blocksort_bulk(int v);
 void pairs_set_blocksort_bulk(int v);
 void segsort_set_bulk(int v);
 void merge_set_samples(int v);
+void merge_set_fanin(int v);
 
 // Block sort of [0, n) in tiles of keys_tile(L) keys (the merge path's first pass;
 // the whole sort when n fits one tile).

@@ -7,6 +7,7 @@
 #include "hs_internal.h"
 #include "hs_blocksort.cuh"
 #include "hs_merge_tile.cuh"
+#include "hs_merge4.cuh"
 
 namespace hs {
 
@@ -144,28 +145,91 @@ static hs_status launch_keys_level(const int32_t *kin, int32_t *kout, int64_t n,
     return launch_end(t);
 }
 
-// Sorts d_keys[0, n) with explicit scratch: kbuf (n keys), part (the
-// partition entries of n keys) and samp (every 32nd key of n keys, or null
-// for plain partition searches).  The result lands in d_keys.
+// Option "merge_fanin": 4 (default) the tiled keys levels merge four runs
+// per pass (two binary levels of Algorithm 1's Merge in one read and one
+// write of every key; a binary level first when the number of doublings is
+// odd); 2 binary levels only.
+static int g_merge_fanin = 4;
+void merge_set_fanin(int v) { g_merge_fanin = v; }
+
+// Four-way tile: 128 threads x 31 keys, 3936 keys per tile.  With 192 or
+// 256 threads (5920 / 7904 keys) the partitions shrink in number but the
+// merge slows more: 4.26 / 4.36 ms of four-way levels per 2^28 sort against
+// 4.02 ms.
+constexpr int M4_NT = 128, M4_EO = 31;
+
+// One four-way keys level: its partition (four splits per tile boundary,
+// part_cap int64 entries available) and its merge.
+static hs_status launch_keys_level4(const int32_t *kin, int32_t *kout, int64_t n, int64_t w,
+                                    int64_t *part, int64_t part_cap, int32_t *samp,
+                                    cudaStream_t st) {
+    using C = TileMerge4<M4_NT, M4_EO>;
+    static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
+    unsigned *status = nullptr;
+    hs_status r = device_status(&status);
+    if (r != HS_OK) return r;
+    const LevelTiles lt = level_tiles_span(n, 4 * w, C::TO);
+    if (4 * (lt.nblocks + 1) > part_cap)
+        return fail(HS_ERR_INVALID_ARG, "merge sort: workspace too small for the four-way partitions");
+    LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
+    k_merge4_partition<4><<<(unsigned)((lt.nblocks + 127) / 128), 128, 0, st>>>(
+        kin, samp, n, w, C::TO, lt.tpg, lt.nblocks, part);
+    if ((r = launch_end(t)) != HS_OK) return r;
+    auto kern = k_merge4_tile_bulk<M4_NT, M4_EO>;
+    if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
+    t = launch_begin(K_MERGE4_KEYS, st);
+    kern<<<(unsigned)lt.nblocks, M4_NT, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, lt.tpg, samp,
+                                                             status);
+    return launch_end(t);
+}
+
+// Whether the global levels over an n-key array merge four runs per pass.
+static bool four_way_levels(int64_t n, int vec) { return g_merge_fanin == 4 && tiled_levels(n, vec); }
+
+// Launches of the global levels that double the runs d times.
+static int level_launches(int d, bool four) { return four ? d / 2 + d % 2 : d; }
+
+// Runs the global levels that take sorted runs of w keys through d
+// doublings (one launch pair per binary or four-way level), ping-ponging
+// kcur/kalt; on return kcur holds the result.
+static hs_status run_levels(int32_t *&kcur, int32_t *&kalt, int64_t n, int64_t w, int d,
+                            bool four, int64_t *part, int64_t part_cap, int32_t *samp, int vec,
+                            cudaStream_t st) {
+    hs_status r = HS_OK;
+    while (d > 0 && r == HS_OK) {
+        if (four && d % 2 == 0) {
+            r = launch_keys_level4(kcur, kalt, n, w, part, part_cap, samp, st);
+            w *= 4;
+            d -= 2;
+        } else {
+            r = launch_keys_level(kcur, kalt, n, w, part, samp, vec, st);
+            w *= 2;
+            d -= 1;
+        }
+        std::swap(kcur, kalt);
+    }
+    return r;
+}
+
+// Sorts d_keys[0, n) with explicit scratch: kbuf (n keys), part (part_cap
+// partition entries) and samp (every 32nd key of n keys, or null for plain
+// partition searches).  The result lands in d_keys.
 static hs_status merge_sort_with(int32_t *d_keys, int64_t n, hs_netset s, int32_t *kbuf,
-                                 int64_t *part, int32_t *samp, cudaStream_t st) {
+                                 int64_t *part, int64_t part_cap, int32_t *samp,
+                                 cudaStream_t st) {
     const int L = leaf_size(s);
     const int64_t T = keys_tile(L, n);
-    int passes = 0;
-    for (int64_t w = T; w < n; w *= 2) ++passes;
+    const int d = global_levels(n, T);
     const int vec = aligned(d_keys, 16) ? 1 : 0;
     if (!tiled_levels(n, vec)) samp = nullptr;
+    const bool four = four_way_levels(n, vec);
     // Land the last level in the caller's array: with an even number of
-    // global levels the block sort writes in place.
-    int32_t *kcur = (passes % 2 == 0) ? d_keys : kbuf;
+    // launched levels the block sort writes in place.
+    int32_t *kcur = (level_launches(d, four) % 2 == 0) ? d_keys : kbuf;
     int32_t *kalt = (kcur == d_keys) ? kbuf : d_keys;
     hs_status r = blocksort_launch(L, d_keys, kcur, n, s, vec, st, samp);
     if (r != HS_OK) return r;
-    for (int64_t w = T; w < n; w *= 2) {
-        if ((r = launch_keys_level(kcur, kalt, n, w, part, samp, vec, st)) != HS_OK) return r;
-        std::swap(kcur, kalt);
-    }
-    return HS_OK;
+    return run_levels(kcur, kalt, n, T, d, four, part, part_cap, samp, vec, st);
 }
 
 struct MergeScratch {
@@ -194,7 +258,7 @@ hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, v
         return fail(HS_ERR_INVALID_ARG, "merge sort: workspace smaller than hs_sort_workspace_bytes");
     if (!aligned(d_ws, 16)) return fail(HS_ERR_INVALID_ARG, "merge sort: workspace not 16-byte aligned");
     const MergeScratch m = carve_merge_workspace(d_ws, n_);
-    return merge_sort_with(d_keys, n, s, m.kbuf, m.part, m.samp, st);
+    return merge_sort_with(d_keys, n, s, m.kbuf, m.part, (int64_t)merge_ws_part_entries(n_), m.samp, st);
 }
 
 // Chunk-local merge levels of the host-buffer sort: the most that keep one
@@ -234,6 +298,10 @@ hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, h
     const MergeScratch m = carve_merge_workspace(d_ws, n_);
     const int vec = aligned(d_keys, 16) ? 1 : 0;
     int32_t *samp = tiled_levels(n, vec) ? m.samp : nullptr;
+    // Decided once for the whole array, so that every chunk runs the same
+    // number of launches (the parity that places its block sort).
+    const bool four = four_way_levels(n, vec);
+    const int64_t part_cap = (int64_t)merge_ws_part_entries(n_);
 
     cudaStream_t cs = nullptr;
     cudaEvent_t ev[kChunks] = {};
@@ -252,21 +320,16 @@ hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, h
             r = fail_cuda(e, "host sort: wait for a chunk");
             break;
         }
-        // The block sort writes where k ping-pong levels end in d_keys.
-        int32_t *cur = (k % 2 == 0) ? d_keys + b : m.kbuf + b;
-        int32_t *alt = (k % 2 == 0) ? m.kbuf + b : d_keys + b;
+        // The block sort writes where the chunk's ping-pong levels end in d_keys.
+        const bool even = level_launches(k, four) % 2 == 0;
+        int32_t *cur = even ? d_keys + b : m.kbuf + b;
+        int32_t *alt = even ? m.kbuf + b : d_keys + b;
         int32_t *csamp = samp ? samp + b / kSampleStride : nullptr;
         r = blocksort_launch_shape(shape, L, d_keys + b, cur, len, s, vec, st, csamp);
-        for (int j = 0; j < k && r == HS_OK; ++j) {
-            r = launch_keys_level(cur, alt, len, T << j, m.part, csamp, vec, st);
-            std::swap(cur, alt);
-        }
+        if (r == HS_OK) r = run_levels(cur, alt, len, T, k, four, m.part, part_cap, csamp, vec, st);
     }
     int32_t *kcur = d_keys, *kalt = m.kbuf;
-    for (int64_t w = W; w < n && r == HS_OK; w *= 2) {
-        r = launch_keys_level(kcur, kalt, n, w, m.part, samp, vec, st);
-        std::swap(kcur, kalt);
-    }
+    if (r == HS_OK) r = run_levels(kcur, kalt, n, W, levels - k, four, m.part, part_cap, samp, vec, st);
     if (r == HS_OK && (e = cudaMemcpyAsync(h_keys, kcur, n_ * sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         r = fail_cuda(e, "host sort: copy out");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess && r == HS_OK) r = fail_cuda(e, "host sort: synchronize");

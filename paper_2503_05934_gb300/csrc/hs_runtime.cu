@@ -11,6 +11,7 @@
 #include "hs_bulk.cuh"
 #include "hs_common.cuh"
 #include "hs_networks.cuh"
+#include "hs_merge4.cuh"
 
 namespace hs {
 
@@ -19,13 +20,13 @@ namespace hs {
 static const char *const kRangeNames[K_COUNT] = {
     "hs:blocksort_keys", "hs:blocksort_pairs", "hs:merge_partition", "hs:merge_keys",
     "hs:merge_pairs",    "hs:qs_plan",         "hs:qs_partition",    "hs:qs_leaves",
-    "hs:seg_classify",   "hs:seg_sort",        "hs:selftest"};
+    "hs:seg_classify",   "hs:seg_sort",        "hs:selftest",        "hs:merge4_keys"};
 
 static const char *const kKernelNames[K_COUNT] = {
     "blocksort_keys", "blocksort_pairs", "merge_partition", "merge_keys",
     "merge_pairs",    "qs_plan",         "qs_partition",
     "qs_leaves",      "seg_classify",    "seg_sort",
-    "selftest"};
+    "selftest",       "merge4_keys"};
 
 const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kKernelNames[id] : "?"; }
 
@@ -190,6 +191,21 @@ hs_status ensure_smem(const void *func, int bytes) {
     if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute");
     done.push_back({func, dev});
     return HS_OK;
+}
+
+template <int K>
+static void merge_split_k(const int32_t *keys, const int32_t *samp, const int64_t *starts,
+                          const int64_t *lens, int64_t rank, int64_t *a) {
+    KwayRuns<K> R;
+    R.keys = keys;
+    R.samp = samp;
+    for (int i = 0; i < K; ++i) {
+        R.start[i] = starts[i];
+        R.len[i] = lens[i];
+    }
+    int64_t out[K];
+    kway_split<K>(R, rank, out);
+    for (int i = 0; i < K; ++i) a[i] = out[i];
 }
 
 }  // namespace hs
@@ -402,6 +418,12 @@ hs_status hs_set_option(const char *name, int64_t value) {
         merge_set_blocksort_threads((int)value);
         return HS_OK;
     }
+    if (std::strcmp(name, "merge_fanin") == 0) {
+        if (value != 2 && value != 4)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_fanin must be 2 or 4");
+        merge_set_fanin((int)value);
+        return HS_OK;
+    }
     if (std::strcmp(name, "merge_samples") == 0) {
         if (value != 0 && value != 1)
             return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_samples must be 0 or 1");
@@ -469,6 +491,25 @@ int hs_network_pairs(int m, int *pairs, int cap) {
     op.cap = cap;
     network_dyn(m, op);
     return op.n;
+}
+
+int hs_merge_split(const int32_t *keys, const int32_t *samp, const int64_t *starts,
+                   const int64_t *lens, int k_runs, int64_t rank, int64_t *a) {
+    if (!starts || !lens || !a || (k_runs != 2 && k_runs != 4 && k_runs != 8)) return -1;
+    int64_t total = 0;
+    for (int i = 0; i < k_runs; ++i) {
+        if (lens[i] < 0 || starts[i] < 0) return -1;
+        if (lens[i] > 0 && !keys) return -1;
+        if (samp && starts[i] % kSampleStride != 0) return -1;
+        total += lens[i];
+    }
+    if (rank < 0 || rank > total) return -1;
+    switch (k_runs) {
+        case 2: merge_split_k<2>(keys, samp, starts, lens, rank, a); break;
+        case 4: merge_split_k<4>(keys, samp, starts, lens, rank, a); break;
+        default: merge_split_k<8>(keys, samp, starts, lens, rank, a); break;
+    }
+    return 0;
 }
 
 int hs_network_apply(int m, int32_t *a) {

@@ -255,12 +255,67 @@ def test_workspace_reuse_and_launch_count(hs):
         torch.cuda.synchronize()
         assert np.array_equal(t.cpu().numpy(), np.sort(a))
     # 1 block sort + 2 launches (partition, merge) per global level over the
-    # block-sort tile the library reports for this n
+    # block-sort tile the library reports for this n; four-way levels take
+    # two doublings each, after one binary level when their number is odd
     tile = int(hs.lib().hs_keys_tile(hs.netset_mask("6To8"), n))
     levels = 0
     while tile << levels < n:
         levels += 1
-    assert hs.hs_launch_count() - before == 3 * (1 + 2 * levels)
+    assert hs.hs_launch_count() - before == 3 * (1 + 2 * (levels // 2 + levels % 2))
+
+
+def _four_way_inputs(n, seed):
+    """Key patterns that stress the four-way split: uniform, few distinct
+    values (equal keys spanning all four runs of a group), sorted, reversed,
+    descending blocks (later runs of a group hold smaller keys), all equal,
+    and only the two extreme values."""
+    a = g.random_i32(n, seed)
+    blocks = max(1, n // 5000)
+    desc = (np.arange(n, dtype=np.int64) // 5000)
+    return {
+        "uniform": a,
+        "few": (a % 3).astype(np.int32),
+        "sorted": np.sort(a),
+        "reverse": np.sort(a)[::-1].copy(),
+        "desc_blocks": ((blocks - desc) * 1000 + (a % 1000)).astype(np.int32),
+        "all_equal": np.full(n, -5, np.int32),
+        "extremes": np.where(a > 0, 2**31 - 1, -2**31).astype(np.int32),
+    }
+
+
+@pytest.mark.parametrize("netset", ["6To8", "3To5"])
+def test_four_way_levels(hs, netset):
+    """Four-way merge levels (two of Algorithm 1's merge levels per pass)
+    against the oracle and against binary levels only: odd and even numbers
+    of doublings, last groups with one to four runs, partial last runs, and
+    the key patterns of _four_way_inputs."""
+    mask = hs.netset_mask(netset)
+    cases = []
+    for base in [1 << 16, 1 << 20, 3 << 20]:
+        T = int(hs.lib().hs_keys_tile(mask, base))
+        cases += [2 * T, 3 * T + 4, 4 * T, 4 * T + 8, 5 * T, 7 * T - 4, 8 * T, 9 * T + 12,
+                  16 * T + 4, 17 * T + 4, 33 * T - 8, 64 * T + 100]
+    cases += [(1 << 22) + 4 * 12_345, 3 << 22]
+    cases = sorted({c for c in cases if c % 4 == 0})
+    try:
+        for n in cases:
+            for name, a in _four_way_inputs(n, n).items():
+                want = oracle.merge_sort(a, netset)
+                for fanin in (4, 2):
+                    hs.hs_set_option("merge_fanin", fanin)
+                    assert np.array_equal(gpu_sort(hs, a, "merge", netset), want), (n, name, fanin)
+    finally:
+        hs.hs_set_option("merge_fanin", 4)
+
+
+def test_four_way_levels_unaligned_and_ragged(hs):
+    """Unaligned starts and lengths that are not multiples of four take the
+    binary generic levels; the result is the same."""
+    for n in [4 * 8928 + 1, 16 * 8928 + 3, (1 << 20) + 2]:
+        a = g.random_i32(n, 3 * n)
+        want = oracle.merge_sort(a, "6To8")
+        assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), want), n
+        assert np.array_equal(gpu_sort(hs, a, "merge", "6To8", offset=1), want), n
 
 
 def test_tail_not_multiple_of_four(hs):
@@ -331,13 +386,16 @@ def test_profiling_counters(hs):
         torch.cuda.synchronize()
         n_bs, ms_bs = hs.hs_prof_read("blocksort_keys")
         n_mk, ms_mk = hs.hs_prof_read("merge_keys")
+        n_m4, ms_m4 = hs.hs_prof_read("merge4_keys")
     finally:
         hs.hs_prof_enable(False)
     tile = int(hs.lib().hs_keys_tile(hs.netset_mask("6To8"), 1 << 18))
     levels = 0
     while tile << levels < (1 << 18):
         levels += 1
-    assert n_bs == 1 and n_mk == levels and ms_bs > 0 and ms_mk > 0
+    # binary level first when the number of doublings is odd, then four-way
+    assert levels == 5
+    assert n_bs == 1 and n_mk == 1 and n_m4 == 2 and min(ms_bs, ms_mk, ms_m4) > 0
 
 
 def test_profiling_one_kernel(hs):

@@ -137,6 +137,7 @@ OPTIONS = [
     ("merge_tile", 9, 5, [-1, 11]),
     ("merge_kernel", 1, 0, [2]),
     ("merge_samples", 1, 0, [2]),
+    ("merge_fanin", 4, 2, [0, 1, 3, 8]),
     ("blocksort_shape", -1, 4, [-2, 6]),
     ("blocksort_bulk", 1, 0, [2, -1]),
     ("pairs_blocksort", 0, 3, [4]),
@@ -160,3 +161,66 @@ def test_option_values_are_validated(hs, name, default, other, bad):
 
 def test_unknown_option_is_rejected(hs):
     assert hs.hs_set_option(b"no_such_option", 1) == 1
+
+
+def _brute_split(keys, starts, lens, rank):
+    """Counts per run among the first `rank` outputs of the stable merge:
+    order by (key, run), positions ascending within a run (lexsort)."""
+    run_of, vals = [], []
+    for i, (s, ln) in enumerate(zip(starts, lens)):
+        vals.append(keys[s:s + ln])
+        run_of.append(np.full(ln, i, np.int64))
+    v = np.concatenate(vals) if vals else np.zeros(0, np.int32)
+    r = np.concatenate(run_of) if run_of else np.zeros(0, np.int64)
+    order = np.lexsort((np.arange(v.size), r, v.astype(np.int64)))
+    return np.bincount(r[order[:rank]], minlength=len(lens))
+
+
+@pytest.mark.parametrize("k_runs", [2, 4, 8])
+def test_merge_split_host_against_brute_force(k_runs):
+    """The four-way levels' K-way split (host build) equals the counts of a
+    brute-force stable merge at every rank, on runs with heavy duplicates,
+    all-equal keys, disjoint ranges, empty and ragged runs, with and without
+    the sample array."""
+    import paper_2503_05934_gb300 as hs
+    rng = np.random.default_rng(7 + k_runs)
+    for trial in range(60):
+        kind = trial % 4
+        lens = [int(x) for x in rng.integers(0, 200, k_runs)]
+        if trial % 5 == 0:
+            lens[int(rng.integers(0, k_runs))] = 0
+        runs = []
+        for i, ln in enumerate(lens):
+            if kind == 0:
+                x = rng.integers(-4, 4, ln)
+            elif kind == 1:
+                x = rng.integers(-2**31, 2**31, ln)
+            elif kind == 2:
+                x = np.arange(ln) + 1000 * (k_runs - i)  # later runs hold smaller keys
+            else:
+                x = np.full(ln, 2**31 - 1)
+            runs.append(np.sort(x).astype(np.int32))
+        # runs at 32-aligned starts with gaps, so the sample array applies
+        starts, keys = [], np.zeros(0, np.int32)
+        for r in runs:
+            pad = (-keys.size) % 32 + 32 * int(rng.integers(0, 2))
+            keys = np.concatenate([keys, rng.integers(-9, 9, pad).astype(np.int32)])
+            starts.append(keys.size)
+            keys = np.concatenate([keys, r])
+        samp = keys[::32].copy()
+        total = sum(lens)
+        for rank in sorted(set([0, total] + [int(x) for x in rng.integers(0, total + 1, 25)])):
+            want = _brute_split(keys, starts, lens, rank)
+            assert np.array_equal(hs.hs_merge_split(keys, starts, lens, rank), want)
+            assert np.array_equal(hs.hs_merge_split(keys, starts, lens, rank, samp), want)
+
+
+def test_merge_split_host_rejects_bad_arguments():
+    import paper_2503_05934_gb300 as hs
+    keys = np.arange(64, dtype=np.int32)
+    with pytest.raises(ValueError):
+        hs.hs_merge_split(keys, [0, 32, 40], [8, 8, 8], 3)  # 3 runs
+    with pytest.raises(ValueError):
+        hs.hs_merge_split(keys, [0, 32], [8, 8], 17)  # rank past the total
+    with pytest.raises(ValueError):
+        hs.hs_merge_split(keys, [0, 33], [8, 8], 3, keys[::32])  # unaligned start with samples
