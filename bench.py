@@ -274,6 +274,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
         "data": "synthetic", "config": workload_config(args, n),
+        # what each step actually sorted: a bounded sample of the workload
+        # named in config, so keys/s compare per key
+        "sample_sorted": {"n": sample_n, "of_n": n, "keys": "first keys of the same seeded array"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -149,15 +149,18 @@ HS_API hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netse
  * synchronise the device and stall.  The paper has no counterpart; this is a
  * library convenience around the HS_ALGO_MERGE path of hs_sort_i32.
  *   d_keys, n, s, stream   as hs_sort_i32; no workspace argument.
- *   Scratch: a fixed __device__ array of about 16 MiB inside the library (keys
- *     copy + partition indices for HS_NOALLOC_MAX_KEYS keys).  Every GPU where
- *     the library's code is loaded holds it until the process exits.
+ *   Scratch: a fixed __device__ array of 17,433,344 bytes (16.6 MiB) inside
+ *     the library (keys copy, partition entries and samples for
+ *     HS_NOALLOC_MAX_KEYS keys).  Every GPU where the library's code is loaded
+ *     holds it until the process exits.
  *   Limit: n <= HS_NOALLOC_MAX_KEYS (2^22 = 4,194,304 keys); a larger n returns
  *     HS_ERR_INVALID_ARG before any launch.
  *   Set-up: the first call on a device, with that device current, looks up the
- *     scratch array's device address (cudaGetSymbolAddress) and caches it; make
- *     that first call before any stream capture.  The current device must be
- *     the one that owns d_keys and stream.
+ *     scratch array's device address (cudaGetSymbolAddress) and caches it for
+ *     the life of the process; make that first call before any stream capture.
+ *     The current device must be the one that owns d_keys and stream.  Do not
+ *     use this entry point across a cudaDeviceReset of a device it has run on:
+ *     the cached address belongs to the context that the reset destroyed.
  *   Sharing: every call uses the same scratch array, which keeps the previous
  *     call's contents (nothing in it needs to start at zero).  Calls whose GPU
  *     work overlaps (other streams, other host threads) race on it: serialise
@@ -254,7 +257,10 @@ HS_API hs_status hs_tune_cache_load(const char *path);
  *     pool of budget_bytes once, plus four streams.
  *   hs_server_submit: returns at once with a ticket; HS_ERR_OVER_BUDGET if the
  *     request alone exceeds the budget; HS_ERR_UNSUPPORTED for HS_ALGO_QUICK.
- *     The caller must not touch d_keys until hs_server_wait returns.
+ *     d_keys must hold its final contents when submit is called: the server's
+ *     streams wait on no stream of the caller, so keys written asynchronously
+ *     must be complete first (for example, synchronise the stream that wrote
+ *     them).  The caller must not touch d_keys until hs_server_wait returns.
  *   hs_server_wait: blocks until the request finished; *result is its status,
  *     *latency_s the seconds from submit to completion.  Each ticket is waited
  *     for once.

@@ -204,13 +204,35 @@ def hoare_partition(a: np.ndarray, low: int, high: int, pivot_index: int):
     return out, int(j)
 
 
-def segsort(a: np.ndarray, offsets: np.ndarray, algo: str = "merge", netset="6To8") -> np.ndarray:
+def segsort(a: np.ndarray, offsets: np.ndarray, algo: str = "merge", netset="6To8",
+            threads: int = 1) -> np.ndarray:
+    """Sorts every segment a[off[i]:off[i+1]] on a copy (Algorithm 1 or 2
+    per segment).  threads > 1 hands disjoint ranges of whole segments to
+    that many host threads (the segments are independent; ctypes releases
+    the GIL during each call), which changes nothing in the arithmetic."""
     out = np.ascontiguousarray(a, dtype=np.int32).copy()
     off = np.ascontiguousarray(offsets, dtype=np.int64)
-    rc = lib().or_segsort(_i32(out), _i64(off), off.size - 1, 0 if algo == "merge" else 1,
-                          netset_mask(netset))
-    if rc:
-        raise ValueError(f"or_segsort failed ({rc})")
+    nseg = off.size - 1
+    mode, mask = 0 if algo == "merge" else 1, netset_mask(netset)
+
+    def run(s0: int, s1: int) -> int:
+        if s1 <= s0:
+            return 0
+        sub = out[off[s0]:off[s1]]
+        o = np.ascontiguousarray(off[s0:s1 + 1] - off[s0])
+        return lib().or_segsort(_i32(sub), _i64(o), s1 - s0, mode, mask)
+
+    if threads <= 1 or nseg < 2 * threads:
+        rcs = [run(0, nseg)]
+    else:
+        import concurrent.futures as cf
+        # ranges of about equal key counts
+        cuts = np.searchsorted(off, np.linspace(off[0], off[-1], threads + 1)[1:-1])
+        bounds = [0] + sorted(set(int(c) for c in cuts)) + [nseg]
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            rcs = list(ex.map(lambda ab: run(*ab), zip(bounds[:-1], bounds[1:])))
+    if any(rcs):
+        raise ValueError(f"or_segsort failed ({[r for r in rcs if r]})")
     return out
 
 

@@ -294,8 +294,11 @@ def hs_sort_i32_noalloc(keys: torch.Tensor, netset="6To8", stream=None) -> torch
     workspace, no device allocation); ``keys.numel()`` <= NOALLOC_MAX_KEYS."""
     _check_i32(keys, "keys")
     n = keys.numel()
-    check(lib().hs_sort_i32_noalloc(keys.data_ptr() if n else None, n, netset_mask(netset),
-                                    _stream_ptr(stream)))
+    # The library picks the scratch array of the current device: make it the
+    # keys' device for the call (and take that device's stream by default).
+    with torch.cuda.device(keys.device):
+        check(lib().hs_sort_i32_noalloc(keys.data_ptr() if n else None, n, netset_mask(netset),
+                                        _stream_ptr(stream)))
     return keys
 
 

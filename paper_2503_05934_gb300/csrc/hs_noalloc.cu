@@ -23,6 +23,9 @@ constexpr size_t kNoallocMaxKeys = HS_NOALLOC_MAX_KEYS;
 // formula as hs_sort_workspace_bytes (the layout grows monotonically in n, so
 // every shorter input fits).
 constexpr size_t kNoallocBytes = merge_workspace_size(kNoallocMaxKeys, 0);
+// 17,433,344 bytes (16.6 MiB): 16 MiB of keys, 131,584 bytes of partition
+// entries and 524,544 bytes of samples.  The header states this figure.
+static_assert(kNoallocBytes == 17433344, "the scratch size the header documents changed");
 
 // The scratch area.  In host code this name is only a host-side stand-in for
 // the device symbol: its device address comes from cudaGetSymbolAddress below.
@@ -58,6 +61,7 @@ using namespace hs;
 
 extern "C" hs_status hs_sort_i32_noalloc(int32_t *d_keys, size_t n, hs_netset s,
                                          hs_stream_t stream) {
+    const ApiRange range("hs_sort_i32_noalloc");
     clear_error();
     if (!netset_ok(s))
         return fail(HS_ERR_INVALID_ARG, "hs_sort_i32_noalloc: netset is neither a set of sizes 3..8 nor a VarSort configuration");

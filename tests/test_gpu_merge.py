@@ -417,9 +417,10 @@ def test_profiling_one_kernel(hs):
 
 
 def test_full_size_keys_2p28(hs):
-    """2^28 uniform int32 keys, {6,7,8}: the benchmark's workload and launch
-    configuration, checked by sortedness, multiset fingerprint and sampled
-    order statistics from the oracle."""
+    """2^28 uniform int32 keys, {6,7,8}: the benchmark's workload (same seed)
+    and launch configuration, equal element by element to the oracle's
+    Algorithm 1 on the whole array; sortedness, multiset fingerprint and
+    sampled order statistics as well."""
     import torch
     n = 1 << 28
     a = g.random_i32(n, g.config_seed(2))
@@ -428,11 +429,30 @@ def test_full_size_keys_2p28(hs):
     hs.hs_device_check()
     out = t.cpu().numpy()
     del t
+    assert np.array_equal(out, oracle.merge_sort(a, "6To8"))
     check_sorted_permutation(a, out, samples=6)
 
 
+def test_above_2p31_keys(hs):
+    """2^31 + 49,380 uniform keys (8 GiB, a multiple of four: the tiled
+    binary and four-way levels), past every 32-bit index: sorted, multiset
+    fingerprint kept, sampled order statistics from the oracle's counts."""
+    import torch
+    n = (1 << 31) + 49_380
+    a = g.random_i32(n, g.config_seed(2, salt=31))
+    t = to_dev(a)
+    hs.hs_sort_i32(t, "merge", "6To8")
+    hs.hs_device_check()
+    out = t.cpu().numpy()
+    del t
+    torch.cuda.empty_cache()
+    check_sorted_permutation(a, out, samples=4)
+
+
 def test_full_size_pairs_2p27(hs):
-    """2^27 stable pairs, keys from 2^16 distinct values, value = index."""
+    """2^27 stable pairs, keys from 2^16 distinct values, value = index (the
+    benchmark's pair workload): equal element by element to the oracle's
+    stable Algorithm 1, and a complete stability check."""
     import torch
     n = 1 << 27
     k, v = g.pair_keys_16bit(n, g.config_seed(2, salt=1))
@@ -441,4 +461,6 @@ def test_full_size_pairs_2p27(hs):
     torch.cuda.synchronize()
     ko, vo = tk.cpu().numpy(), tv.cpu().numpy()
     del tk, tv
+    ek, ev = oracle.merge_sort_pairs(k, v, "6To8")
+    assert np.array_equal(ko, ek) and np.array_equal(vo, ev)
     check_stable_pairs_index_values(k, ko, vo)

@@ -82,6 +82,16 @@ def test_depth_guard_fallback(hs, cap):
     assert np.array_equal(out, oracle.quick_sort(a, "6To8"))
 
 
+def test_full_size_quick_2p28(hs):
+    """2^28 uniform keys through the quick path (the benchmark's quick
+    workload, same seed), equal element by element to the oracle's
+    Algorithm 2."""
+    n = 1 << 28
+    a = g.random_i32(n, g.config_seed(2))
+    out = gpu_quick(hs, a, "6To8")
+    assert np.array_equal(out, oracle.quick_sort(a, "6To8"))
+
+
 def test_large_quick_2p26(hs):
     import torch
     n = 1 << 26

@@ -192,6 +192,25 @@ def test_prefix_of_the_batched_workload(hs):
     assert fingerprint(out) == fingerprint(keys)
 
 
+def test_full_batched_workload_against_oracle(hs):
+    """The whole batched workload of the benchmark: 200,000 segments, sizes
+    log-uniform in [3, 65,536] (about 1.31 G keys), mixed distributions, in
+    one persistent launch with the default plan: equal element by element
+    to the oracle sorting every segment (host threads over disjoint ranges
+    of whole segments)."""
+    import os
+    import torch
+    keys, off, _ = g.segmented(200_000, g.config_seed(3))
+    tk, to = _dev(hs, keys, off)
+    hs.hs_segsort_i32(tk, to)
+    hs.hs_device_check()
+    out = tk.cpu().numpy()
+    del tk, to
+    torch.cuda.empty_cache()
+    want = oracle.segsort(keys, off, "merge", "6To8", threads=min(16, os.cpu_count() or 1))
+    assert np.array_equal(out, want)
+
+
 @pytest.mark.parametrize("bulk", [0, 1])
 @pytest.mark.parametrize("shift", [0, 1, 3])
 def test_bulk_and_thread_staging(hs, bulk, shift):

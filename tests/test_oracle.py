@@ -302,3 +302,16 @@ def test_int64_merge_sort(netset):
         _, c64 = oracle.merge_sort_i64(hs_inputs.keys_i64(n, "random", 1), netset, counters=True)
         _, c32 = oracle.merge_sort(hs_inputs.random_i32(n, 1), netset, counters=True)
         assert c64["net_calls"] == c32["net_calls"] and c64["merge_calls"] == c32["merge_calls"]
+
+
+def test_segsort_threads_give_the_same_result(oracle_lib):
+    """The threaded driver of the oracle's segmented sort hands disjoint
+    ranges of whole segments to host threads: the result equals the
+    single-threaded call and numpy's per-segment sort."""
+    import hs_inputs as g
+    keys, off, _ = g.segmented(3000, 11)
+    one = oracle_lib.segsort(keys, off, "merge", "6To8")
+    many = oracle_lib.segsort(keys, off, "merge", "6To8", threads=7)
+    assert np.array_equal(one, many)
+    for s in (0, 1, 1499, 2999):
+        assert np.array_equal(many[off[s]:off[s + 1]], np.sort(keys[off[s]:off[s + 1]]))

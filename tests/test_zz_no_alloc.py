@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import hs_inputs as g
+import oracle
 from helpers import hs_module
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +48,22 @@ def test_noalloc_matches_workspace_entry_point_on_consecutive_calls():
         torch.cuda.synchronize()
         assert torch.equal(got, want), n
         assert np.all(np.diff(got.cpu().numpy().astype(np.int64)) >= 0)
+        # and directly against the oracle's Algorithm 1
+        assert np.array_equal(got.cpu().numpy(), oracle.merge_sort(a, "6To8")), n
+
+
+def test_noalloc_python_binding_uses_the_keys_device():
+    """The Python binding runs the call with the keys' device current (its
+    scratch array and stream are that device's), and sorts as the oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    hs = hs_module()
+    a = g.random_i32(300_001, 43)
+    t = torch.from_numpy(a).cuda()
+    hs.hs_sort_i32_noalloc(t, "6To8")
+    torch.cuda.synchronize()
+    assert np.array_equal(t.cpu().numpy(), oracle.merge_sort(a, "6To8"))
 
 
 def test_noalloc_rejects_sizes_above_the_limit():
