@@ -43,7 +43,7 @@ _CSRC = "paper_2503_05934_gb300/csrc/"
 KERNEL_SOURCES = {
     "merge_keys": [_CSRC + f for f in ("hs_merge_tile.cuh", "hs_bulk.cuh",
                                        "hs_merge_prims.cuh", "hs_common.cuh")],
-    "merge4_keys": [_CSRC + f for f in ("hs_merge4.cuh", "hs_merge.cu", "hs_bulk.cuh",
+    "merge4_keys": [_CSRC + f for f in ("hs_merge4.cuh", "hs_bulk.cuh",
                                         "hs_merge_prims.cuh", "hs_common.cuh")],
 }
 

@@ -340,52 +340,19 @@ HS_API hs_status hs_bulk_wait_selftest(uint32_t polls, hs_stream_t stream);
  *   "quick_partition": 3 (default) 3-way partitions (< / = / > pivot); 2 the
  *     2-way form of Algorithm 2 (left <= pivot <= right, keys equal to the
  *     pivot alternating sides by their rank among the equal keys).
- *   "blocksort_shape": keys block-sort shape, 0: 512 threads x 2 leaves,
- *     1: 1024 x 2, 2: 256 x 4, 3: 512 x 4, 4: 288 x 4, 5: 576 x 4, -1 (default): per
- *     array, 4 when its larger tile saves a global level over 2, else 2.  A thread holds its
- *     leaves as leaf, ..., leaf, leaf-1 keys, so the first merge tile holds
- *     (leaves * leaf - 1) * threads keys.
- *   "blocksort_threads": 512 or 1024: shape 0 or 1.
- *   "merge_kernel": 1 (default) tiled merge levels in the "merge_tile" shape,
- *     odd outputs per thread (used for keys when both buffers are 16-byte
- *     aligned and n % 4 == 0), 0 staged-load serial merges.
- *   "merge_tile": shape of the tiled keys level: 9 (default) 128 threads x
- *     31 keys with exact per-thread windows, the tile moved in and out by
- *     bulk copies (copy engine); 8 the same with 96 x 31, 10 with 192 x 31;
- *     the cp.async-staged forms 5 96 x 31, 1 64 x 31, 2 128 x 31, 3 64 x 63,
- *     4 128 x 23, 6 192 x 31, 7 256 x 31; 0 256 x 15 with two windows.
+ *   "blocksort_shape": keys block-sort shape, 2: 256 threads, 4: 288 threads,
+ *     -1 (default): per array, 4 when its larger tile saves a global level
+ *     over 2, else 2.  A thread holds four leaves of leaf, leaf, leaf and
+ *     leaf-1 keys, so a tile holds (4 * leaf - 1) * threads keys.
  *   "merge_fanin": 4 (default) the tiled keys levels merge four runs per
  *     pass: a four-way merge-path split per output tile, then two stages of
  *     binary merges in shared memory, one read and one write of every key for
  *     two of Algorithm 1's merge levels (a binary level first when the number
  *     of levels is odd); 2 binary levels only.
- *   "merge_samples": 1 (default) the tiled keys levels' partition searches
- *     start on every 32nd key of the level's input, written by the pass
- *     before; 0 plain searches in the keys.
- *   "pairs_blocksort": pair block-sort shape, 0 (default) 256 threads x 4
- *     leaves, 1: 512 x 2, 2: 512 x 4, 3: 288 x 4.
- *   "pairs_merge": tiled pair levels (16-byte aligned keys and values,
- *     n % 4 == 0) with 3 (default) 128 threads x 31 pairs moved in and out
- *     by bulk copies, 1 the same staged by cp.async, 2 96 x 31 staged by
- *     cp.async, all with sampled partition searches; 0 staged-load serial
- *     merges.
- *   "blocksort_bulk": keys block sort of the merge path with 1 (default)
- *     each full tile moved in and out by one bulk copy when the array is
- *     16-byte aligned, 0 tiles staged by the threads.
- *   "segsort_bulk": batched form (hs_segsort_i32, the server) with 1
- *     (default) the tiles and merge chunks of segments longer than one warp
- *     tile moved in and out of shared memory by bulk copies of their 16-byte
- *     aligned interiors (at most three keys at each end by plain loads and
- *     stores); 0 staged by the threads.
- *   "pairs_blocksort_bulk": pair block sort with 1 (default) each full tile's
- *     keys and values moved in and out by bulk copies when all four arrays
- *     are 16-byte aligned, 0 tiles staged by the threads.
- *   "i64_merge": int64 sorts (hs_sort_i64) with 1 (default) tiles moved in
- *     and out by bulk copies: block-sort tiles when the arrays are 16-byte
- *     aligned, merge-level tiles when they are and n is even; 0 block-sort
- *     tiles staged by the threads and merge-level tiles by cp.async.
- *     Every option gives identical results.
- * Unknown names or values return HS_ERR_INVALID_ARG. */
+ * Tiled levels (bulk-copied tiles, sampled partition searches) serve 16-byte
+ * aligned buffers whose length is a multiple of 4 keys (of 2 for int64);
+ * other buffers take thread-staged generic forms.  Every option gives
+ * identical results.  Unknown names or values return HS_ERR_INVALID_ARG. */
 HS_API hs_status hs_set_option(const char *name, int64_t value);
 
 /* Keys per block-sort tile of the merge path for an n-key array and network

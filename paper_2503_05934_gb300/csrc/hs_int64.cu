@@ -197,7 +197,10 @@ struct TileMerge64 {
     static constexpr int SMEM_BYTES = REG * 8;
 };
 
-template <int NT, int EO, bool VEC>
+// Thread-staged form (any 8-byte alignment, any n): the tile's A and B keys
+// are loaded into shared memory by the threads and the outputs leave by
+// plain stores.
+template <int NT, int EO>
 __global__ void __launch_bounds__(NT)
     k_merge_tile64(const K64 *in, K64 *out, int64_t n, int64_t w, const int64_t *part, int tpg,
                    K64 *samp) {
@@ -215,28 +218,10 @@ __global__ void __launch_bounds__(NT)
     const int na = (int)(a1 - a0);
     const int tot = (int)(o1 - o0);
     const int nb = tot - na;
-    const K64 *A, *B;
-    if constexpr (VEC) {
-        // 16-byte buffers: stage the 16-byte covers of A and B by cp.async.
-        const int64_t ga = m.gs + a0, gb = m.gs + w + (o0 - a0);
-        const int64_t ca = ga & ~int64_t(1), cb = gb & ~int64_t(1);
-        const int nca = (int)(((ga + na + 1) & ~int64_t(1)) - ca) / 2;
-        const int ncb = (int)(((gb + nb + 1) & ~int64_t(1)) - cb) / 2;
-        for (int q = threadIdx.x; q < nca + ncb; q += NT) {
-            if (q < nca) cp_async16(s64 + 2 * q, in + ca + 2 * q);
-            else cp_async16(s64 + 2 * q, in + cb + 2 * (q - nca));
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        A = s64 + (int)(ga - ca);
-        B = s64 + 2 * nca + (int)(gb - cb);
-    } else {
-        const K64 *gA = in + m.gs + a0, *gB = in + m.gs + w + (o0 - a0);
-        for (int q = threadIdx.x; q < tot; q += NT) s64[q] = ld_stream(q < na ? gA + q : gB + (q - na));
-        __syncthreads();
-        A = s64;
-        B = s64 + na;
-    }
+    const K64 *gA = in + m.gs + a0, *gB = in + m.gs + w + (o0 - a0);
+    for (int q = threadIdx.x; q < tot; q += NT) s64[q] = ld_stream(q < na ? gA + q : gB + (q - na));
+    __syncthreads();
+    const K64 *A = s64, *B = s64 + na;
 
     const int diag = threadIdx.x * EO;
     const int lane = threadIdx.x & 31;
@@ -266,21 +251,9 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
     K64 *dst = out + m.gs + o0;
-    int i0 = 0;
-    if constexpr (VEC) {  // gs and o0 are even: 16-byte aligned output
-        const int n2 = tot >> 1;
-        for (int q = threadIdx.x; q < n2; q += NT) {
-            const int4 v = *reinterpret_cast<const int4 *>(s64 + 2 * q);
-            st_stream(reinterpret_cast<int4 *>(dst) + q, v);
-        }
-        i0 = 2 * n2;
-        if (samp)
-            for (int q = threadIdx.x * kSampleStride; q < tot; q += NT * kSampleStride)
-                samp[(m.gs + o0 + q) / kSampleStride] = s64[q];
-    }
-    for (int i = i0 + threadIdx.x; i < tot; i += NT) {
+    for (int i = threadIdx.x; i < tot; i += NT) {
         st_stream(dst + i, s64[i]);
-        if (!VEC && samp && i % kSampleStride == 0) samp[(m.gs + o0 + i) / kSampleStride] = s64[i];
+        if (samp && i % kSampleStride == 0) samp[(m.gs + o0 + i) / kSampleStride] = s64[i];
     }
 }
 
@@ -390,12 +363,9 @@ constexpr int M64_NT = 96, M64_EO = 31;      // merge level: 96 threads x 31 key
 
 int64_t tile64(int L, int64_t) { return (int64_t)B64_NT * (4 * L - 1); }
 
-// Tile copies (option "i64_merge"): 1 (default) the bulk-copy forms
-// (k_blocksort64_bulk for 16-byte aligned arrays, k_merge_tile64_bulk when
-// the buffers are 16-byte aligned and n is even), 0 the thread-staged block
-// sort and the cp.async-staged levels.
-static int g_i64_bulk = 1;
-void i64_set_bulk(int v) { g_i64_bulk = v; }
+// Tile copies: the bulk-copy forms (k_blocksort64_bulk for 16-byte aligned
+// arrays, k_merge_tile64_bulk when the buffers are 16-byte aligned and n is
+// even), else the thread-staged block sort and levels.
 
 size_t merge_workspace_bytes_i64(size_t n) {
     return ws_align(n * sizeof(K64)) + merge_ws_part_bytes(n) + ws_align((n / 32 + 8) * sizeof(K64));
@@ -408,7 +378,7 @@ static hs_status launch_blocksort64_t(const K64 *kin, K64 *kout, int64_t n, hs_n
     using C = BlockSort64<B64_NT, L>;
     const unsigned grid = (unsigned)((n + C::T - 1) / C::T);
     hs_status r;
-    if (vec && aligned(kout, 16) && g_i64_bulk) {
+    if (vec && aligned(kout, 16)) {
         unsigned *status = nullptr;
         if ((r = device_status(&status)) != HS_OK) return r;
         auto kern = k_blocksort64_bulk<B64_NT, L>;
@@ -465,8 +435,8 @@ hs_status merge_sort_i64(int64_t *d_keys, size_t n_, hs_netset s, void *d_ws, si
     using C = TileMerge64<M64_NT, M64_EO>;
     static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
     const bool vec = aligned(d_keys, 16) && (!kbuf || aligned(kbuf, 16)) && (n % 2) == 0;
-    const bool bulk = vec && g_i64_bulk;
-    auto kern = vec ? k_merge_tile64<M64_NT, M64_EO, true> : k_merge_tile64<M64_NT, M64_EO, false>;
+    const bool bulk = vec;
+    auto kern = k_merge_tile64<M64_NT, M64_EO>;
     auto kern_bulk = k_merge_tile64_bulk<M64_NT, M64_EO>;
     unsigned *status = nullptr;
     if (bulk && passes > 0 && (r = device_status(&status)) != HS_OK) return r;

@@ -102,21 +102,11 @@ size_t merge_workspace_bytes_i64(size_t n);
 int64_t tile64(int L, int64_t n);  // int64 block-sort tile for n keys
 hs_status merge_sort_i64(int64_t *d_keys, size_t n, hs_netset s, void *d_ws, size_t ws_bytes,
                          cudaStream_t st);
-void pairs_set_blocksort(int v);
-void pairs_set_merge(int v);
 
 // Tile of the keys block sort of an n-key array for leaf size L, and its
 // shape options.
 int64_t keys_tile(int L, int64_t n);
-void merge_set_blocksort_threads(int nt);
 void merge_set_blocksort_shape(int v);
-void merge_set_kernel(int k);
-void merge_set_tile(int v);
-void i64_set_bulk(int v);
-void merge_set_blocksort_bulk(int v);
-void pairs_set_blocksort_bulk(int v);
-void segsort_set_bulk(int v);
-void merge_set_samples(int v);
 void merge_set_fanin(int v);
 
 // Block sort of [0, n) in tiles of keys_tile(L) keys (the merge path's first pass;

@@ -13,27 +13,16 @@ namespace hs {
 
 size_t merge_workspace_bytes(size_t n, int with_values) { return merge_workspace_size(n, with_values); }
 
-// Keys block sort: block_sort_tile3 with two leaves (L, L-1) or four leaves
-// (L, L, L, L-1) per thread.  Shapes (option "blocksort_shape"):
-//   0: 512 threads x 2 leaves   1: 1024 x 2   2: 256 x 4   3: 512 x 4
-//   4: 288 x 4 (tiles of 8928 keys for the {6,7,8} set)   5: 576 x 4
+// Keys block sort: four leaves (L, L, L, L-1 keys) per thread, in one of two
+// shapes (option "blocksort_shape"):
+//   2: 256 threads (tiles of 256 * (4L - 1) keys: 7936 for the {6,7,8} set)
+//   4: 288 threads (8928 keys for the {6,7,8} set)
 //  -1 (default): per n, shape 4 when its larger tile needs fewer global
 //      levels than shape 2's (e.g. every power of two from 2^14 up), else 2.
 static int g_bs_shape = -1;
 
-static int shape_threads(int shape) {
-    switch (shape) {
-        case 1: return 1024;
-        case 2: return 256;
-        case 4: return 288;
-        case 5: return 576;
-        default: return 512;
-    }
-}
-static int shape_leaves(int shape) { return shape >= 2 ? 4 : 2; }
-static int64_t shape_tile(int shape, int L) {
-    return (int64_t)shape_threads(shape) * (shape_leaves(shape) * L - 1);
-}
+static int shape_threads(int shape) { return shape == 4 ? 288 : 256; }
+static int64_t shape_tile(int shape, int L) { return (int64_t)shape_threads(shape) * (4 * L - 1); }
 static int global_levels(int64_t n, int64_t tile) {
     int p = 0;
     for (int64_t w = tile; w < n; w *= 2) ++p;
@@ -46,47 +35,43 @@ static int shape_for(int64_t n, int L) {
 
 int64_t keys_tile(int L, int64_t n) { return shape_tile(shape_for(n, L), L); }
 
-void merge_set_blocksort_threads(int nt) { g_bs_shape = (nt == 1024) ? 1 : 0; }
 void merge_set_blocksort_shape(int v) { g_bs_shape = v; }
 
-// Option "blocksort_bulk": 1 (default) 16-byte aligned arrays use the
-// bulk-copy form (k_blocksort3_bulk), 0 the thread-staged form.
-static int g_bs_bulk = 1;
-void merge_set_blocksort_bulk(int v) { g_bs_bulk = v; }
-
-template <int NT, int L, int LEAVES>
+// 16-byte aligned arrays (vec) use the bulk-copy form (k_blocksort3_bulk:
+// each full tile in and out by one bulk copy); others the thread-staged form.
+template <int NT, int L>
 static hs_status launch_blocksort_t(const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
                                     int vec, int32_t *samp, cudaStream_t st) {
-    using C = BlockSort3<NT, L, LEAVES>;
+    using C = BlockSort3<NT, L, 4>;
     const int64_t grid = (n + C::T - 1) / C::T;
     hs_status r;
-    if (vec && g_bs_bulk) {
+    if (vec) {
         unsigned *status = nullptr;
         if ((r = device_status(&status)) != HS_OK) return r;
-        auto kern = k_blocksort3_bulk<NT, L, LEAVES>;
+        auto kern = k_blocksort3_bulk<NT, L, 4>;
         if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
         LaunchToken t = launch_begin(K_BLOCKSORT_KEYS, st);
         kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, samp, status);
         return launch_end(t);
     }
-    auto kern = k_blocksort3<NT, L, LEAVES>;
+    auto kern = k_blocksort3<NT, L, 4>;
     if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
     LaunchToken t = launch_begin(K_BLOCKSORT_KEYS, st);
     kern<<<(unsigned)grid, NT, C::SMEM_BYTES, st>>>(kin, kout, n, s, vec, samp);
     return launch_end(t);
 }
 
-template <int NT, int LEAVES>
+template <int NT>
 static hs_status launch_blocksort_nt(int L, const int32_t *kin, int32_t *kout, int64_t n,
                                      hs_netset s, int vec, int32_t *samp, cudaStream_t st) {
     switch (L) {
-        case 1: return launch_blocksort_t<NT, 1, LEAVES>(kin, kout, n, s, vec, samp, st);
-        case 3: return launch_blocksort_t<NT, 3, LEAVES>(kin, kout, n, s, vec, samp, st);
-        case 4: return launch_blocksort_t<NT, 4, LEAVES>(kin, kout, n, s, vec, samp, st);
-        case 5: return launch_blocksort_t<NT, 5, LEAVES>(kin, kout, n, s, vec, samp, st);
-        case 6: return launch_blocksort_t<NT, 6, LEAVES>(kin, kout, n, s, vec, samp, st);
-        case 7: return launch_blocksort_t<NT, 7, LEAVES>(kin, kout, n, s, vec, samp, st);
-        case 8: return launch_blocksort_t<NT, 8, LEAVES>(kin, kout, n, s, vec, samp, st);
+        case 1: return launch_blocksort_t<NT, 1>(kin, kout, n, s, vec, samp, st);
+        case 3: return launch_blocksort_t<NT, 3>(kin, kout, n, s, vec, samp, st);
+        case 4: return launch_blocksort_t<NT, 4>(kin, kout, n, s, vec, samp, st);
+        case 5: return launch_blocksort_t<NT, 5>(kin, kout, n, s, vec, samp, st);
+        case 6: return launch_blocksort_t<NT, 6>(kin, kout, n, s, vec, samp, st);
+        case 7: return launch_blocksort_t<NT, 7>(kin, kout, n, s, vec, samp, st);
+        case 8: return launch_blocksort_t<NT, 8>(kin, kout, n, s, vec, samp, st);
     }
     return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
 }
@@ -94,14 +79,8 @@ static hs_status launch_blocksort_nt(int L, const int32_t *kin, int32_t *kout, i
 static hs_status blocksort_launch_shape(int shape, int L, const int32_t *kin, int32_t *kout,
                                         int64_t n, hs_netset s, int vec, cudaStream_t st,
                                         int32_t *samp) {
-    switch (shape) {
-        case 1: return launch_blocksort_nt<1024, 2>(L, kin, kout, n, s, vec, samp, st);
-        case 2: return launch_blocksort_nt<256, 4>(L, kin, kout, n, s, vec, samp, st);
-        case 3: return launch_blocksort_nt<512, 4>(L, kin, kout, n, s, vec, samp, st);
-        case 4: return launch_blocksort_nt<288, 4>(L, kin, kout, n, s, vec, samp, st);
-        case 5: return launch_blocksort_nt<576, 4>(L, kin, kout, n, s, vec, samp, st);
-        default: return launch_blocksort_nt<512, 2>(L, kin, kout, n, s, vec, samp, st);
-    }
+    if (shape == 4) return launch_blocksort_nt<288>(L, kin, kout, n, s, vec, samp, st);
+    return launch_blocksort_nt<256>(L, kin, kout, n, s, vec, samp, st);
 }
 
 hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, hs_netset s,
@@ -109,27 +88,17 @@ hs_status blocksort_launch(int L, const int32_t *kin, int32_t *kout, int64_t n, 
     return blocksort_launch_shape(shape_for(n, L), L, kin, kout, n, s, vec, st, samp);
 }
 
-// Global levels: the tiled kernel (option "merge_kernel" 1, the default) for
-// 16-byte aligned buffers with n % 4 == 0, in the shape of option
-// "merge_tile"; otherwise, or with option 0, the generic serial-merge pass.
-static int g_merge_kernel = 1;
-static int g_merge_tile = kDefaultMergeTile;
-// Sampled partition searches (option "merge_samples", 1 by default): every
-// pass also writes each 32nd key of its output for the next partition.
-static int g_merge_samples = 1;
-
-void merge_set_kernel(int k) { g_merge_kernel = k; }
-void merge_set_tile(int v) { g_merge_tile = v; }
-void merge_set_samples(int v) { g_merge_samples = v; }
-
+// Global levels: the tiled kernels (bulk-copy tiles, sampled partition
+// searches) for 16-byte aligned buffers with n % 4 == 0; otherwise the
+// generic serial-merge pass, which takes any 4-byte alignment.
 constexpr int MG_NT = 256, MG_E = 16;  // generic keys level
 
-static bool tiled_levels(int64_t n, int vec) { return vec && g_merge_kernel == 1 && (n % 4) == 0; }
+static bool tiled_levels(int64_t n, int vec) { return vec && (n % 4) == 0; }
 
 static hs_status launch_keys_level(const int32_t *kin, int32_t *kout, int64_t n, int64_t w,
                                    int64_t *part, int32_t *samp, int vec, cudaStream_t st) {
     if (tiled_levels(n, vec))
-        return launch_keys_tile_level(g_merge_tile, kin, kout, n, w, part, samp, st);
+        return launch_keys_tile_level(kin, kout, n, w, part, samp, st);
     const LevelTiles lt = level_tiles(n, w, MG_NT * MG_E);
     LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
     k_merge_partition<<<(unsigned)((lt.nblocks + 255) / 256), 256, 0, st>>>(
@@ -152,11 +121,7 @@ static hs_status launch_keys_level(const int32_t *kin, int32_t *kout, int64_t n,
 static int g_merge_fanin = 4;
 void merge_set_fanin(int v) { g_merge_fanin = v; }
 
-// Four-way tile: 128 threads x 31 keys, 3936 keys per tile.  With 192 or
-// 256 threads (5920 / 7904 keys) the partitions shrink in number but the
-// merge slows more: 4.26 / 4.36 ms of four-way levels per 2^28 sort against
-// 4.02 ms.
-constexpr int M4_NT = 128, M4_EO = 31;
+constexpr int M4_NT = kMerge4Threads, M4_EO = kMerge4Keys;
 
 // One four-way keys level: its partition (four splits per tile boundary,
 // part_cap int64 entries available) and its merge.
@@ -242,9 +207,7 @@ static MergeScratch carve_merge_workspace(void *d_ws, size_t n) {
     MergeScratch m;
     m.kbuf = reinterpret_cast<int32_t *>(p);
     m.part = reinterpret_cast<int64_t *>(p + merge_ws_keys_bytes(n));
-    m.samp = g_merge_samples
-                 ? reinterpret_cast<int32_t *>(p + merge_ws_keys_bytes(n) + merge_ws_part_bytes(n))
-                 : nullptr;
+    m.samp = reinterpret_cast<int32_t *>(p + merge_ws_keys_bytes(n) + merge_ws_part_bytes(n));
     return m;
 }
 

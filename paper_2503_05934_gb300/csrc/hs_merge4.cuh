@@ -376,10 +376,10 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
-// Partition entries (int64) a four-way level over n keys needs, with its
-// tiles of at least `to` keys over groups of at least `span` keys.
-HS_HD int64_t merge4_part_entries(int64_t n, int64_t span, int64_t to) {
-    return 4 * (level_tiles_span(n, span, to).nblocks + 1);
-}
+// The launch shape of the four-way tile: 128 threads x 31 keys, 3936 keys
+// per tile.  With 192 or 256 threads (5920 / 7904 keys) the partitions shrink
+// in number but the merge slows more: 4.26 / 4.36 ms of four-way levels per
+// 2^28 sort against 4.02 ms.
+constexpr int kMerge4Threads = 128, kMerge4Keys = 31;
 
 }  // namespace hs

@@ -12,12 +12,13 @@ namespace hs {
 
 // ---------------------------------------------------------------------------
 // Tiled pairs level (16-byte aligned key and value buffers, n % 4 == 0).  One
-// CTA per output tile of TO = NT*EO pairs: the tile's A and B key and value
-// ranges are staged by 16-byte asynchronous copies of their aligned covers;
-// each thread finds its merge-path split, takes its end split from the next
-// lane, and merges exactly its own outputs serially (stable: A's element on
-// ties), picking each value by the same decision; the outputs then leave
-// through shared memory as 16-byte streaming stores.
+// CTA per output tile of TO = NT*EO pairs: one thread issues the four cover
+// copies (keys and values of A and B, cp.async.bulk, completion counted on an
+// mbarrier); each thread finds its merge-path split, takes its end split from
+// the next lane, and merges exactly its own outputs serially (stable: A's
+// element on ties), picking each value by the same decision; once the tile
+// is merged, one bulk store each of the output keys and values leaves, and
+// each thread writes the samples among its own outputs from registers.
 template <int NT, int EO>
 struct TileMergePairs {
     static constexpr int EOUT = EO;
@@ -26,100 +27,6 @@ struct TileMergePairs {
     static constexpr int SMEM_BYTES = 2 * REG * 4;  // keys, values
 };
 
-template <int NT, int EO>
-__global__ void __launch_bounds__(NT)
-    k_merge_tile_pairs(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
-                       int64_t n, int64_t w, const int64_t *part, int tpg, int32_t *samp) {
-    using C = TileMergePairs<NT, EO>;
-    constexpr int TO = C::TO;
-    extern __shared__ __align__(16) int32_t smem[];
-    int32_t *sK = smem, *sV = smem + C::REG;
-    const int64_t g = blockIdx.x / tpg;
-    const int t = blockIdx.x - (int)(g * tpg);
-    const MergeGeom m = merge_geom(g, n, w);
-    const int64_t glen = m.alen + m.blen;
-    const int64_t o0 = (int64_t)t * TO;
-    const int64_t o1 = (o0 + TO) < glen ? (o0 + TO) : glen;
-    const int64_t a0 = part[blockIdx.x];
-    const int64_t a1 = (o1 == glen) ? m.alen : part[blockIdx.x + 1];
-    const int na = (int)(a1 - a0);
-    const int tot = (int)(o1 - o0);
-    const int nb = tot - na;
-    const int64_t ga = m.gs + a0, gb = m.gs + w + (o0 - a0);
-    const int64_t ca = ga & ~int64_t(3), cb = gb & ~int64_t(3);
-    const int nca = (int)(((ga + na + 3) & ~int64_t(3)) - ca) / 4;
-    const int ncb = (int)(((gb + nb + 3) & ~int64_t(3)) - cb) / 4;
-    for (int q = threadIdx.x; q < nca + ncb; q += NT) {
-        const int64_t src = q < nca ? ca + 4 * q : cb + 4 * (q - nca);
-        cp_async16(sK + 4 * q, kin + src);
-        cp_async16(sV + 4 * q, vin + src);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    const int offA = (int)(ga - ca), offB = 4 * nca + (int)(gb - cb);
-    const int32_t *A = sK + offA, *B = sK + offB;
-    const int32_t *VA = sV + offA, *VB = sV + offB;
-
-    const int diag = threadIdx.x * EO;
-    const int lane = threadIdx.x & 31;
-    const int dcl = diag < tot ? diag : tot;
-    int lo = dcl > nb ? dcl - nb : 0, hi = dcl < na ? dcl : na;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (A[mid] <= B[dcl - 1 - mid]) lo = mid + 1;
-        else hi = mid;
-    }
-    __shared__ int wsplit[NT / 32 + 1];
-    int end = __shfl_down_sync(0xffffffffu, lo, 1);
-    if (lane == 0) wsplit[threadIdx.x >> 5] = lo;
-    if (threadIdx.x == 0) wsplit[NT / 32] = na;
-    __syncthreads();
-    const int dend = (diag + EO) < tot ? (diag + EO) : tot;
-    if (lane == 31) end = wsplit[(threadIdx.x >> 5) + 1];
-    if (dend == tot) end = na;
-    const int cnt = dend - dcl;
-
-    // Serial stable merge of A[lo, end) and B[dcl - lo, dcl - lo + cnt - (end - lo)).
-    // A read at ia == end or ib == eb lands inside the covers (each run is
-    // followed by at least one staged word), and its key is never taken.
-    int32_t ok[EO], ov[EO];
-    {
-        int ia = lo, ib = dcl - lo;
-        const int eb = ib + cnt - (end - lo);
-        int32_t ka = A[ia], kb = B[ib];
-#pragma unroll
-        for (int k = 0; k < EO; ++k) {
-            const bool take_b = (ib < eb) && ((ia >= end) || (kb < ka));
-            ok[k] = take_b ? kb : ka;
-            ov[k] = take_b ? VB[ib] : VA[ia];
-            ib += take_b;
-            ia += !take_b;
-            const int32_t nx = take_b ? B[ib] : A[ia];
-            kb = take_b ? nx : kb;
-            ka = take_b ? ka : nx;
-        }
-    }
-    __syncthreads();
-    if (cnt > 0) {
-#pragma unroll
-        for (int k = 0; k < EO; ++k) {
-            if (k < cnt) {
-                sK[diag + k] = ok[k];
-                sV[diag + k] = ov[k];
-            }
-        }
-    }
-    __syncthreads();
-    int32_t *dk = kout + m.gs + o0, *dv = vout + m.gs + o0;  // 16-byte aligned
-    store_tile_out<NT>(dk, sK, tot, samp, m.gs + o0);
-    store_tile_out<NT>(dv, sV, tot, nullptr, 0);
-}
-
-// Bulk-copy form of the tiled pairs level: one thread issues the four cover
-// copies (keys and values of A and B, cp.async.bulk, completion counted on an
-// mbarrier) and, once the tile is merged, one bulk store each of the output
-// keys and values; each thread writes the samples among its own outputs from
-// registers.  Same merge and results as k_merge_tile_pairs.
 template <int NT, int EO>
 __global__ void __launch_bounds__(NT)
     k_merge_tile_pairs_bulk(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
@@ -197,7 +104,9 @@ __global__ void __launch_bounds__(NT)
     if (dend == tot) end = na;
     const int cnt = dend - dcl;
 
-    // Serial stable merge, as in k_merge_tile_pairs.
+    // Serial stable merge of A[lo, end) and B[dcl - lo, dcl - lo + cnt - (end - lo)).
+    // A read at ia == end or ib == eb lands inside the covers (each run is
+    // followed by at least one staged word), and its key is never taken.
     int32_t ok_[EO], ov[EO];
     {
         int ia = lo, ib = dcl - lo;
@@ -245,34 +154,12 @@ __global__ void __launch_bounds__(NT)
 // ---------------------------------------------------------------------------
 // Planner.
 
-// Block sort shape (option "pairs_blocksort"): 0 = 256 threads x 4 leaves
-// (the default; tiles of 256*(4L - 1) pairs), 1 = 512 x 2 leaves, 2 = 512 x 4
-// leaves (one CTA per SM), 3 = 288 x 4 leaves (tiles of at least 8192 pairs
-// for the {6,7,8} set).
-static int g_pairs_bs = 0;
-// Merge level (option "pairs_merge"): 3 = tiled, 128 threads x 31 pairs moved
-// by bulk copies (the default when aligned), 1 = tiled, 128 x 31 staged by
-// cp.async, 2 = the same with 96 x 31, 0 = the generic serial-merge pass.
-// The tiled levels use sampled partition searches.
-static int g_pairs_merge = 3;
+// Block sort: 256 threads x 4 leaves (tiles of 256 * (4L - 1) pairs).
+constexpr int PB_NT = 256;
+int64_t pairs_tile(int L) { return (int64_t)PB_NT * (4 * L - 1); }
 
-void pairs_set_blocksort(int v) { g_pairs_bs = v; }
-void pairs_set_merge(int v) { g_pairs_merge = v; }
-
-int64_t pairs_tile(int L) {
-    switch (g_pairs_bs) {
-        case 1: return 512 * (2 * L - 1);
-        case 2: return 512 * (4 * L - 1);
-        case 3: return 288 * (4 * L - 1);
-        default: return 256 * (4 * L - 1);
-    }
-}
-
-// Option "pairs_blocksort_bulk": 1 (default) 16-byte aligned arrays use the
-// bulk-copy form (k_blocksort_pairs_bulk), 0 the thread-staged form.
-static int g_pairs_bs_bulk = 1;
-void pairs_set_blocksort_bulk(int v) { g_pairs_bs_bulk = v; }
-
+// 16-byte aligned key and value arrays (vec) use the bulk-copy block sort
+// (k_blocksort_pairs_bulk), others the thread-staged one.
 template <int NT, int L, int LEAVES>
 static hs_status launch_pairs_blocksort_t(const int32_t *kin, int32_t *kout, const int32_t *vin,
                                           int32_t *vout, int64_t n, hs_netset s, int vec,
@@ -281,7 +168,7 @@ static hs_status launch_pairs_blocksort_t(const int32_t *kin, int32_t *kout, con
     const int64_t grid = (n + C::T - 1) / C::T;
     hs_status r;
     if constexpr (C::BULK_OK) {
-        if (vec && g_pairs_bs_bulk) {
+        if (vec) {
             unsigned *status = nullptr;
             if ((r = device_status(&status)) != HS_OK) return r;
             auto kern = k_blocksort_pairs_bulk<NT, L, LEAVES>;
@@ -316,11 +203,13 @@ static hs_status launch_pairs_blocksort_nt(int L, const int32_t *kin, int32_t *k
 
 constexpr int PG_NT = 256, PG_E = 8;  // generic level
 
-template <int NT, int EO, bool BULK>
+// Tiled pairs level: 128 threads x 31 pairs, sampled partition searches.
+constexpr int PM_NT = 128, PM_EO = 31;
+
 static hs_status launch_pairs_tile(const int32_t *kin, int32_t *kout, const int32_t *vin,
                                    int32_t *vout, int64_t n, int64_t w, int64_t *part,
                                    int32_t *samp, cudaStream_t st) {
-    using C = TileMergePairs<NT, EO>;
+    using C = TileMergePairs<PM_NT, PM_EO>;
     static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
     const LevelTiles lt = level_tiles(n, w, C::TO);
     LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
@@ -328,36 +217,22 @@ static hs_status launch_pairs_tile(const int32_t *kin, int32_t *kout, const int3
         kin, samp, n, w, C::TO, (int)lt.tpg, lt.nblocks, part);
     hs_status r = launch_end(t);
     if (r != HS_OK) return r;
-    if constexpr (BULK) {
-        unsigned *status = nullptr;
-        if ((r = device_status(&status)) != HS_OK) return r;
-        auto kern = k_merge_tile_pairs_bulk<NT, EO>;
-        if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
-        t = launch_begin(K_MERGE_PAIRS, st);
-        kern<<<(unsigned)lt.nblocks, NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, w, part,
-                                                              (int)lt.tpg, samp, status);
-        return launch_end(t);
-    }
-    auto kern = k_merge_tile_pairs<NT, EO>;
+    unsigned *status = nullptr;
+    if ((r = device_status(&status)) != HS_OK) return r;
+    auto kern = k_merge_tile_pairs_bulk<PM_NT, PM_EO>;
     if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
     t = launch_begin(K_MERGE_PAIRS, st);
-    kern<<<(unsigned)lt.nblocks, NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, w, part,
-                                                          (int)lt.tpg, samp);
+    kern<<<(unsigned)lt.nblocks, PM_NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, w, part,
+                                                             (int)lt.tpg, samp, status);
     return launch_end(t);
 }
 
-static bool pairs_tiled(int64_t n, int vec) { return vec && g_pairs_merge >= 1 && (n % 4) == 0; }
+static bool pairs_tiled(int64_t n, int vec) { return vec && (n % 4) == 0; }
 
 static hs_status launch_pairs_level(const int32_t *kin, int32_t *kout, const int32_t *vin,
                                     int32_t *vout, int64_t n, int64_t w, int64_t *part,
                                     int32_t *samp, int vec, cudaStream_t st) {
-    if (pairs_tiled(n, vec)) {
-        switch (g_pairs_merge) {
-            case 1: return launch_pairs_tile<128, 31, false>(kin, kout, vin, vout, n, w, part, samp, st);
-            case 2: return launch_pairs_tile<96, 31, false>(kin, kout, vin, vout, n, w, part, samp, st);
-            default: return launch_pairs_tile<128, 31, true>(kin, kout, vin, vout, n, w, part, samp, st);
-        }
-    }
+    if (pairs_tiled(n, vec)) return launch_pairs_tile(kin, kout, vin, vout, n, w, part, samp, st);
     const LevelTiles lt = level_tiles(n, w, PG_NT * PG_E);
     LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
     k_merge_partition<<<(unsigned)((lt.nblocks + 255) / 256), 256, 0, st>>>(
@@ -404,13 +279,7 @@ hs_status pairs_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, v
     int32_t *kalt = (kcur == d_keys) ? kbuf : d_keys;
     int32_t *valt = (vcur == d_vals) ? vbuf : d_vals;
 
-    hs_status r;
-    switch (g_pairs_bs) {
-        case 1: r = launch_pairs_blocksort_nt<512, 2>(L, d_keys, kcur, d_vals, vcur, n, s, vec, samp, st); break;
-        case 2: r = launch_pairs_blocksort_nt<512, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, samp, st); break;
-        case 3: r = launch_pairs_blocksort_nt<288, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, samp, st); break;
-        default: r = launch_pairs_blocksort_nt<256, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, samp, st);
-    }
+    hs_status r = launch_pairs_blocksort_nt<PB_NT, 4>(L, d_keys, kcur, d_vals, vcur, n, s, vec, samp, st);
     if (r != HS_OK) return r;
     for (int64_t w = T; w < n; w *= 2) {
         if ((r = launch_pairs_level(kcur, kalt, vcur, valt, n, w, part, samp, vec, st)) != HS_OK) return r;

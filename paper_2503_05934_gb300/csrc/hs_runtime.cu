@@ -394,76 +394,16 @@ hs_status hs_set_option(const char *name, int64_t value) {
         quick_set_two_way(value == 2 ? 1 : 0);
         return HS_OK;
     }
-    if (std::strcmp(name, "merge_kernel") == 0) {
-        if (value != 0 && value != 1)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_kernel must be 0 or 1");
-        merge_set_kernel((int)value);
-        return HS_OK;
-    }
-    if (std::strcmp(name, "merge_tile") == 0) {
-        if (value < 0 || value > 10)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_tile must be 0..10");
-        merge_set_tile((int)value);
-        return HS_OK;
-    }
     if (std::strcmp(name, "blocksort_shape") == 0) {
-        if (value < -1 || value > 5)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_shape must be -1..5");
+        if (value != -1 && value != 2 && value != 4)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_shape must be -1, 2 or 4");
         merge_set_blocksort_shape((int)value);
-        return HS_OK;
-    }
-    if (std::strcmp(name, "blocksort_threads") == 0) {
-        if (value != 512 && value != 1024)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_threads must be 512 or 1024");
-        merge_set_blocksort_threads((int)value);
         return HS_OK;
     }
     if (std::strcmp(name, "merge_fanin") == 0) {
         if (value != 2 && value != 4)
             return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_fanin must be 2 or 4");
         merge_set_fanin((int)value);
-        return HS_OK;
-    }
-    if (std::strcmp(name, "merge_samples") == 0) {
-        if (value != 0 && value != 1)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_samples must be 0 or 1");
-        merge_set_samples((int)value);
-        return HS_OK;
-    }
-    if (std::strcmp(name, "pairs_blocksort") == 0) {
-        if (value < 0 || value > 3)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: pairs_blocksort must be 0..3");
-        pairs_set_blocksort((int)value);
-        return HS_OK;
-    }
-    if (std::strcmp(name, "blocksort_bulk") == 0) {
-        if (value != 0 && value != 1)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: blocksort_bulk must be 0 or 1");
-        merge_set_blocksort_bulk((int)value);
-        return HS_OK;
-    }
-    if (std::strcmp(name, "segsort_bulk") == 0) {
-        if (value != 0 && value != 1)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: segsort_bulk must be 0 or 1");
-        segsort_set_bulk((int)value);
-        return HS_OK;
-    }
-    if (std::strcmp(name, "pairs_blocksort_bulk") == 0) {
-        if (value != 0 && value != 1)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: pairs_blocksort_bulk must be 0 or 1");
-        pairs_set_blocksort_bulk((int)value);
-        return HS_OK;
-    }
-    if (std::strcmp(name, "i64_merge") == 0) {
-        if (value != 0 && value != 1)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: i64_merge must be 0 or 1");
-        i64_set_bulk((int)value);
-        return HS_OK;
-    }
-    if (std::strcmp(name, "pairs_merge") == 0) {
-        if (value < 0 || value > 3)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: pairs_merge must be 0..3");
-        pairs_set_merge((int)value);
         return HS_OK;
     }
     return fail(HS_ERR_INVALID_ARG, std::string("hs_set_option: unknown option ") + name);

@@ -1,7 +1,7 @@
 // Batched form: many independent arrays sorted by one persistent launch.
 //
 // Every array ("segment") is sorted by a single CTA, as Algorithm 1 would sort
-// it: network leaves and shared-memory merge levels (block_sort_tile3) for a
+// it: network leaves and shared-memory merge levels (the block sort's) for a
 // segment of at most one tile; for a longer segment, tile-sized pieces first,
 // then CTA-local merge levels through the segment's scratch area, which stays
 // in L2 at the sizes this form targets (up to 64K keys).  Persistent CTAs take
@@ -26,8 +26,6 @@
 namespace hs {
 
 constexpr int SPLIT_CAP = 256;  // merge-level chunk boundaries searched per batch
-
-HS_DEV bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Bulk-copy staging of the batched form.  Segments start anywhere, so a run
 // g[0, cnt) of keys is placed at s[0, cnt) with s congruent to g modulo 16
@@ -132,97 +130,13 @@ HS_DEV int64_t warp_merge_path(const int32_t *A, const int32_t *B, int64_t diag,
 
 // One merge level over a single segment by one CTA: runs of w in src are
 // merged into runs of 2w in dst.  Output chunks of T keys: their merge-path
-// splits are found by one warp per chunk boundary; each chunk is then staged
-// in shared memory, each thread merges exactly its own EO outputs (exact
-// window, end split from the next lane), and the outputs leave through shared
-// memory as coalesced stores.
-template <int NT, int L, int LV>
-HS_DEV void cta_merge_level(const int32_t *src, int32_t *dst, int64_t n, int64_t w, int32_t *s,
-                            int64_t *split) {
-    using C = BlockSort3<NT, L, LV>;
-    constexpr int T = C::T, EO = C::EO, P = C::P;
-    const int64_t span = 2 * w;
-    const int64_t ngroups = (n + span - 1) / span;
-    const int64_t tpg = (span + T - 1) / T;
-    const int64_t last = n - (ngroups - 1) * span;
-    const int64_t nchunks = (ngroups - 1) * tpg + (last + T - 1) / T;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int *wsplit = s + C::T + C::P + 32;
-    for (int64_t c0 = 0; c0 < nchunks; c0 += SPLIT_CAP) {
-        const int64_t c1 = std::min<int64_t>(nchunks, c0 + SPLIT_CAP);
-        // Splits of boundaries c0 .. c1 (c1 may open the next batch).
-        for (int64_t c = c0 + warp; c <= c1 && c < nchunks; c += NT / 32) {
-            const int64_t g = c / tpg, t = c - g * tpg;
-            const MergeGeom m = merge_geom(g, n, w);
-            int64_t diag = t * T;
-            if (diag > m.alen + m.blen) diag = m.alen + m.blen;
-            const int64_t lo = diag > m.blen ? diag - m.blen : 0;
-            const int64_t hi = diag < m.alen ? diag : m.alen;
-            const int64_t r = warp_merge_path(src + m.gs, src + m.gs + w, diag, lo, hi, lane);
-            if (lane == 0) split[c - c0] = r;
-        }
-        __syncthreads();
-        for (int64_t c = c0; c < c1; ++c) {
-            const int64_t g = c / tpg, t = c - g * tpg;
-            const MergeGeom m = merge_geom(g, n, w);
-            const int64_t glen = m.alen + m.blen;
-            const int64_t o0 = t * T;
-            const int64_t o1 = std::min<int64_t>(o0 + T, glen);
-            const int64_t a0 = split[c - c0];
-            const int64_t a1 = (o1 == glen) ? m.alen : split[c + 1 - c0];
-            const int na = (int)(a1 - a0);
-            const int tot = (int)(o1 - o0);
-            const int nb = tot - na;
-            const int32_t *gA = src + m.gs + a0, *gB = src + m.gs + w + (o0 - a0);
-            for (int i = threadIdx.x; i < tot; i += NT) cp_async4(s + i, i < na ? gA + i : gB + (i - na));
-            cp_async_wait_all();
-            __syncthreads();
-            const int32_t *A = s, *B = s + na;
-            const int diag = threadIdx.x * EO;
-            const int dcl = diag < tot ? diag : tot;
-            int lo = dcl > nb ? dcl - nb : 0, hi = dcl < na ? dcl : na;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (A[mid] <= B[dcl - 1 - mid]) lo = mid + 1;
-                else hi = mid;
-            }
-            int end = __shfl_down_sync(0xffffffffu, lo, 1);
-            if (lane == 0) wsplit[warp] = lo;
-            if (threadIdx.x == 0) wsplit[NT / 32] = na;
-            __syncthreads();
-            const int dend = (diag + EO) < tot ? (diag + EO) : tot;
-            if (lane == 31) end = wsplit[warp + 1];
-            if (dend == tot) end = na;
-            const int cnt = dend - dcl;
-            int32_t x[P];
-            if (cnt > 0) exact_window_merge<EO, P>(A, lo, B, dcl - lo, end - lo, cnt, x);
-            __syncthreads();
-            if (cnt > 0) {
-#pragma unroll
-                for (int k = 0; k < EO; ++k)
-                    if (k < cnt) s[diag + k] = x[k];
-            }
-            __syncthreads();
-            int32_t *out = dst + m.gs + o0;
-            // Plain (cached) stores: the next level reads these keys back from L2.
-            int start = 0;
-            if (aligned16(out)) {
-                for (int q = threadIdx.x; q < (tot >> 2); q += NT)
-                    reinterpret_cast<int4 *>(out)[q] = *reinterpret_cast<const int4 *>(s + 4 * q);
-                start = tot & ~3;
-            }
-            for (int i = start + threadIdx.x; i < tot; i += NT) out[i] = s[i];
-            __syncthreads();
-        }
-    }
-}
-
-// cta_merge_level with bulk-copy staging: each chunk's A and B ranges are
-// placed congruent to their global addresses in two regions of the buffer
-// (A first, B from the next 16-byte boundary after it), and the merged chunk
-// leaves from a copy congruent to its destination (src and dst need not be
-// congruent to each other).  False if a copy wait gave up or the chunk's
-// split sizes do not fit the buffer.
+// splits are found by one warp per chunk boundary; each chunk's A and B
+// ranges are then placed congruent to their global addresses in two regions
+// of the buffer (A first, B from the next 16-byte boundary after it), each
+// thread merges exactly its own EO outputs (exact window, end split from the
+// next lane), and the merged chunk leaves from a copy congruent to its
+// destination (src and dst need not be congruent to each other).  False if a
+// copy wait gave up or the chunk's split sizes do not fit the buffer.
 template <int NT, int L, int LV>
 HS_DEV bool cta_merge_level_staged(const int32_t *src, int32_t *dst, int64_t n, int64_t w,
                                    int32_t *sbase, int64_t *split, Stager &sg) {
@@ -365,49 +279,30 @@ HS_DEV bool sort_tile_staged(int32_t *sbase, const int32_t *src, int32_t *dst, i
     return true;
 }
 
-// BULK: every tile and merge chunk moves by bulk copies (sg); otherwise the
-// threads stage them.  False (uniform across the CTA) if a copy wait gave up.
-template <int NT, int L, int LV, bool BULK>
+// Every tile and merge chunk moves by bulk copies of its 16-byte aligned
+// interior (sg).  False (uniform across the CTA) if a copy wait gave up.
+template <int NT, int L, int LV>
 HS_DEV bool sort_segment(const SegDesc &d, uint32_t netset, int32_t *s, int64_t *split,
                          Stager &sg) {
     using C = BlockSort3<NT, L, LV>;
     constexpr int T = C::T;
     const int64_t n = d.n;
     if (n <= 1) return true;
-    if (n <= T) {
-        if constexpr (BULK) return sort_tile_staged<NT, L, LV, true>(s, d.keys, d.keys, (int)n, netset, sg);
-        block_sort_tile3<NT, L, LV, true>(d.keys, d.keys, (int)n, netset, aligned16(d.keys), s);
-        return true;
-    }
+    if (n <= T) return sort_tile_staged<NT, L, LV, true>(s, d.keys, d.keys, (int)n, netset, sg);
     int levels = 0;
     for (int64_t w = T; w < n; w *= 2) ++levels;
     // Ping-pong so that the last level lands in d.keys.
     int32_t *cur = (levels % 2 == 0) ? d.keys : d.scratch;
     int32_t *alt = (levels % 2 == 0) ? d.scratch : d.keys;
-    if constexpr (BULK) {
-        for (int64_t base = 0; base < n; base += T) {
-            const int cnt = (int)std::min<int64_t>(T, n - base);
-            if (!sort_tile_staged<NT, L, LV, false>(s, d.keys + base, cur + base, cnt, netset, sg))
-                return false;
-        }
-        // The merge levels read the tiles back.
-        stores_done();
-        for (int64_t w = T; w < n; w *= 2) {
-            if (!cta_merge_level_staged<NT, L, LV>(cur, alt, n, w, s, split, sg)) return false;
-            int32_t *tmp = cur;
-            cur = alt;
-            alt = tmp;
-        }
-        return true;
-    }
-    const bool vec = aligned16(d.keys) && aligned16(cur);
     for (int64_t base = 0; base < n; base += T) {
         const int cnt = (int)std::min<int64_t>(T, n - base);
-        block_sort_tile3<NT, L, LV>(d.keys + base, cur + base, cnt, netset, vec, s);
-        __syncthreads();
+        if (!sort_tile_staged<NT, L, LV, false>(s, d.keys + base, cur + base, cnt, netset, sg))
+            return false;
     }
+    // The merge levels read the tiles back.
+    stores_done();
     for (int64_t w = T; w < n; w *= 2) {
-        cta_merge_level<NT, L, LV>(cur, alt, n, w, s, split);
+        if (!cta_merge_level_staged<NT, L, LV>(cur, alt, n, w, s, split, sg)) return false;
         int32_t *tmp = cur;
         cur = alt;
         alt = tmp;
@@ -462,7 +357,7 @@ constexpr int seg_smem_bytes() {
 // segments from the back of the array (cdesc[ndesc - 1 - j]) until both
 // lists are drained.  Large segments first also balances the load: the
 // short items fill the gaps at the end.
-template <int NT, int L, int LV, bool BULK>
+template <int NT, int L, int LV>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 2)
     k_seg_sort(const SegDesc *cdesc, int64_t ndesc, unsigned long long *ctrl, uint32_t netset,
                unsigned *status) {
@@ -470,15 +365,13 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 2)
     __shared__ int64_t s_split[SPLIT_CAP + 1];
     __shared__ unsigned long long s_item[2];
     __shared__ __align__(8) uint64_t s_bar;
-    Stager sg{&s_bar, 0u, BULK ? l2_evict_normal_policy() : 0ull, status};
-    if (BULK) {
-        // The congruent staging relies on a 16-byte aligned dynamic buffer.
-        if ((smem_addr(smem) & 15u) != 0) {
-            if (threadIdx.x == 0) atomicOr(status, kStatusMisaligned);
-            return;
-        }
-        if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    Stager sg{&s_bar, 0u, l2_evict_normal_policy(), status};
+    // The congruent staging relies on a 16-byte aligned dynamic buffer.
+    if ((smem_addr(smem) & 15u) != 0) {
+        if (threadIdx.x == 0) atomicOr(status, kStatusMisaligned);
+        return;
     }
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
     const unsigned long long nlarge = ctrl[2], nsmall = ctrl[3];
     if (threadIdx.x == 0) s_item[0] = atomicAdd(&ctrl[0], 1ull);
     __syncthreads();
@@ -491,7 +384,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 2)
         if (threadIdx.x == 0) next = atomicAdd(&ctrl[0], 1ull);
         const SegDesc d = cdesc[item];
         // A copy wait that gave up (status raised) ends this CTA's work.
-        if (!sort_segment<NT, L, LV, BULK>(d, netset, smem, s_split, sg)) return;
+        if (!sort_segment<NT, L, LV>(d, netset, smem, s_split, sg)) return;
         if (threadIdx.x == 0) s_item[it ^ 1] = next;
         __syncthreads();
     }
@@ -573,15 +466,10 @@ struct SegKernelInfo {
     int64_t small_max;  // segments of up to this many keys are sorted by one warp
 };
 
-// Option "segsort_bulk": 1 (default) large segments move tiles and merge
-// chunks by bulk copies (k_seg_sort<..., true>), 0 the threads stage them.
-static int g_seg_bulk = 1;
-void segsort_set_bulk(int v) { g_seg_bulk = v; }
-
 template <int NT, int L, int LV>
 static hs_status seg_kernel_info(SegKernelInfo *out) {
     constexpr int SMEM = seg_smem_bytes<NT, L, LV>();
-    auto kern = g_seg_bulk ? k_seg_sort<NT, L, LV, true> : k_seg_sort<NT, L, LV, false>;
+    auto kern = k_seg_sort<NT, L, LV>;
     hs_status r = ensure_smem((const void *)kern, SMEM);
     if (r != HS_OK) return r;
     int occ = 0;

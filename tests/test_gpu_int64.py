@@ -39,21 +39,19 @@ def test_int64_sizes_and_distributions(hs, netset):
             assert np.array_equal(gpu_sort64(hs, a, netset), oracle.merge_sort_i64(a, netset)), (n, dist)
 
 
-@pytest.mark.parametrize("form", [0, 1])
-def test_int64_merge_level_forms(hs, form):
-    """Both int64 merge-level forms (tiles staged by cp.async, or moved by
-    bulk copies) give the oracle's result: tile edges of the 2976-key merge
-    tile, odd multiples of the block-sort tile, few distinct keys."""
-    hs.hs_set_option("i64_merge", form)
-    try:
-        for n in [3 * 2976 + 2, 2 * 7936, 3 * 7936, 100_002, 1 << 20, (1 << 20) + 2]:
-            for dist in g.DISTS:
-                a = g.keys_i64(n, dist, 5000 + n + form)
-                assert np.array_equal(gpu_sort64(hs, a), oracle.merge_sort_i64(a, "6To8")), (n, dist)
-        few = (g.keys_i64(400_002, "random", 6) % 3).astype(np.int64)
+def test_int64_merge_level_forms(hs):
+    """Both int64 merge-level forms give the oracle's result: bulk-copied
+    tiles (16-byte aligned, n even) and thread-staged tiles (n odd), at tile
+    edges of the 2976-key merge tile, odd multiples of the block-sort tile,
+    and few distinct keys."""
+    for n in [3 * 2976 + 2, 3 * 2976 + 1, 2 * 7936, 3 * 7936 + 1, 100_002, 100_001, 1 << 20,
+              (1 << 20) + 3]:
+        for dist in g.DISTS:
+            a = g.keys_i64(n, dist, 5000 + n)
+            assert np.array_equal(gpu_sort64(hs, a), oracle.merge_sort_i64(a, "6To8")), (n, dist)
+    for n in (400_002, 400_001):
+        few = (g.keys_i64(n, "random", 6) % 3).astype(np.int64)
         assert np.array_equal(gpu_sort64(hs, few), oracle.merge_sort_i64(few, "6To8"))
-    finally:
-        hs.hs_set_option("i64_merge", 1)
 
 
 def test_int64_extremes_duplicates_and_unaligned(hs):

@@ -134,58 +134,27 @@ def test_pairs_unaligned(hs):
     assert np.array_equal(ko, ek) and np.array_equal(vo, ev)
 
 
-@pytest.mark.parametrize("bs", [0, 1, 2, 3])
-@pytest.mark.parametrize("merge", [0, 1, 2, 3])
-def test_pairs_options_keep_results(hs, bs, merge):
-    """Every pair block-sort shape and merge-level kernel gives the oracle's
-    stable order: sizes around the tiles (7936 / 7680 / 15872 / 8928 pairs
-    per block-sort tile, 3968 per merge tile), n % 4 != 0, an unaligned
-    start, few distinct keys (long equal runs across tiles) and arbitrary
-    values."""
-    hs.hs_set_option("pairs_blocksort", bs)
-    hs.hs_set_option("pairs_merge", merge)
-    try:
-        rng = np.random.default_rng(40 + 2 * bs + merge)
-        for n in [2, 7, 31, 3967, 3968, 3969, 7679, 7680, 7681, 7935, 7936, 7937, 8927, 8928,
-                  8929, 15_871, 15_872, 15_873, 61_441, 250_003, 1 << 20]:
-            for kinds in ["few", "wide"]:
-                if kinds == "few":
-                    k = rng.integers(0, 5, n).astype(np.int32)
-                else:
-                    k = rng.integers(-(1 << 31), 1 << 31, n, dtype=np.int64).astype(np.int32)
-                v = rng.integers(-(1 << 31), 1 << 31, n, dtype=np.int64).astype(np.int32)
-                ek, ev = oracle.merge_sort_pairs(k, v, "6To8")
-                for off in ([0, 3] if n < 100_000 else [0]):
-                    ko, vo = gpu_sort_pairs(hs, k, v, "6To8", offset=off)
-                    assert np.array_equal(ko, ek), (n, kinds, off)
-                    assert np.array_equal(vo, ev), (n, kinds, off)
-    finally:
-        hs.hs_set_option("pairs_blocksort", 0)
-        hs.hs_set_option("pairs_merge", 3)
-
-
-@pytest.mark.parametrize("bs", [0, 3])
-@pytest.mark.parametrize("bulk", [0, 1])
-def test_pairs_blocksort_copy_forms(hs, bs, bulk):
-    """The pair block sort with its tiles moved by bulk copies or staged by
-    the threads gives the oracle's stable order: whole tiles, partial last
-    tiles and single partial tiles, few distinct keys and arbitrary values."""
-    hs.hs_set_option("pairs_blocksort", bs)
-    hs.hs_set_option("pairs_blocksort_bulk", bulk)
-    try:
-        rng = np.random.default_rng(70 + 2 * bs + bulk)
-        for n in [7936, 7940, 8928, 8932, 2 * 7936, 3 * 8928, 100_004, 1 << 20]:
-            for kinds in ["few", "wide"]:
-                hi = 5 if kinds == "few" else 1 << 31
-                k = rng.integers(-hi if kinds == "wide" else 0, hi, n, dtype=np.int64).astype(np.int32)
-                v = rng.integers(-(1 << 31), 1 << 31, n, dtype=np.int64).astype(np.int32)
-                ek, ev = oracle.merge_sort_pairs(k, v, "6To8")
-                ko, vo = gpu_sort_pairs(hs, k, v, "6To8")
-                assert np.array_equal(ko, ek), (n, kinds)
-                assert np.array_equal(vo, ev), (n, kinds)
-    finally:
-        hs.hs_set_option("pairs_blocksort", 0)
-        hs.hs_set_option("pairs_blocksort_bulk", 1)
+def test_pairs_copy_forms_keep_results(hs):
+    """The pair sort's two forms give the oracle's stable order: bulk-copied
+    block-sort tiles and merge tiles (16-byte aligned keys and values,
+    n % 4 == 0) and thread-staged ones (an unaligned start or n % 4 != 0),
+    at sizes around the 7936-pair block-sort tile and the 3968-pair merge
+    tile, with few distinct keys (long equal runs across tiles) and
+    arbitrary values."""
+    rng = np.random.default_rng(40)
+    for n in [2, 7, 31, 3967, 3968, 3969, 7935, 7936, 7937, 7940, 15_871, 15_872, 15_873,
+              3 * 7936, 61_441, 250_003, 1 << 20]:
+        for kinds in ["few", "wide"]:
+            if kinds == "few":
+                k = rng.integers(0, 5, n).astype(np.int32)
+            else:
+                k = rng.integers(-(1 << 31), 1 << 31, n, dtype=np.int64).astype(np.int32)
+            v = rng.integers(-(1 << 31), 1 << 31, n, dtype=np.int64).astype(np.int32)
+            ek, ev = oracle.merge_sort_pairs(k, v, "6To8")
+            for off in ([0, 3] if n < 300_000 else [0]):
+                ko, vo = gpu_sort_pairs(hs, k, v, "6To8", offset=off)
+                assert np.array_equal(ko, ek), (n, kinds, off)
+                assert np.array_equal(vo, ev), (n, kinds, off)
 
 
 @pytest.mark.parametrize("netset", ["none", "3To5", "Odd", "3To4", "6To8", "3", "PowerOf2"])
@@ -335,45 +304,32 @@ def test_many_duplicates_and_runs(hs):
         assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), mod
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
-@pytest.mark.parametrize("samples", [0, 1])
-def test_merge_tile_shapes_and_samples(hs, tile, samples):
-    """Every tiled merge-level shape, with and without sampled partition
-    searches, on uniform keys, few distinct keys and presorted runs."""
-    hs.hs_set_option("merge_tile", tile)
-    hs.hs_set_option("merge_samples", samples)
-    try:
-        for n in [9000, 65_536, 250_000, 1 << 20]:
-            for kind in ["uniform", "few", "sorted"]:
-                a = g.random_i32(n, n + tile)
-                if kind == "few":
-                    a = (a % 3).astype(np.int32)
-                elif kind == "sorted":
-                    a = g.keys(n, "nearly", n + tile)
-                assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), (n, kind)
-    finally:
-        hs.hs_set_option("merge_tile", 9)
-        hs.hs_set_option("merge_samples", 1)
-
-
-@pytest.mark.parametrize("shape", [-1, 0, 1, 2, 3, 4, 5])
-@pytest.mark.parametrize("kernel", [0, 1])
-@pytest.mark.parametrize("bulk", [0, 1])
-def test_tuning_options_keep_results(hs, shape, kernel, bulk):
-    """Block-sort shape, its bulk-copy form and the merge-level kernel
-    change speed, not bytes."""
+@pytest.mark.parametrize("shape", [-1, 2, 4])
+@pytest.mark.parametrize("fanin", [2, 4])
+def test_shapes_and_fanin_keep_results(hs, shape, fanin):
+    """Block-sort shape (256 or 288 threads, or the per-size rule) and the
+    merge fan-in change speed, not results: aligned arrays (bulk-copied
+    tiles, sampled partitions), unaligned ones (thread-staged tiles, the
+    generic levels) and n % 4 != 0, on uniform keys, few distinct keys and
+    presorted runs, under four network sets."""
     hs.hs_set_option("blocksort_shape", shape)
-    hs.hs_set_option("merge_kernel", kernel)
-    hs.hs_set_option("blocksort_bulk", bulk)
+    hs.hs_set_option("merge_fanin", fanin)
     try:
         for netset in ["6To8", "3To5", "none", "Odd"]:
-            for n in [1, 7, 8191, 8928, 8929, 16385, 17856, 17857, 100_003, 1 << 20]:
-                a = g.random_i32(n, n + 10 * (shape + 1) + kernel)
-                assert np.array_equal(gpu_sort(hs, a, "merge", netset), oracle.merge_sort(a, netset))
+            for n in [1, 7, 7936, 7937, 8928, 8929, 16385, 17856, 17860, 100_003, 1 << 20]:
+                a = g.random_i32(n, n + 10 * (shape + 1) + fanin)
+                want = oracle.merge_sort(a, netset)
+                assert np.array_equal(gpu_sort(hs, a, "merge", netset), want), (netset, n)
+                if n > 8000:
+                    assert np.array_equal(gpu_sort(hs, a, "merge", netset, offset=1), want), (netset, n)
+        for n in [9000, 65_536, 250_000]:
+            for kind in ["few", "sorted"]:
+                a = g.random_i32(n, n + shape)
+                a = (a % 3).astype(np.int32) if kind == "few" else g.keys(n, "nearly", n + shape)
+                assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), (n, kind)
     finally:
         hs.hs_set_option("blocksort_shape", -1)
-        hs.hs_set_option("merge_kernel", 1)
-        hs.hs_set_option("blocksort_bulk", 1)
+        hs.hs_set_option("merge_fanin", 4)
 
 
 def test_profiling_counters(hs):

@@ -211,28 +211,23 @@ def test_full_batched_workload_against_oracle(hs):
     assert np.array_equal(out, want)
 
 
-@pytest.mark.parametrize("bulk", [0, 1])
 @pytest.mark.parametrize("shift", [0, 1, 3])
-def test_bulk_and_thread_staging(hs, bulk, shift):
+def test_bulk_staging_at_any_alignment(hs, shift):
     """Large segments staged by bulk copies of their 16-byte aligned
-    interiors (three keys at most at each end by the threads) or by the
-    threads alone give the oracle's result, with the key buffer 16-byte
-    aligned or shifted by one or three keys against the workspace (then a
-    tile's output leaves by plain stores)."""
+    interiors (three keys at most at each end by the threads) give the
+    oracle's result, with the key buffer 16-byte aligned or shifted by one or
+    three keys against the workspace (then a tile's output leaves by plain
+    stores)."""
     import torch
     sizes = np.array([993, 994, 995, 996, 7935, 7936, 7937, 7938, 8931, 15_875, 16_387, 40_003,
                       65_536, 3, 1, 2, 4, 5, 6, 7, 70_001, 12_345], np.int64)
     keys, off, _ = g.segmented(0, 31 + shift, sizes=sizes)
     want = oracle.segsort(keys, off, "merge", "6To8")
-    hs.hs_set_option("segsort_bulk", bulk)
-    try:
-        for plan in [hs.make_plan("6To8", 256), hs.make_plan("Odd", 512), hs.make_plan("3To5", 256)]:
-            buf = torch.empty(keys.size + shift, dtype=torch.int32, device="cuda")
-            tk = buf[shift:]
-            tk.copy_(torch.from_numpy(keys))
-            to = torch.from_numpy(np.ascontiguousarray(off, dtype=np.int64)).cuda()
-            hs.hs_segsort_i32(tk, to, "merge", "6To8", plan=plan)
-            hs.hs_device_check()
-            assert np.array_equal(tk.cpu().numpy(), want), plan
-    finally:
-        hs.hs_set_option("segsort_bulk", 1)
+    for plan in [hs.make_plan("6To8", 256), hs.make_plan("Odd", 512), hs.make_plan("3To5", 256)]:
+        buf = torch.empty(keys.size + shift, dtype=torch.int32, device="cuda")
+        tk = buf[shift:]
+        tk.copy_(torch.from_numpy(keys))
+        to = torch.from_numpy(np.ascontiguousarray(off, dtype=np.int64)).cuda()
+        hs.hs_segsort_i32(tk, to, "merge", "6To8", plan=plan)
+        hs.hs_device_check()
+        assert np.array_equal(tk.cpu().numpy(), want), plan
