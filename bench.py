@@ -442,9 +442,30 @@ def run_ours(args):
             tot += time.perf_counter() - t0
         tot = max_over_ranks(tot, pg, dev)
         assert bool(np.all(h_buf.numpy()[1:] >= h_buf.numpy()[:-1])), "e2e output not sorted"
+        # The host link on this machine: plain copies of the same bytes, each
+        # way (context for how much of the end-to-end time is copying).
+        d_tmp = torch.empty(n, dtype=torch.int32, device=dev)
+        link = {}
+        for name, dst, src in (("h2d_gbs", d_tmp, h_buf), ("d2h_gbs", h_buf, d_tmp)):
+            best = None
+            for _ in range(3):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                dst.copy_(src, non_blocking=True)
+                torch.cuda.synchronize(dev)
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+            link[name] = 4 * n / best / 1e9
+        del d_tmp
+        copy_ms = 4 * n / (link["h2d_gbs"] * 1e9) * 1e3 + 4 * n / (link["d2h_gbs"] * 1e9) * 1e3
         line["e2e"] = {"value": whole_job_rate(ws_world, n * e2e_steps, tot), "unit": UNIT,
                        "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
-                       "steps": e2e_steps, "api": "hs_sort_i32_host (pinned host buffer)"}
+                       "steps": e2e_steps, "api": "hs_sort_i32_host (pinned host buffer)",
+                       "ms_per_step": tot / e2e_steps * 1e3,
+                       "link": {k: round(v, 1) for k, v in link.items()},
+                       # both copies back to back, nothing else: the floor
+                       # for a call that must copy in before it can copy out
+                       "copies_alone_ms": copy_ms}
         del ws_h, h_buf
 
     # ---- extra forms (stable pairs), timed the same way

@@ -132,12 +132,17 @@ HS_API hs_status hs_sort_i64(int64_t *d_keys, size_t n, hs_algo a, hs_netset s, 
 /* Host-buffer form, for callers whose keys live in host memory: copies
  * h_keys to the device, sorts them as hs_sort_i32 does, copies the result
  * back into h_keys and waits for `stream` before returning (synchronous).
- * For merge sorts of 2^22 keys or more the copy in travels in 8 chunks on a
- * second stream and each chunk is sorted as soon as it has arrived; merge
- * levels over the sorted chunks finish the sort.
+ * For merge sorts of 2^22 keys or more the copy in travels in at most 8
+ * chunks on a library-created copy stream; each chunk is sorted completely on
+ * one of three library-created side streams as soon as it has arrived (the
+ * chunks' sorts overlap one another and the copy of the next chunks); merge
+ * levels over the sorted chunks on `stream` finish the sort, and the last
+ * one runs in eight parts whose keys are copied out as soon as each is done.
+ * The extra streams and events are created and destroyed inside the call.
  * Pinned host memory makes the copies faster; pageable memory also works.
  *   d_ws: ws_bytes >= hs_sort_host_workspace_bytes(n, a); it holds the
- *   device copy of the keys followed by the sort workspace. */
+ *   device copy of the keys, the sort workspace and (merge) the chunks'
+ *   partition entries. */
 HS_API size_t hs_sort_host_workspace_bytes(size_t n, hs_algo a);
 HS_API hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
                            size_t ws_bytes, hs_stream_t stream);

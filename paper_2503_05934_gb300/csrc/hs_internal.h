@@ -93,10 +93,13 @@ hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, vo
                      size_t ws_bytes, cudaStream_t st);
 hs_status pairs_sort(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, void *d_ws,
                      size_t ws_bytes, cudaStream_t st);
-// Host keys in and out, input copy overlapped with per-chunk sorts (merge
-// path; synchronous).  d_keys: device space for n keys; d_ws: merge workspace.
+// Host keys in and out, input copy overlapped with per-chunk sorts and the
+// copy out with the last level (merge path; synchronous).  d_keys: device
+// space for n keys; d_ws: merge workspace; d_part: host_part_entries(n)
+// int64 partition entries for the chunks' own levels.
+size_t host_part_entries(size_t n);
 hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n, hs_netset s,
-                                  void *d_ws, cudaStream_t st);
+                                  void *d_ws, int64_t *d_part, cudaStream_t st);
 int64_t pairs_tile(int L);
 size_t merge_workspace_bytes_i64(size_t n);
 int64_t tile64(int L, int64_t n);  // int64 block-sort tile for n keys

@@ -124,10 +124,16 @@ void merge_set_fanin(int v) { g_merge_fanin = v; }
 constexpr int M4_NT = kMerge4Threads, M4_EO = kMerge4Keys;
 
 // One four-way keys level: its partition (four splits per tile boundary,
-// part_cap int64 entries available) and its merge.
+// part_cap int64 entries available) and its merge.  With parts > 1 the merge
+// is launched as `parts` launches over consecutive ranges of output tiles,
+// and part_done[p] is recorded on st after launch p, whose outputs end at
+// part_end[p] (for a level of one group, every last level: outputs
+// [part_end[p - 1], part_end[p]) of the array).
 static hs_status launch_keys_level4(const int32_t *kin, int32_t *kout, int64_t n, int64_t w,
                                     int64_t *part, int64_t part_cap, int32_t *samp,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, int parts = 1,
+                                    cudaEvent_t *part_done = nullptr,
+                                    int64_t *part_end = nullptr) {
     using C = TileMerge4<M4_NT, M4_EO>;
     static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
     unsigned *status = nullptr;
@@ -142,10 +148,22 @@ static hs_status launch_keys_level4(const int32_t *kin, int32_t *kout, int64_t n
     if ((r = launch_end(t)) != HS_OK) return r;
     auto kern = k_merge4_tile_bulk<M4_NT, M4_EO>;
     if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
-    t = launch_begin(K_MERGE4_KEYS, st);
-    kern<<<(unsigned)lt.nblocks, M4_NT, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, lt.tpg, samp,
-                                                             status);
-    return launch_end(t);
+    if (parts < 1 || !part_done) parts = 1;
+    for (int p = 0; p < parts; ++p) {
+        const int64_t b0 = lt.nblocks * p / parts, b1 = lt.nblocks * (p + 1) / parts;
+        if (b1 > b0) {
+            t = launch_begin(K_MERGE4_KEYS, st);
+            kern<<<(unsigned)(b1 - b0), M4_NT, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, lt.tpg,
+                                                                    samp, status, b0);
+            if ((r = launch_end(t)) != HS_OK) return r;
+        }
+        if (part_done) {
+            if (part_end) part_end[p] = std::min<int64_t>(b1 * C::TO, n);
+            const cudaError_t e = cudaEventRecord(part_done[p], st);
+            if (e != cudaSuccess) return fail_cuda(e, "merge sort: record a level part");
+        }
+    }
+    return HS_OK;
 }
 
 // Whether the global levels over an n-key array merge four runs per pass.
@@ -156,14 +174,20 @@ static int level_launches(int d, bool four) { return four ? d / 2 + d % 2 : d; }
 
 // Runs the global levels that take sorted runs of w keys through d
 // doublings (one launch pair per binary or four-way level), ping-ponging
-// kcur/kalt; on return kcur holds the result.
+// kcur/kalt; on return kcur holds the result.  With last_parts > 1 a
+// four-way last level is launched in that many parts (see
+// launch_keys_level4), recording part_done[p] after each.
 static hs_status run_levels(int32_t *&kcur, int32_t *&kalt, int64_t n, int64_t w, int d,
                             bool four, int64_t *part, int64_t part_cap, int32_t *samp, int vec,
-                            cudaStream_t st) {
+                            cudaStream_t st, int last_parts = 1, cudaEvent_t *part_done = nullptr,
+                            int64_t *part_end = nullptr) {
     hs_status r = HS_OK;
     while (d > 0 && r == HS_OK) {
         if (four && d % 2 == 0) {
-            r = launch_keys_level4(kcur, kalt, n, w, part, part_cap, samp, st);
+            const bool last = d == 2;
+            r = launch_keys_level4(kcur, kalt, n, w, part, part_cap, samp, st,
+                                   last ? last_parts : 1, last ? part_done : nullptr,
+                                   last ? part_end : nullptr);
             w *= 4;
             d -= 2;
         } else {
@@ -224,81 +248,148 @@ hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, v
     return merge_sort_with(d_keys, n, s, m.kbuf, m.part, (int64_t)merge_ws_part_entries(n_), m.samp, st);
 }
 
-// Chunk-local merge levels of the host-buffer sort: the most that keep one
-// chunk's sort (block sort + k levels) within the time its copy in takes, so
-// that sorting keeps pace with the copies.  Planning rates, measured on
-// GB300: host link 200 GB/s, block sort 130 Gkeys/s, a merge level 8 B/key at
-// 6.5 TB/s plus 30 us of partition and launch latency.
-static int host_local_levels(int64_t chunk, int max_levels) {
-    const double copy_s = 4.0 * chunk / 200e9;
-    const double sort_s = chunk / 130e9;
-    const double level_s = 8.0 * chunk / 6.5e12 + 30e-6;
-    int k = 0;
-    while (k < max_levels && sort_s + (k + 1) * level_s <= copy_s) ++k;
-    return k;
+// Host-buffer merge sort, for n of at least a few chunks' worth of keys.
+//
+//  * The keys are copied in as at most kHostChunks chunks on a copy stream.
+//    A chunk holds C = T * 2^k keys (T the block-sort tile, C the smallest
+//    such length with at most kHostChunks chunks), so every chunk is a whole
+//    run of the merge sort's level of width C.
+//  * As each chunk lands it is sorted completely (block sort and its own
+//    merge levels) on one of kHostSideStreams side streams; chunks overlap
+//    one another and the copy of the next ones.  Each chunk uses its own
+//    slice of partition entries (hs_host_part_entries per chunk).
+//  * On the caller's stream the merge levels over the sorted chunks finish
+//    the sort.  The last (four-way) level runs as kHostOutParts launches
+//    over consecutive ranges of output tiles, and each part's keys are
+//    copied out as soon as it is done, while the next parts still merge.
+//
+// d_keys is device memory for n keys; d_ws the merge workspace for n keys;
+// d_part the chunks' partition slices (host_part_entries(n) int64).
+constexpr int kHostChunks = 8, kHostSideStreams = 3, kHostOutParts = 8;
+
+static int64_t host_chunk_keys(int64_t n, int64_t T) {
+    int64_t C = T;
+    while (C * kHostChunks < n) C *= 2;
+    return C;
+}
+// Partition entries one chunk of C keys needs at most (four per tile
+// boundary of 3936-key tiles over groups of four runs of at least one
+// block-sort tile, or one per 3968-key tile of a binary level), with room.
+static int64_t chunk_part_entries(int64_t C) { return C / 512 + 64; }
+
+size_t host_part_entries(size_t n) {
+    // C < n / 4 + 2T for n >= kHostChunks * T, and chunks <= kHostChunks.
+    return (size_t)kHostChunks * (size_t)chunk_part_entries((int64_t)(n / 4 + 2 * 8928 * 2)) + 64;
 }
 
-// Host-buffer merge sort.  The keys are copied in as about eight chunks on a
-// second stream; as each chunk lands it is block sorted and merged k levels
-// deep into runs of W = T << k keys (chunks are whole multiples of W, so these
-// are exactly the first k levels of the whole sort).  The remaining levels run
-// over the whole array, and the result is copied out.  d_keys is device
-// memory for n keys; d_ws the merge workspace for n keys.
 hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, hs_netset s,
-                                  void *d_ws, cudaStream_t st) {
-    constexpr int kChunks = 8;
+                                  void *d_ws, int64_t *d_part, cudaStream_t st) {
     const int64_t n = (int64_t)n_;
     const int L = leaf_size(s);
     const int shape = shape_for(n, L);
     const int64_t T = shape_tile(shape, L);
-    const int levels = global_levels(n, T);
-    const int k = host_local_levels((n + kChunks - 1) / kChunks, levels > 0 ? levels - 1 : 0);
-    const int64_t W = T << k;
-    // Chunk length: whole runs of W keys, so chunk starts are multiples of
-    // T (16-byte aligned, sample positions at multiples of 32).
-    const int64_t C = W * std::max<int64_t>(1, (n + kChunks * W - 1) / (kChunks * W));
+    const int64_t C = host_chunk_keys(n, T);
     const int nch = (int)((n + C - 1) / C);
+    const int64_t PC = chunk_part_entries(C);
+    if ((size_t)(nch * PC) > host_part_entries(n_))
+        return fail(HS_ERR_INVALID_ARG, "host sort: partition slices exceed their workspace");
     const MergeScratch m = carve_merge_workspace(d_ws, n_);
     const int vec = aligned(d_keys, 16) ? 1 : 0;
     int32_t *samp = tiled_levels(n, vec) ? m.samp : nullptr;
     // Decided once for the whole array, so that every chunk runs the same
-    // number of launches (the parity that places its block sort).
+    // kind of levels (the parity of its launches places its block sort).
     const bool four = four_way_levels(n, vec);
     const int64_t part_cap = (int64_t)merge_ws_part_entries(n_);
 
-    cudaStream_t cs = nullptr;
-    cudaEvent_t ev[kChunks] = {};
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    cudaStream_t cs = nullptr, side[kHostSideStreams] = {};
+    cudaEvent_t ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {}, ev_part[kHostOutParts] = {};
+    int64_t part_end[kHostOutParts] = {};
     hs_status r = HS_OK;
-    for (int c = 0; c < nch && e == cudaSuccess; ++c) e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming);
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int i = 0; i < kHostSideStreams && e == cudaSuccess; ++i)
+        e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
     for (int c = 0; c < nch && e == cudaSuccess; ++c) {
-        const int64_t b = c * C, len = std::min<int64_t>(C, n - b);
-        e = cudaMemcpyAsync(d_keys + b, h_keys + b, (size_t)len * sizeof(int32_t), cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[c], cs);
+        e = cudaEventCreateWithFlags(&ev_in[c], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_done[c], cudaEventDisableTiming);
     }
-    if (e != cudaSuccess) r = fail_cuda(e, "host sort: chunked copy in");
+    for (int p = 0; p < kHostOutParts && e == cudaSuccess; ++p)
+        e = cudaEventCreateWithFlags(&ev_part[p], cudaEventDisableTiming);
+    // The copy stream and the side streams start after what the caller's
+    // stream has queued so far (the workspace may still be in use there).
+    cudaEvent_t ev_start = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
+    for (int i = 0; i < kHostSideStreams && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(side[i], ev_start, 0);
+    if (e != cudaSuccess) r = fail_cuda(e, "host sort: streams and events");
     for (int c = 0; c < nch && r == HS_OK; ++c) {
         const int64_t b = c * C, len = std::min<int64_t>(C, n - b);
-        if ((e = cudaStreamWaitEvent(st, ev[c], 0)) != cudaSuccess) {
+        e = cudaMemcpyAsync(d_keys + b, h_keys + b, (size_t)len * sizeof(int32_t), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in[c], cs);
+        if (e != cudaSuccess) r = fail_cuda(e, "host sort: chunked copy in");
+    }
+    for (int c = 0; c < nch && r == HS_OK; ++c) {
+        const int64_t b = c * C, len = std::min<int64_t>(C, n - b);
+        cudaStream_t ss = side[c % kHostSideStreams];
+        if ((e = cudaStreamWaitEvent(ss, ev_in[c], 0)) != cudaSuccess) {
             r = fail_cuda(e, "host sort: wait for a chunk");
             break;
         }
         // The block sort writes where the chunk's ping-pong levels end in d_keys.
-        const bool even = level_launches(k, four) % 2 == 0;
+        const int d = global_levels(len, T);
+        const bool even = level_launches(d, four) % 2 == 0;
         int32_t *cur = even ? d_keys + b : m.kbuf + b;
         int32_t *alt = even ? m.kbuf + b : d_keys + b;
         int32_t *csamp = samp ? samp + b / kSampleStride : nullptr;
-        r = blocksort_launch_shape(shape, L, d_keys + b, cur, len, s, vec, st, csamp);
-        if (r == HS_OK) r = run_levels(cur, alt, len, T, k, four, m.part, part_cap, csamp, vec, st);
+        r = blocksort_launch_shape(shape, L, d_keys + b, cur, len, s, vec, ss, csamp);
+        if (r == HS_OK) r = run_levels(cur, alt, len, T, d, four, d_part + c * PC, PC, csamp, vec, ss);
+        if (r == HS_OK && (e = cudaEventRecord(ev_done[c], ss)) != cudaSuccess)
+            r = fail_cuda(e, "host sort: chunk done");
+        if (r == HS_OK && (e = cudaStreamWaitEvent(st, ev_done[c], 0)) != cudaSuccess)
+            r = fail_cuda(e, "host sort: join a chunk");
     }
     int32_t *kcur = d_keys, *kalt = m.kbuf;
-    if (r == HS_OK) r = run_levels(kcur, kalt, n, W, levels - k, four, m.part, part_cap, samp, vec, st);
-    if (r == HS_OK && (e = cudaMemcpyAsync(h_keys, kcur, n_ * sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        r = fail_cuda(e, "host sort: copy out");
+    const int d_final = global_levels(n, C);
+    // The last level in parts, each copied out as soon as it is done (a
+    // four-way last level; otherwise one copy after the last level).
+    const bool split = four && d_final >= 2;
+    if (r == HS_OK)
+        r = run_levels(kcur, kalt, n, C, d_final, four, m.part, part_cap, samp, vec, st,
+                       split ? kHostOutParts : 1, split ? ev_part : nullptr, split ? part_end : nullptr);
+    if (r == HS_OK) {
+        if (split) {
+            int64_t lo = 0;
+            for (int p = 0; p < kHostOutParts && e == cudaSuccess; ++p) {
+                const int64_t hi = part_end[p];
+                e = cudaStreamWaitEvent(cs, ev_part[p], 0);
+                if (e == cudaSuccess && hi > lo)
+                    e = cudaMemcpyAsync(h_keys + lo, kcur + lo, (size_t)(hi - lo) * sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, cs);
+                lo = hi;
+            }
+        } else {
+            e = cudaEventRecord(ev_start, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_keys, kcur, n_ * sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
+        }
+        if (e != cudaSuccess) r = fail_cuda(e, "host sort: copy out");
+    }
+    // Wait for everything queued, on every stream, before releasing them.
+    for (int i = 0; i < kHostSideStreams; ++i)
+        if (side[i] && (e = cudaStreamSynchronize(side[i])) != cudaSuccess && r == HS_OK)
+            r = fail_cuda(e, "host sort: side stream");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess && r == HS_OK) r = fail_cuda(e, "host sort: synchronize");
     if (cs && (e = cudaStreamSynchronize(cs)) != cudaSuccess && r == HS_OK) r = fail_cuda(e, "host sort: copy stream");
-    for (int c = 0; c < nch; ++c)
-        if (ev[c]) cudaEventDestroy(ev[c]);
+    for (int c = 0; c < kHostChunks; ++c) {
+        if (ev_in[c]) cudaEventDestroy(ev_in[c]);
+        if (ev_done[c]) cudaEventDestroy(ev_done[c]);
+    }
+    for (int p = 0; p < kHostOutParts; ++p)
+        if (ev_part[p]) cudaEventDestroy(ev_part[p]);
+    if (ev_start) cudaEventDestroy(ev_start);
+    for (int i = 0; i < kHostSideStreams; ++i)
+        if (side[i]) cudaStreamDestroy(side[i]);
     if (cs) cudaStreamDestroy(cs);
     return r;
 }

@@ -265,7 +265,7 @@ HS_DEV int stage_merge(const int32_t *A, int na, const int32_t *B, int nb, int d
 template <int NT, int EO>
 __global__ void __launch_bounds__(NT)
     k_merge4_tile_bulk(const int32_t *in, int32_t *out, int64_t n, int64_t w, const int64_t *part,
-                       int64_t tpg, int32_t *samp, unsigned *status) {
+                       int64_t tpg, int32_t *samp, unsigned *status, int64_t block0) {
     using C = TileMerge4<NT, EO>;
     constexpr int TO = C::TO, P = C::P;
     static_assert(kSampleStride == 32, "sample positions are multiples of 32");
@@ -273,8 +273,9 @@ __global__ void __launch_bounds__(NT)
     __shared__ __align__(8) uint64_t bar;
     __shared__ int wsplit[NT / 32 + 1];
 
-    const int64_t g = blockIdx.x / tpg;
-    const int64_t t = blockIdx.x - g * tpg;
+    const int64_t b = block0 + blockIdx.x;  // output tile (a launch may cover a range of them)
+    const int64_t g = b / tpg;
+    const int64_t t = b - g * tpg;
     int64_t start[4], len[4];
     kway_runs_geom<4>(g, n, w, start, len);
     const int64_t glen = len[0] + len[1] + len[2] + len[3];
@@ -287,8 +288,8 @@ __global__ void __launch_bounds__(NT)
     int pos = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int64_t s = part[4 * blockIdx.x + i];
-        const int64_t e = last_tile ? len[i] : part[4 * (blockIdx.x + 1) + i];
+        const int64_t s = part[4 * b + i];
+        const int64_t e = last_tile ? len[i] : part[4 * (b + 1) + i];
         cnt[i] = (int)(e - s);
         src[i] = start[i] + s;
         const int64_t c0 = src[i] & ~int64_t(3);

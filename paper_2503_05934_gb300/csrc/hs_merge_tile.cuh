@@ -40,21 +40,22 @@ struct TileMerge2 {
 template <int NT, int EO>
 __global__ void __launch_bounds__(NT)
     k_merge_tile_bulk(const int32_t *in, int32_t *out, int64_t n, int64_t w, const int64_t *part,
-                      int tpg, int32_t *samp, unsigned *status) {
+                      int tpg, int32_t *samp, unsigned *status, int64_t block0) {
     using C = TileMerge2<NT, EO>;
     constexpr int TO = C::TO, P = C::P;
     static_assert(kSampleStride == 32, "sample positions are multiples of 32");
     extern __shared__ __align__(16) int32_t smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int wsplit[NT / 32 + 1];
-    const int64_t g = blockIdx.x / tpg;
-    const int t = blockIdx.x - (int)(g * tpg);
+    const int64_t b = block0 + blockIdx.x;  // output tile (a launch may cover a range of them)
+    const int64_t g = b / tpg;
+    const int t = (int)(b - g * tpg);
     const MergeGeom m = merge_geom(g, n, w);
     const int64_t glen = m.alen + m.blen;
     const int64_t o0 = (int64_t)t * TO;
     const int64_t o1 = (o0 + TO) < glen ? (o0 + TO) : glen;
-    const int64_t a0 = part[blockIdx.x];
-    const int64_t a1 = (o1 == glen) ? m.alen : part[blockIdx.x + 1];
+    const int64_t a0 = part[b];
+    const int64_t a1 = (o1 == glen) ? m.alen : part[b + 1];
     const int na = (int)(a1 - a0);
     const int tot = (int)(o1 - o0);
     const int nb = tot - na;
@@ -162,7 +163,7 @@ static hs_status launch_tile_bulk(const int32_t *kin, int32_t *kout, int64_t n, 
     if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
     LaunchToken t = launch_begin(K_MERGE_KEYS, st);
     kern<<<(unsigned)lt.nblocks, NT, C::SMEM_BYTES, st>>>(kin, kout, n, w, part, (int)lt.tpg, samp,
-                                                          status);
+                                                          status, int64_t(0));
     return launch_end(t);
 }
 

@@ -333,7 +333,9 @@ hs_status hs_sort_i64(int64_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d
 }
 
 size_t hs_sort_host_workspace_bytes(size_t n, hs_algo a) {
-    return align_up(n * sizeof(int32_t), 256) + hs_sort_workspace_bytes(n, 0, a);
+    // [device keys][sort workspace][partition entries of the chunks' levels]
+    return align_up(n * sizeof(int32_t), 256) + align_up(hs_sort_workspace_bytes(n, 0, a), 256) +
+           (a == HS_ALGO_MERGE ? align_up(host_part_entries(n) * sizeof(int64_t), 256) : 0);
 }
 
 hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
@@ -351,8 +353,11 @@ hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netset s, vo
     int32_t *d_keys = static_cast<int32_t *>(d_ws);
     size_t kb = align_up(n * sizeof(int32_t), 256);
     // Large merge sorts overlap the copy in with per-chunk sorts.
-    if (a == HS_ALGO_MERGE && n >= ((size_t)1 << 22))
-        return merge_sort_host_chunked(h_keys, d_keys, n, s, static_cast<char *>(d_ws) + kb, cs);
+    if (a == HS_ALGO_MERGE && n >= ((size_t)1 << 22)) {
+        const size_t wb = align_up(hs_sort_workspace_bytes(n, 0, a), 256);
+        return merge_sort_host_chunked(h_keys, d_keys, n, s, static_cast<char *>(d_ws) + kb,
+                                       reinterpret_cast<int64_t *>(static_cast<char *>(d_ws) + kb + wb), cs);
+    }
     cudaError_t e = cudaMemcpyAsync(d_keys, h_keys, n * sizeof(int32_t), cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return fail_cuda(e, "hs_sort_i32_host: host-to-device copy");
     st = hs_sort_i32(d_keys, n, a, s, static_cast<char *>(d_ws) + kb, ws_bytes - kb, stream);

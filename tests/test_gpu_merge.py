@@ -198,6 +198,24 @@ def test_host_buffer_entry_chunked(hs, n):
     assert np.array_equal(p.numpy(), want)
 
 
+@pytest.mark.parametrize("fanin", [2, 4])
+@pytest.mark.parametrize("netset", ["6To8", "none"])
+def test_host_buffer_pipeline_options(hs, fanin, netset):
+    """The chunked host-buffer sort (chunks sorted on side streams, the last
+    level copied out in parts) under both fan-ins and the smallest block-sort
+    tile, against the oracle."""
+    import torch
+    hs.hs_set_option("merge_fanin", fanin)
+    try:
+        for n in [1 << 22, (1 << 22) + 4 * 777, 9 * (1 << 20) + 3]:
+            a = g.random_i32(n, 60 + n + fanin)
+            h = torch.from_numpy(a.copy()).pin_memory()
+            hs.hs_sort_i32_host(h, "merge", netset)
+            assert np.array_equal(h.numpy(), oracle.merge_sort(a, netset)), n
+    finally:
+        hs.hs_set_option("merge_fanin", 4)
+
+
 def test_bulk_copy_wait_gives_up_with_a_status(hs):
     """A bulk-copy wait that can never complete (an mbarrier armed for bytes
     no copy delivers) ends after its poll limit with HS_ERR_TIMEOUT from
