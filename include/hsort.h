@@ -138,7 +138,8 @@ HS_API hs_status hs_sort_i64(int64_t *d_keys, size_t n, hs_algo a, hs_netset s, 
  * chunks' sorts overlap one another and the copy of the next chunks); merge
  * levels over the sorted chunks on `stream` finish the sort, and the last
  * one runs in eight parts whose keys are copied out as soon as each is done.
- * The extra streams and events are created and destroyed inside the call.
+ * The copy and side streams and their events are created by the first such
+ * call per host thread and device and kept for the life of the process.
  * Pinned host memory makes the copies faster; pageable memory also works.
  *   d_ws: ws_bytes >= hs_sort_host_workspace_bytes(n, a); it holds the
  *   device copy of the keys, the sort workspace and (merge) the chunks'
@@ -349,11 +350,13 @@ HS_API hs_status hs_bulk_wait_selftest(uint32_t polls, hs_stream_t stream);
  *     -1 (default): per array, 4 when its larger tile saves a global level
  *     over 2, else 2.  A thread holds four leaves of leaf, leaf, leaf and
  *     leaf-1 keys, so a tile holds (4 * leaf - 1) * threads keys.
- *   "merge_fanin": 4 (default) the tiled keys levels merge four runs per
- *     pass: a four-way merge-path split per output tile, then two stages of
- *     binary merges in shared memory, one read and one write of every key for
- *     two of Algorithm 1's merge levels (a binary level first when the number
- *     of levels is odd); 2 binary levels only.
+ *   "merge_fanin": 4 the tiled keys levels merge four runs per pass: a
+ *     four-way merge-path split per output tile, then two stages of binary
+ *     merges in shared memory, one read and one write of every key for two
+ *     of Algorithm 1's merge levels (a binary level first when the number of
+ *     levels is odd); 2 binary levels only; 0 (default) four-way levels for
+ *     arrays of at least 2^27 keys, binary below (the four-way partition's
+ *     latency outweighs the saved pass on smaller arrays).
  * Tiled levels (bulk-copied tiles, sampled partition searches) serve 16-byte
  * aligned buffers whose length is a multiple of 4 keys (of 2 for int64);
  * other buffers take thread-staged generic forms.  Every option gives

@@ -3,6 +3,8 @@
 // ping-ponging between the caller's array and the workspace so that the last
 // level lands in the caller's array.
 #include <algorithm>
+#include <new>
+#include <vector>
 
 #include "hs_internal.h"
 #include "hs_blocksort.cuh"
@@ -114,11 +116,18 @@ static hs_status launch_keys_level(const int32_t *kin, int32_t *kout, int64_t n,
     return launch_end(t);
 }
 
-// Option "merge_fanin": 4 (default) the tiled keys levels merge four runs
+// Option "merge_fanin": the tiled keys levels of an array merge four runs
 // per pass (two binary levels of Algorithm 1's Merge in one read and one
 // write of every key; a binary level first when the number of doublings is
-// odd); 2 binary levels only.
-static int g_merge_fanin = 4;
+// odd) with 4, binary levels only with 2, and with 0 (the default) four-way
+// levels for arrays of at least kFourWayMinKeys keys.  A four-way level
+// saves a pass over the keys but its partition is a latency-bound chain of
+// 15 to 27 rounds (0.04 to 0.1 ms), so it pays off only on large arrays:
+// whole sorts measured on GB300 with four-way against binary levels took
+// 0.17 / 0.11 ms at 2^18 keys, 0.39 / 0.26 at 2^22, 1.10 / 0.95 at 2^25,
+// 1.84 / 1.74 at 2^26, 3.37 / 3.38 at 2^27 and 6.54 / 6.90 ms at 2^28.
+constexpr int64_t kFourWayMinKeys = int64_t(1) << 27;
+static int g_merge_fanin = 0;
 void merge_set_fanin(int v) { g_merge_fanin = v; }
 
 constexpr int M4_NT = kMerge4Threads, M4_EO = kMerge4Keys;
@@ -167,7 +176,10 @@ static hs_status launch_keys_level4(const int32_t *kin, int32_t *kout, int64_t n
 }
 
 // Whether the global levels over an n-key array merge four runs per pass.
-static bool four_way_levels(int64_t n, int vec) { return g_merge_fanin == 4 && tiled_levels(n, vec); }
+static bool four_way_levels(int64_t n, int vec) {
+    if (!tiled_levels(n, vec) || g_merge_fanin == 2) return false;
+    return g_merge_fanin == 4 || n >= kFourWayMinKeys;
+}
 
 // Launches of the global levels that double the runs d times.
 static int level_launches(int d, bool four) { return four ? d / 2 + d % 2 : d; }
@@ -282,6 +294,58 @@ size_t host_part_entries(size_t n) {
     return (size_t)kHostChunks * (size_t)chunk_part_entries((int64_t)(n / 4 + 2 * 8928 * 2)) + 64;
 }
 
+// Streams and events of the host-buffer pipeline, created on first use per
+// host thread and device and kept for the life of the process (creating them
+// per call costs host time on every call).
+struct HostPipe {
+    int device = -1;
+    cudaStream_t cs = nullptr, side[kHostSideStreams] = {};
+    cudaEvent_t ev_start = nullptr, ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {},
+                ev_part[kHostOutParts] = {};
+};
+
+static hs_status host_pipe(HostPipe **out) {
+    static thread_local std::vector<HostPipe *> pipes;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e, "host sort: current device");
+    for (HostPipe *p : pipes)
+        if (p->device == dev) {
+            *out = p;
+            return HS_OK;
+        }
+    HostPipe *p = new (std::nothrow) HostPipe();
+    if (!p) return fail(HS_ERR_NO_MEMORY, "host sort: pipeline state");
+    p->device = dev;
+    e = cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking);
+    for (int i = 0; i < kHostSideStreams && e == cudaSuccess; ++i)
+        e = cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
+    for (int c = 0; c < kHostChunks && e == cudaSuccess; ++c) {
+        e = cudaEventCreateWithFlags(&p->ev_in[c], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done[c], cudaEventDisableTiming);
+    }
+    for (int q = 0; q < kHostOutParts && e == cudaSuccess; ++q)
+        e = cudaEventCreateWithFlags(&p->ev_part[q], cudaEventDisableTiming);
+    if (e != cudaSuccess) {  // release what was made; the next call retries
+        for (int c = 0; c < kHostChunks; ++c) {
+            if (p->ev_in[c]) cudaEventDestroy(p->ev_in[c]);
+            if (p->ev_done[c]) cudaEventDestroy(p->ev_done[c]);
+        }
+        for (int q = 0; q < kHostOutParts; ++q)
+            if (p->ev_part[q]) cudaEventDestroy(p->ev_part[q]);
+        if (p->ev_start) cudaEventDestroy(p->ev_start);
+        for (int i = 0; i < kHostSideStreams; ++i)
+            if (p->side[i]) cudaStreamDestroy(p->side[i]);
+        if (p->cs) cudaStreamDestroy(p->cs);
+        delete p;
+        return fail_cuda(e, "host sort: streams and events");
+    }
+    pipes.push_back(p);
+    *out = p;
+    return HS_OK;
+}
+
 hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, hs_netset s,
                                   void *d_ws, int64_t *d_part, cudaStream_t st) {
     const int64_t n = (int64_t)n_;
@@ -296,32 +360,26 @@ hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, h
     const MergeScratch m = carve_merge_workspace(d_ws, n_);
     const int vec = aligned(d_keys, 16) ? 1 : 0;
     int32_t *samp = tiled_levels(n, vec) ? m.samp : nullptr;
-    // Decided once for the whole array, so that every chunk runs the same
-    // kind of levels (the parity of its launches places its block sort).
+    // The levels over the whole array are four-way by its size; a chunk's own
+    // levels by the chunk's (the parity of its launches places its block
+    // sort), and only when the whole array takes tiled levels.
     const bool four = four_way_levels(n, vec);
     const int64_t part_cap = (int64_t)merge_ws_part_entries(n_);
 
-    cudaStream_t cs = nullptr, side[kHostSideStreams] = {};
-    cudaEvent_t ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {}, ev_part[kHostOutParts] = {};
+    HostPipe *pp = nullptr;
+    hs_status r = host_pipe(&pp);
+    if (r != HS_OK) return r;
+    cudaStream_t cs = pp->cs;
+    cudaStream_t *side = pp->side;
+    cudaEvent_t *ev_in = pp->ev_in, *ev_done = pp->ev_done, *ev_part = pp->ev_part;
+    cudaEvent_t ev_start = pp->ev_start;
     int64_t part_end[kHostOutParts] = {};
-    hs_status r = HS_OK;
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    for (int i = 0; i < kHostSideStreams && e == cudaSuccess; ++i)
-        e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
-    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
-        e = cudaEventCreateWithFlags(&ev_in[c], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_done[c], cudaEventDisableTiming);
-    }
-    for (int p = 0; p < kHostOutParts && e == cudaSuccess; ++p)
-        e = cudaEventCreateWithFlags(&ev_part[p], cudaEventDisableTiming);
     // The copy stream and the side streams start after what the caller's
     // stream has queued so far (the workspace may still be in use there).
-    cudaEvent_t ev_start = nullptr;
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ev_start, st);
+    cudaError_t e = cudaEventRecord(ev_start, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
     for (int i = 0; i < kHostSideStreams && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(side[i], ev_start, 0);
-    if (e != cudaSuccess) r = fail_cuda(e, "host sort: streams and events");
+    if (e != cudaSuccess) r = fail_cuda(e, "host sort: order the streams");
     for (int c = 0; c < nch && r == HS_OK; ++c) {
         const int64_t b = c * C, len = std::min<int64_t>(C, n - b);
         e = cudaMemcpyAsync(d_keys + b, h_keys + b, (size_t)len * sizeof(int32_t), cudaMemcpyHostToDevice, cs);
@@ -337,12 +395,13 @@ hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, h
         }
         // The block sort writes where the chunk's ping-pong levels end in d_keys.
         const int d = global_levels(len, T);
-        const bool even = level_launches(d, four) % 2 == 0;
+        const bool four_c = tiled_levels(n, vec) && four_way_levels(len, vec);
+        const bool even = level_launches(d, four_c) % 2 == 0;
         int32_t *cur = even ? d_keys + b : m.kbuf + b;
         int32_t *alt = even ? m.kbuf + b : d_keys + b;
         int32_t *csamp = samp ? samp + b / kSampleStride : nullptr;
         r = blocksort_launch_shape(shape, L, d_keys + b, cur, len, s, vec, ss, csamp);
-        if (r == HS_OK) r = run_levels(cur, alt, len, T, d, four, d_part + c * PC, PC, csamp, vec, ss);
+        if (r == HS_OK) r = run_levels(cur, alt, len, T, d, four_c, d_part + c * PC, PC, csamp, vec, ss);
         if (r == HS_OK && (e = cudaEventRecord(ev_done[c], ss)) != cudaSuccess)
             r = fail_cuda(e, "host sort: chunk done");
         if (r == HS_OK && (e = cudaStreamWaitEvent(st, ev_done[c], 0)) != cudaSuccess)
@@ -375,22 +434,13 @@ hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, h
         }
         if (e != cudaSuccess) r = fail_cuda(e, "host sort: copy out");
     }
-    // Wait for everything queued, on every stream, before releasing them.
+    // Wait for everything queued, on every stream: the call is synchronous,
+    // and the cached streams start the next call idle.
     for (int i = 0; i < kHostSideStreams; ++i)
-        if (side[i] && (e = cudaStreamSynchronize(side[i])) != cudaSuccess && r == HS_OK)
+        if ((e = cudaStreamSynchronize(side[i])) != cudaSuccess && r == HS_OK)
             r = fail_cuda(e, "host sort: side stream");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess && r == HS_OK) r = fail_cuda(e, "host sort: synchronize");
-    if (cs && (e = cudaStreamSynchronize(cs)) != cudaSuccess && r == HS_OK) r = fail_cuda(e, "host sort: copy stream");
-    for (int c = 0; c < kHostChunks; ++c) {
-        if (ev_in[c]) cudaEventDestroy(ev_in[c]);
-        if (ev_done[c]) cudaEventDestroy(ev_done[c]);
-    }
-    for (int p = 0; p < kHostOutParts; ++p)
-        if (ev_part[p]) cudaEventDestroy(ev_part[p]);
-    if (ev_start) cudaEventDestroy(ev_start);
-    for (int i = 0; i < kHostSideStreams; ++i)
-        if (side[i]) cudaStreamDestroy(side[i]);
-    if (cs) cudaStreamDestroy(cs);
+    if ((e = cudaStreamSynchronize(cs)) != cudaSuccess && r == HS_OK) r = fail_cuda(e, "host sort: copy stream");
     return r;
 }
 

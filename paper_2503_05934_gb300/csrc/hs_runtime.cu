@@ -406,8 +406,8 @@ hs_status hs_set_option(const char *name, int64_t value) {
         return HS_OK;
     }
     if (std::strcmp(name, "merge_fanin") == 0) {
-        if (value != 2 && value != 4)
-            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_fanin must be 2 or 4");
+        if (value != 0 && value != 2 && value != 4)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: merge_fanin must be 0, 2 or 4");
         merge_set_fanin((int)value);
         return HS_OK;
     }

@@ -358,7 +358,10 @@ constexpr int seg_smem_bytes() {
 // lists are drained.  Large segments first also balances the load: the
 // short items fill the gaps at the end.
 template <int NT, int L, int LV>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 2)
+#ifndef HS_SEG_MINCTAS
+#define HS_SEG_MINCTAS 3
+#endif
+__global__ void __launch_bounds__(NT, NT <= 256 ? HS_SEG_MINCTAS : 2)
     k_seg_sort(const SegDesc *cdesc, int64_t ndesc, unsigned long long *ctrl, uint32_t netset,
                unsigned *status) {
     extern __shared__ __align__(16) int32_t smem[];

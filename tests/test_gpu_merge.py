@@ -213,7 +213,7 @@ def test_host_buffer_pipeline_options(hs, fanin, netset):
             hs.hs_sort_i32_host(h, "merge", netset)
             assert np.array_equal(h.numpy(), oracle.merge_sort(a, netset)), n
     finally:
-        hs.hs_set_option("merge_fanin", 4)
+        hs.hs_set_option("merge_fanin", 0)
 
 
 def test_bulk_copy_wait_gives_up_with_a_status(hs):
@@ -230,17 +230,25 @@ def test_bulk_copy_wait_gives_up_with_a_status(hs):
     assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a))
 
 
-def test_workspace_reuse_and_launch_count(hs):
+@pytest.mark.parametrize("fanin", [0, 4])
+def test_workspace_reuse_and_launch_count(hs, fanin):
+    """Three sorts through one workspace; the launch count follows the level
+    plan: binary levels below 2^27 keys by default, four-way levels when
+    forced."""
     import torch
     n = 1 << 20
     ws = torch.empty(hs.hs_sort_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    hs.hs_set_option("merge_fanin", fanin)
     before = hs.hs_launch_count()
-    for seed in range(3):
-        a = g.random_i32(n, seed)
-        t = to_dev(a)
-        hs.hs_sort_i32(t, "merge", "6To8", ws=ws)
-        torch.cuda.synchronize()
-        assert np.array_equal(t.cpu().numpy(), np.sort(a))
+    try:
+        for seed in range(3):
+            a = g.random_i32(n, seed)
+            t = to_dev(a)
+            hs.hs_sort_i32(t, "merge", "6To8", ws=ws)
+            torch.cuda.synchronize()
+            assert np.array_equal(t.cpu().numpy(), np.sort(a))
+    finally:
+        hs.hs_set_option("merge_fanin", 0)
     # 1 block sort + 2 launches (partition, merge) per global level over the
     # block-sort tile the library reports for this n; four-way levels take
     # two doublings each, after one binary level when their number is odd
@@ -248,7 +256,8 @@ def test_workspace_reuse_and_launch_count(hs):
     levels = 0
     while tile << levels < n:
         levels += 1
-    assert hs.hs_launch_count() - before == 3 * (1 + 2 * (levels // 2 + levels % 2))
+    launches = levels // 2 + levels % 2 if fanin == 4 else levels
+    assert hs.hs_launch_count() - before == 3 * (1 + 2 * launches)
 
 
 def _four_way_inputs(n, seed):
@@ -292,7 +301,7 @@ def test_four_way_levels(hs, netset):
                     hs.hs_set_option("merge_fanin", fanin)
                     assert np.array_equal(gpu_sort(hs, a, "merge", netset), want), (n, name, fanin)
     finally:
-        hs.hs_set_option("merge_fanin", 4)
+        hs.hs_set_option("merge_fanin", 0)
 
 
 def test_four_way_levels_unaligned_and_ragged(hs):
@@ -347,13 +356,14 @@ def test_shapes_and_fanin_keep_results(hs, shape, fanin):
                 assert np.array_equal(gpu_sort(hs, a, "merge", "6To8"), np.sort(a)), (n, kind)
     finally:
         hs.hs_set_option("blocksort_shape", -1)
-        hs.hs_set_option("merge_fanin", 4)
+        hs.hs_set_option("merge_fanin", 0)
 
 
 def test_profiling_counters(hs):
     import torch
     hs.hs_prof_reset()
     hs.hs_prof_enable(True)
+    hs.hs_set_option("merge_fanin", 4)  # four-way levels at this size too
     try:
         t = to_dev(g.random_i32(1 << 18, 1))
         hs.hs_sort_i32(t, "merge", "6To8")
@@ -363,6 +373,7 @@ def test_profiling_counters(hs):
         n_m4, ms_m4 = hs.hs_prof_read("merge4_keys")
     finally:
         hs.hs_prof_enable(False)
+        hs.hs_set_option("merge_fanin", 0)
     tile = int(hs.lib().hs_keys_tile(hs.netset_mask("6To8"), 1 << 18))
     levels = 0
     while tile << levels < (1 << 18):

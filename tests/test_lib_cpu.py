@@ -135,7 +135,7 @@ def test_bulk_wait_selftest_rejects_bad_poll_limits(hs):
 # (hs_set_option validates on the host, so no GPU is needed).
 OPTIONS = [
     ("blocksort_shape", -1, 4, [-2, 0, 1, 3, 5, 6]),
-    ("merge_fanin", 4, 2, [0, 1, 3, 8]),
+    ("merge_fanin", 0, 4, [1, 3, 8, -1]),
     ("quick_partition", 3, 2, [1, 4]),
 ]
 
