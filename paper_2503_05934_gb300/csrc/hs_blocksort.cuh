@@ -295,6 +295,16 @@ __global__ void __launch_bounds__(NT, blocksort_min_ctas(NT))
                                     base);
 }
 
+// A whole small array [0, n) (n <= the tile) sorted by one CTA of NT
+// threads in one launch: leaves and every merge level in shared memory; the
+// threads and groups past the live keys skip their work (SKIP).
+template <int NT, int L, int LEAVES>
+__global__ void __launch_bounds__(NT, 1)
+    k_blocksort_small(const int32_t *kin, int32_t *kout, int n, uint32_t netset, int vec) {
+    extern __shared__ __align__(16) int32_t smem[];
+    block_sort_tile3<NT, L, LEAVES, true>(kin, kout, n, netset, vec != 0, smem);
+}
+
 // Bulk-copy form for 16-byte aligned arrays: a full tile arrives by one bulk
 // copy (completion counted on an mbarrier) and leaves by one bulk store, and
 // each thread writes the samples among its own keys from registers, so the

@@ -65,6 +65,11 @@ def _edge_sizes(netset):
     sizes |= {T - 1, T, T + 1, 2 * T - 1, 2 * T, 2 * T + 1, 3 * T + 5, 4 * T - 3}
     sizes |= {(1 << k) + d for k in (14, 15, 16, 17, 20) for d in (-1, 0, 1)}
     sizes |= {4096 * 3 + 7, 70_001}
+    # around the single-CTA small-array tile: 1024 threads x (2L - 1) keys
+    # (x 3 for the classical set)
+    L = max([k for k in range(3, 9) if (oracle.NETSETS[netset] >> k) & 1] or [1])
+    small = 1024 * (3 if L == 1 else 2 * L - 1)
+    sizes |= {small - 1, small, small + 1}
     return sorted(sizes)
 
 
