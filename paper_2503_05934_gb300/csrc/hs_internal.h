@@ -111,6 +111,7 @@ hs_status merge_sort_i64(int64_t *d_keys, size_t n, hs_netset s, void *d_ws, siz
 int64_t keys_tile(int L, int64_t n);
 void merge_set_blocksort_shape(int v);
 void merge_set_fanin(int v);
+int merge_fanin();  // the option's value: 0 (by size), 2 or 4
 
 // Block sort of [0, n) in tiles of keys_tile(L) keys (the merge path's first pass;
 // the whole sort when n fits one tile).

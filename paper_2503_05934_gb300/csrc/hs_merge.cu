@@ -129,6 +129,7 @@ static hs_status launch_keys_level(const int32_t *kin, int32_t *kout, int64_t n,
 constexpr int64_t kFourWayMinKeys = int64_t(1) << 27;
 static int g_merge_fanin = 0;
 void merge_set_fanin(int v) { g_merge_fanin = v; }
+int merge_fanin() { return g_merge_fanin; }
 
 constexpr int M4_NT = kMerge4Threads, M4_EO = kMerge4Keys;
 

@@ -162,6 +162,36 @@ def test_pairs_copy_forms_keep_results(hs):
                 assert np.array_equal(vo, ev), (n, kinds, off)
 
 
+@pytest.mark.parametrize("fanin", [4, 2])
+def test_pairs_four_way_levels(hs, fanin):
+    """Four-way pair levels (forced at every size) against the oracle's
+    stable order: odd and even numbers of doublings, ragged last groups, few
+    distinct keys (equal keys spread over all four runs of a group, where
+    the run order decides), descending blocks and arbitrary values; binary
+    levels on the same inputs."""
+    rng = np.random.default_rng(91 + fanin)
+    T = int(hs.lib().hs_pairs_tile(hs.netset_mask("6To8")))
+    sizes = sorted({2 * T, 3 * T + 4, 4 * T, 5 * T + 8, 8 * T, 9 * T + 12, 16 * T + 4,
+                    33 * T - 8, 64 * T + 100, (1 << 21) + 4 * 333})
+    hs.hs_set_option("merge_fanin", fanin)
+    try:
+        for n in sizes:
+            for kind in ["few", "wide", "blocks"]:
+                if kind == "few":
+                    k = rng.integers(0, 3, n).astype(np.int32)
+                elif kind == "wide":
+                    k = rng.integers(-(1 << 31), 1 << 31, n, dtype=np.int64).astype(np.int32)
+                else:
+                    k = ((n - np.arange(n)) // 4000).astype(np.int32)
+                v = rng.integers(-(1 << 31), 1 << 31, n, dtype=np.int64).astype(np.int32)
+                ek, ev = oracle.merge_sort_pairs(k, v, "6To8")
+                ko, vo = gpu_sort_pairs(hs, k, v, "6To8")
+                assert np.array_equal(ko, ek), (n, kind)
+                assert np.array_equal(vo, ev), (n, kind)
+    finally:
+        hs.hs_set_option("merge_fanin", 0)
+
+
 @pytest.mark.parametrize("netset", ["none", "3To5", "Odd", "3To4", "6To8", "3", "PowerOf2"])
 def test_pairs_all_netsets_small_words(hs, netset):
     """Every word over {0, 1, 2} of length 1..8, concatenated (ties
