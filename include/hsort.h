@@ -134,7 +134,7 @@ HS_API hs_status hs_sort_i64(int64_t *d_keys, size_t n, hs_algo a, hs_netset s, 
  * back into h_keys and waits for `stream` before returning (synchronous).
  * For merge sorts of 2^22 keys or more the copy in travels in at most 8
  * chunks on a library-created copy stream; each chunk is sorted completely on
- * one of three library-created side streams as soon as it has arrived (the
+ * one of four library-created side streams as soon as it has arrived (the
  * chunks' sorts overlap one another and the copy of the next chunks); merge
  * levels over the sorted chunks on `stream` finish the sort, and the last
  * one runs in eight parts whose keys are copied out as soon as each is done.
