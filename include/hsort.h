@@ -176,6 +176,54 @@ HS_API hs_status hs_sort_i32_host(int32_t *h_keys, size_t n, hs_algo a, hs_netse
 #define HS_NOALLOC_MAX_KEYS 4194304u
 HS_API hs_status hs_sort_i32_noalloc(int32_t *d_keys, size_t n, hs_netset s, hs_stream_t stream);
 
+/* ------------------------------------------------ single-array launch plan */
+
+/* Launch plan of the single-array merge path (hs_sort_i32 with
+ * HS_ALGO_MERGE, its host-buffer form and the server's sorts).  Both fields
+ * change only the time, never the result.  The path decides each of them, in
+ * this order: the options "blocksort_shape" / "merge_fanin" when set to a
+ * value other than their automatic one; a plan hs_sort_autotune (or
+ * hs_tune_cache_load) cached for this device, this array size's log2
+ * bucket and this leaf size; the built-in rules (the larger block-sort tile
+ * when it saves a merge level; four-way levels from 2^27 keys). */
+typedef struct {
+    int32_t blocksort_threads; /* block-sort CTA: 256 (tile 256 x (4L - 1) keys)
+                                  or 288 (288 x (4L - 1) keys); L = leaf size */
+    int32_t merge_fanin;       /* runs merged per pass of the global levels: 2 or
+                                  4 (four applies only to 16-byte aligned keys
+                                  with n % 4 == 0; other arrays merge two-way) */
+    int32_t reserved[2];       /* 0 */
+} hs_sort_plan;
+
+/* Autotuner of the single-array merge path: times every candidate plan
+ * (blocksort_threads 256 / 288 x merge_fanin 2 / 4 where four-way applies),
+ * one warm-up and two timed sorts each with CUDA events on `stream`, on the
+ * caller's keys with network set s, and returns the fastest in *best (its
+ * time, the smaller of the two, in *best_ms if non-NULL).  The keys are
+ * restored to their input order afterwards.  The winner is cached
+ * in-process by device name, floor(log2 n) and leaf size, and from then on
+ * the merge path uses it for every array in that bucket (unless an option
+ * overrides it); a cached entry is returned without timing.  The cache is
+ * saved and loaded with the batched form's (hs_tune_cache_save / _load,
+ * entries of kind "sort").  n <= 1 returns {256, 2} without timing.
+ * Synchronous.
+ *   d_keys  device keys, 4-byte aligned.
+ *   d_ws    ws_bytes >= hs_sort_autotune_workspace_bytes(n), 16-byte
+ *           aligned (the merge workspace plus a copy of the keys).
+ * Errors: HS_ERR_INVALID_ARG for NULL/unaligned pointers, a bad netset or a
+ * short workspace; HS_ERR_CUDA if a copy, launch or event fails (the keys are
+ * still restored when the restoring copy itself succeeds). */
+HS_API size_t hs_sort_autotune_workspace_bytes(size_t n);
+HS_API hs_status hs_sort_autotune(int32_t *d_keys, size_t n, hs_netset s, void *d_ws,
+                                  size_t ws_bytes, hs_stream_t stream, hs_sort_plan *best,
+                                  double *best_ms);
+/* The plan the merge path would take now for n keys at address d_keys
+ * (only its 16-byte alignment is read; NULL reads as aligned) with network
+ * set s: options, cached plan or rules, as above.  Host only; launches
+ * nothing.  HS_ERR_INVALID_ARG for a NULL result or a bad netset. */
+HS_API hs_status hs_sort_plan_for(const int32_t *d_keys, size_t n, hs_netset s,
+                                  hs_sort_plan *out);
+
 /* ----------------------------------------------------------- batched form */
 
 /* Launch plan of the batched form: which network set forms the leaves and
@@ -242,11 +290,17 @@ HS_API size_t hs_segsort_autotune_workspace_bytes(size_t n_keys, size_t num_segs
 HS_API hs_status hs_segsort_autotune(int32_t *d_keys, size_t n_keys, const int64_t *d_offsets,
                                      size_t num_segs, void *d_ws, size_t ws_bytes,
                                      hs_stream_t stream, hs_plan *best, double *best_ms);
-/* The autotuner cache as a JSON file: save writes every entry; load merges
- * the file's entries into the in-process cache (HS_ERR_INVALID_ARG if the
- * file cannot be read or parsed). */
+/* The autotuners' cache as a JSON file: an array of objects, one per entry,
+ * of kind "batched" (hs_segsort_autotune; objects without a kind read as
+ * batched) or "sort" (hs_sort_autotune).  Save writes every entry; load
+ * merges the file's entries into the in-process cache, all or none
+ * (HS_ERR_INVALID_ARG if the file cannot be read or parsed, or an entry
+ * holds an invalid plan). */
 HS_API hs_status hs_tune_cache_save(const char *path);
 HS_API hs_status hs_tune_cache_load(const char *path);
+/* Empties both autotuners' in-process caches: the merge path goes back to
+ * its built-in rules and the next autotune call times again. */
+HS_API void hs_tune_cache_clear(void);
 
 /* ---------------------------------------------------------------- serving */
 

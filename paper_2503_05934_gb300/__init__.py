@@ -14,7 +14,7 @@ import ctypes
 
 import torch
 
-from ._lib import HsortError, Plan, check, lib
+from ._lib import HsortError, Plan, SortPlan, check, lib
 
 NETSETS = {
     "none": 0x000, "3": 0x008, "3To4": 0x018, "3To5": 0x038, "6To8": 0x1C0,
@@ -33,7 +33,7 @@ __all__ = [
     "Plan", "make_plan",
     "hs_segsort_workspace_bytes", "hs_segsort_i32", "hs_sort_i32_many", "Graph",
     "hs_segsort_capture", "hs_segsort_autotune", "hs_tune_cache_save", "hs_tune_cache_load",
-    "Server", "hs_merge_split",
+    "Server", "hs_merge_split", "SortPlan", "hs_sort_autotune", "hs_sort_plan_for", "hs_tune_cache_clear",
 ]
 
 
@@ -225,12 +225,41 @@ def hs_segsort_autotune(keys: torch.Tensor, offsets: torch.Tensor, ws: torch.Ten
     return plan, float(ms.value)
 
 
+def hs_sort_autotune(keys: torch.Tensor, netset="6To8", ws: torch.Tensor | None = None,
+                     stream=None):
+    """Times the single-array merge path's plans on ``keys``; returns (SortPlan,
+    milliseconds) of the fastest and caches it for this size bucket; keys unchanged."""
+    _check_i32(keys, "keys")
+    n = keys.numel()
+    ws = _workspace(int(lib().hs_sort_autotune_workspace_bytes(n)), keys.device, ws)
+    plan = SortPlan()
+    ms = ctypes.c_double()
+    with torch.cuda.device(keys.device):
+        check(lib().hs_sort_autotune(keys.data_ptr() if n else None, n, netset_mask(netset),
+                                     ws.data_ptr(), ws.numel() * ws.element_size(),
+                                     _stream_ptr(stream), ctypes.byref(plan), ctypes.byref(ms)))
+    return plan, float(ms.value)
+
+
+def hs_sort_plan_for(n: int, netset="6To8", keys: torch.Tensor | None = None) -> SortPlan:
+    """The plan the merge path takes now for ``n`` keys (aligned unless ``keys`` says
+    otherwise).  Host only; reads the cache of the current CUDA device."""
+    plan = SortPlan()
+    check(lib().hs_sort_plan_for(keys.data_ptr() if keys is not None else None, n,
+                                 netset_mask(netset), ctypes.byref(plan)))
+    return plan
+
+
 def hs_tune_cache_save(path: str) -> None:
     check(lib().hs_tune_cache_save(path.encode()))
 
 
 def hs_tune_cache_load(path: str) -> None:
     check(lib().hs_tune_cache_load(path.encode()))
+
+
+def hs_tune_cache_clear() -> None:
+    lib().hs_tune_cache_clear()
 
 
 class Server:

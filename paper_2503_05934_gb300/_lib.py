@@ -40,8 +40,12 @@ SIGNATURES = {
     "hs_segsort_autotune_workspace_bytes": (_sz, [_sz, _sz]),
     "hs_segsort_autotune": (_int, [_vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp,
                                    ctypes.POINTER(ctypes.c_double)]),
+    "hs_sort_autotune_workspace_bytes": (_sz, [_sz]),
+    "hs_sort_autotune": (_int, [_vp, _sz, _u32, _vp, _sz, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "hs_sort_plan_for": (_int, [_vp, _sz, _u32, _vp]),
     "hs_tune_cache_save": (_int, [ctypes.c_char_p]),
     "hs_tune_cache_load": (_int, [ctypes.c_char_p]),
+    "hs_tune_cache_clear": (None, []),
     "hs_server_create": (_int, [_sz, ctypes.POINTER(_vp)]),
     "hs_server_submit": (_int, [_vp, _vp, _sz, _int, _u32, ctypes.POINTER(ctypes.c_uint64)]),
     "hs_server_wait": (_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_int),
@@ -80,6 +84,16 @@ class Plan(ctypes.Structure):
     def as_dict(self) -> dict:
         return {"netset": int(self.netset), "block_threads": int(self.block_threads),
                 "ctas_per_sm": int(self.ctas_per_sm)}
+
+
+class SortPlan(ctypes.Structure):
+    """hs_sort_plan: block-sort CTA size and merge fan-in of the single-array merge path."""
+    _fields_ = [("blocksort_threads", ctypes.c_int32), ("merge_fanin", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+    def as_dict(self) -> dict:
+        return {"blocksort_threads": int(self.blocksort_threads),
+                "merge_fanin": int(self.merge_fanin)}
 
 
 class HsortError(RuntimeError):

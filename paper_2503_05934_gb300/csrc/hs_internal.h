@@ -111,6 +111,27 @@ hs_status merge_sort_i64(int64_t *d_keys, size_t n, hs_netset s, void *d_ws, siz
 int64_t keys_tile(int L, int64_t n);
 void merge_set_blocksort_shape(int v);
 void merge_set_fanin(int v);
+
+// Launch plan of the single-array merge path (see hs_sort_plan).
+struct SortPlan {
+    int shape;  // block-sort shape: 2 (256 threads) or 4 (288 threads)
+    int fanin;  // merge fan-in of the tiled keys levels: 2 or 4
+};
+void sort_plan_force(const SortPlan *p);  // this thread's override (null clears)
+// Whether the merge levels over these keys can run four-way (16-byte
+// aligned keys, n a multiple of 4); otherwise the fan-in is always 2.
+bool merge_four_way_possible(const int32_t *d_keys, int64_t n);
+// The plan the merge path takes for these keys now (forced, options, cache, rules).
+SortPlan merge_plan_for(const int32_t *d_keys, int64_t n, int L);
+int size_bucket(int64_t n);               // floor(log2 n)
+hs_status current_device_name(std::string *out);
+void sort_plan_cache_put(const std::string &device, int n_bucket, int leaf, const SortPlan &p,
+                         double ms);
+bool sort_plan_cache_get(const std::string &device, int n_bucket, int leaf, SortPlan *p,
+                         double *ms);
+void sort_plan_cache_clear();
+void sort_plan_cache_each(void (*fn)(void *, const std::string &, int, int, const SortPlan &, double),
+                          void *ctx);
 int merge_fanin();  // the option's value: 0 (by size), 2 or 4
 
 // Block sort of [0, n) in tiles of keys_tile(L) keys (the merge path's first pass;

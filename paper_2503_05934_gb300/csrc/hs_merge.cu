@@ -3,6 +3,9 @@
 // ping-ponging between the caller's array and the workspace so that the last
 // level lands in the caller's array.
 #include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -30,9 +33,120 @@ static int global_levels(int64_t n, int64_t tile) {
     for (int64_t w = tile; w < n; w *= 2) ++p;
     return p;
 }
-static int shape_for(int64_t n, int L) {
-    if (g_bs_shape >= 0) return g_bs_shape;
+// ---------------------------------------------------------------------------
+// Launch plans of the single-array merge path: block-sort shape and merge
+// fan-in.  Decided, in this order, by a plan forced on this thread (while
+// the autotuner times candidates), by the options when they are not at
+// their automatic values, by a plan the autotuner cached for this device,
+// array size (log2 bucket) and leaf size, and otherwise by the built-in
+// rules (shape_rule, the fan-in's size rule).
+static thread_local const SortPlan *t_forced_plan = nullptr;
+void sort_plan_force(const SortPlan *p) { t_forced_plan = p; }
+
+struct SortPlanEntry {
+    std::string device;
+    int n_bucket, leaf;
+    SortPlan plan;
+    double ms;
+};
+static std::mutex g_plan_mu;
+static std::vector<SortPlanEntry> g_plans;
+static std::atomic<int> g_plans_count{0};  // entries cached (a lock-free "none" test)
+
+int size_bucket(int64_t n) {
+    int b = 0;
+    while (b < 62 && (int64_t(2) << b) <= n) ++b;
+    return b;  // floor(log2 n) for n >= 1
+}
+
+// Name of device `dev`, looked up once per ordinal.
+static const std::string *device_name_cached(int dev) {
+    static std::mutex mu;
+    static std::string names[64];
+    static bool have[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!have[dev]) {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        names[dev] = prop.name;
+        have[dev] = true;
+    }
+    return &names[dev];
+}
+
+hs_status current_device_name(std::string *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+    const std::string *nm = device_name_cached(dev);
+    if (!nm) return fail(HS_ERR_CUDA, "cudaGetDeviceProperties failed");
+    *out = *nm;
+    return HS_OK;
+}
+
+void sort_plan_cache_put(const std::string &device, int n_bucket, int leaf, const SortPlan &p,
+                         double ms) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (SortPlanEntry &e : g_plans)
+        if (e.device == device && e.n_bucket == n_bucket && e.leaf == leaf) {
+            e.plan = p;
+            e.ms = ms;
+            return;
+        }
+    g_plans.push_back(SortPlanEntry{device, n_bucket, leaf, p, ms});
+    g_plans_count.store((int)g_plans.size());
+}
+
+bool sort_plan_cache_get(const std::string &device, int n_bucket, int leaf, SortPlan *p,
+                         double *ms) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (const SortPlanEntry &e : g_plans)
+        if (e.device == device && e.n_bucket == n_bucket && e.leaf == leaf) {
+            *p = e.plan;
+            if (ms) *ms = e.ms;
+            return true;
+        }
+    return false;
+}
+
+void sort_plan_cache_clear() {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans.clear();
+    g_plans_count.store(0);
+}
+
+void sort_plan_cache_each(void (*fn)(void *, const std::string &, int, int, const SortPlan &, double),
+                          void *ctx) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (const SortPlanEntry &e : g_plans) fn(ctx, e.device, e.n_bucket, e.leaf, e.plan, e.ms);
+}
+
+// The cached plan for an n-key array of leaf size L on the current device.
+static bool tuned_plan(int64_t n, int L, SortPlan *p) {
+    if (g_plans_count.load() == 0) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const std::string *nm = device_name_cached(dev);
+    return nm && sort_plan_cache_get(*nm, size_bucket(n), L, p, nullptr);
+}
+
+static int shape_rule(int64_t n, int L) {
     return global_levels(n, shape_tile(4, L)) < global_levels(n, shape_tile(2, L)) ? 4 : 2;
+}
+
+static int shape_for(int64_t n, int L) {
+    if (t_forced_plan) return t_forced_plan->shape;
+    if (g_bs_shape >= 0) return g_bs_shape;
+    SortPlan p;
+    if (tuned_plan(n, L, &p)) return p.shape;
+    return shape_rule(n, L);
 }
 
 int64_t keys_tile(int L, int64_t n) { return shape_tile(shape_for(n, L), L); }
@@ -176,10 +290,22 @@ static hs_status launch_keys_level4(const int32_t *kin, int32_t *kout, int64_t n
     return HS_OK;
 }
 
-// Whether the global levels over an n-key array merge four runs per pass.
-static bool four_way_levels(int64_t n, int vec) {
-    if (!tiled_levels(n, vec) || g_merge_fanin == 2) return false;
-    return g_merge_fanin == 4 || n >= kFourWayMinKeys;
+// Whether the global levels over an n-key array (leaf size L) merge four
+// runs per pass.
+bool merge_four_way_possible(const int32_t *d_keys, int64_t n) {
+    return tiled_levels(n, aligned(d_keys, 16) ? 1 : 0);
+}
+static bool four_way_levels(int64_t n, int vec, int L) {
+    if (!tiled_levels(n, vec)) return false;
+    if (t_forced_plan) return t_forced_plan->fanin == 4;
+    if (g_merge_fanin != 0) return g_merge_fanin == 4;
+    SortPlan p;
+    if (tuned_plan(n, L, &p)) return p.fanin == 4;
+    return n >= kFourWayMinKeys;
+}
+
+SortPlan merge_plan_for(const int32_t *d_keys, int64_t n, int L) {
+    return SortPlan{shape_for(n, L), four_way_levels(n, aligned(d_keys, 16) ? 1 : 0, L) ? 4 : 2};
 }
 
 // Launches of the global levels that double the runs d times.
@@ -224,7 +350,7 @@ static hs_status merge_sort_with(int32_t *d_keys, int64_t n, hs_netset s, int32_
     const int d = global_levels(n, T);
     const int vec = aligned(d_keys, 16) ? 1 : 0;
     if (!tiled_levels(n, vec)) samp = nullptr;
-    const bool four = four_way_levels(n, vec);
+    const bool four = four_way_levels(n, vec, L);
     // Land the last level in the caller's array: with an even number of
     // launched levels the block sort writes in place.
     int32_t *kcur = (level_launches(d, four) % 2 == 0) ? d_keys : kbuf;
@@ -406,7 +532,7 @@ hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, h
     // The levels over the whole array are four-way by its size; a chunk's own
     // levels by the chunk's (the parity of its launches places its block
     // sort), and only when the whole array takes tiled levels.
-    const bool four = four_way_levels(n, vec);
+    const bool four = four_way_levels(n, vec, L);
     const int64_t part_cap = (int64_t)merge_ws_part_entries(n_);
 
     HostPipe *pp = nullptr;
@@ -438,7 +564,7 @@ hs_status merge_sort_host_chunked(int32_t *h_keys, int32_t *d_keys, size_t n_, h
         }
         // The block sort writes where the chunk's ping-pong levels end in d_keys.
         const int d = global_levels(len, T);
-        const bool four_c = tiled_levels(n, vec) && four_way_levels(len, vec);
+        const bool four_c = tiled_levels(n, vec) && four_way_levels(len, vec, L);
         const bool even = level_launches(d, four_c) % 2 == 0;
         int32_t *cur = even ? d_keys + b : m.kbuf + b;
         int32_t *alt = even ? m.kbuf + b : d_keys + b;

@@ -219,3 +219,90 @@ def test_merge_split_host_rejects_bad_arguments():
         hs.hs_merge_split(keys, [0, 32], [8, 8], 17)  # rank past the total
     with pytest.raises(ValueError):
         hs.hs_merge_split(keys, [0, 33], [8, 8], 3, keys[::32])  # unaligned start with samples
+
+
+def _plan_for(hs, n, netset=0x1C0, keys=None):
+    from paper_2503_05934_gb300 import _lib
+    p = _lib.SortPlan()
+    assert hs.hs_sort_plan_for(keys, n, netset, ctypes.byref(p)) == 0
+    return int(p.blocksort_threads), int(p.merge_fanin)
+
+
+def test_sort_plan_rules_and_options(hs):
+    """The single-array plan from the built-in rules (no cached plan can match
+    without a device), and the options' precedence over them."""
+    # The 288-thread tile (8928 keys for {6,7,8}) saves a global level for
+    # every power of two from 2^14; 2^13 fits either tile.
+    assert _plan_for(hs, 1 << 20) == (288, 2)
+    assert _plan_for(hs, 9000) == (256, 2)       # 9000 <= 2 * 7936: one level either way
+    assert _plan_for(hs, 1 << 27) == (288, 4)    # four-way levels from 2^27 keys
+    assert _plan_for(hs, (1 << 27) + 2) == (288, 2)          # n % 4 != 0: binary levels
+    assert _plan_for(hs, 1 << 27, keys=FAKE + 4) == (288, 2)  # keys not 16-byte aligned
+    try:
+        assert hs.hs_set_option(b"blocksort_shape", 2) == 0
+        assert hs.hs_set_option(b"merge_fanin", 4) == 0
+        assert _plan_for(hs, 1 << 20) == (256, 4)
+        assert _plan_for(hs, (1 << 20) + 1) == (256, 2)      # four-way does not apply
+        assert hs.hs_set_option(b"merge_fanin", 2) == 0
+        assert _plan_for(hs, 1 << 28) == (256, 2)
+    finally:
+        assert hs.hs_set_option(b"blocksort_shape", -1) == 0
+        assert hs.hs_set_option(b"merge_fanin", 0) == 0
+    assert _plan_for(hs, 1 << 28) == (288, 4)
+    from paper_2503_05934_gb300 import _lib
+    p = _lib.SortPlan()
+    assert hs.hs_sort_plan_for(None, 100, 0x1, ctypes.byref(p)) == 1
+    assert hs.hs_sort_plan_for(None, 100, 0x1C0, None) == 1
+
+
+def test_sort_autotune_argument_errors(hs):
+    from paper_2503_05934_gb300 import _lib
+    p, ms = _lib.SortPlan(), ctypes.c_double(-1.0)
+    n = 1 << 20
+    need = hs.hs_sort_autotune_workspace_bytes(n)
+    assert need >= hs.hs_sort_workspace_bytes(n, 0, 0) + 4 * n
+    assert hs.hs_sort_autotune(FAKE, n, 0x1C0, FAKE, need, None, None, None) == 1
+    assert hs.hs_sort_autotune(FAKE, n, 0x1, FAKE, need, None, ctypes.byref(p), None) == 1
+    assert hs.hs_sort_autotune(None, n, 0x1C0, FAKE, need, None, ctypes.byref(p), None) == 1
+    assert hs.hs_sort_autotune(FAKE + 2, n, 0x1C0, FAKE, need, None, ctypes.byref(p), None) == 1
+    assert hs.hs_sort_autotune(FAKE, n, 0x1C0, FAKE, need - 1, None, ctypes.byref(p), None) == 1
+    assert b"workspace" in hs.hs_last_error()
+    assert hs.hs_sort_autotune(FAKE, n, 0x1C0, FAKE + 4, need, None, ctypes.byref(p), None) == 1
+    # n <= 1: nothing to time, no device needed
+    assert hs.hs_sort_autotune(None, 0, 0x1C0, None, 0, None, ctypes.byref(p), ctypes.byref(ms)) == 0
+    assert (p.blocksort_threads, p.merge_fanin, ms.value) == (256, 2, 0.0)
+
+
+def test_tune_cache_json_holds_both_kinds(hs, tmp_path):
+    """Sort plans and batched plans share the cache file; a file with one
+    invalid entry changes nothing (all or none)."""
+    import json
+    dev = "cache-test-device-a"
+    src = tmp_path / "in.json"
+    src.write_text(json.dumps([
+        {"kind": "sort", "device": dev, "n_bucket": 24, "leaf": 8,
+         "blocksort_threads": 256, "merge_fanin": 4, "ms": 1.25},
+        {"device": dev, "n_bucket": 20, "s_bucket": 10, "m_bucket": 10, "netset": 0x1C0,
+         "block_threads": 256, "ctas_per_sm": 0, "ms": 0.5},
+    ]))
+    assert hs.hs_tune_cache_load(str(src).encode()) == 0
+    out = tmp_path / "out.json"
+    assert hs.hs_tune_cache_save(str(out).encode()) == 0
+    entries = [e for e in json.loads(out.read_text()) if e["device"] == dev]
+    kinds = sorted(e["kind"] for e in entries)
+    assert kinds == ["batched", "sort"]
+    (s,) = [e for e in entries if e["kind"] == "sort"]
+    assert (s["n_bucket"], s["leaf"], s["blocksort_threads"], s["merge_fanin"]) == (24, 8, 256, 4)
+    assert abs(s["ms"] - 1.25) < 1e-9
+    # Invalid sort entries: nothing from the file is cached.
+    dev_b = "cache-test-device-b"
+    for bad in [{"blocksort_threads": 300}, {"merge_fanin": 3}, {"leaf": 9}]:
+        good = {"kind": "sort", "device": dev_b, "n_bucket": 20, "leaf": 8,
+                "blocksort_threads": 288, "merge_fanin": 2, "ms": 1.0}
+        src.write_text(json.dumps([good, dict(good, n_bucket=21, **bad)]))
+        assert hs.hs_tune_cache_load(str(src).encode()) == 1
+        assert hs.hs_tune_cache_save(str(out).encode()) == 0
+        assert not [e for e in json.loads(out.read_text()) if e["device"] == dev_b]
+    src.write_text(json.dumps([{"kind": "other", "device": dev_b}]))
+    assert hs.hs_tune_cache_load(str(src).encode()) == 1
+    assert b"unknown kind" in hs.hs_last_error()
