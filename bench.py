@@ -428,19 +428,19 @@ def run_ours(args):
         h_pristine = host
         h_buf = torch.empty(n, dtype=torch.int32).pin_memory()
         ws_h = torch.empty(hs.hs_sort_host_workspace_bytes(n), dtype=torch.uint8, device=dev)
-        for _ in range(max(1, min(args.warmup, 2))):
+        for _ in range(max(1, min(args.warmup, 3))):
             h_buf.numpy()[:] = h_pristine
             hs.hs_sort_i32_host(h_buf, "merge", args.netset, ws=ws_h, stream=stream)
         e2e_steps = max(1, min(args.steps, 10))
-        tot = 0.0
+        step_s = []
         for _ in range(e2e_steps):
             h_buf.numpy()[:] = h_pristine
             if pg:
                 pg.barrier()
             t0 = time.perf_counter()
             hs.hs_sort_i32_host(h_buf, "merge", args.netset, ws=ws_h, stream=stream)
-            tot += time.perf_counter() - t0
-        tot = max_over_ranks(tot, pg, dev)
+            step_s.append(time.perf_counter() - t0)
+        tot = max_over_ranks(sum(step_s), pg, dev)
         assert bool(np.all(h_buf.numpy()[1:] >= h_buf.numpy()[:-1])), "e2e output not sorted"
         # The host link on this machine: plain copies of the same bytes, each
         # way (context for how much of the end-to-end time is copying).
@@ -462,6 +462,10 @@ def run_ours(args):
                        "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
                        "steps": e2e_steps, "api": "hs_sort_i32_host (pinned host buffer)",
                        "ms_per_step": tot / e2e_steps * 1e3,
+                       # this rank's calls one by one (the host link and host
+                       # memory are shared with other jobs on the node)
+                       "ms_steps": [round(x * 1e3, 3) for x in step_s],
+                       "ms_per_step_median": float(np.median(step_s)) * 1e3,
                        "link": {k: round(v, 1) for k, v in link.items()},
                        # both copies back to back, nothing else: the floor
                        # for a call that must copy in before it can copy out

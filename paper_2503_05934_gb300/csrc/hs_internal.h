@@ -109,6 +109,10 @@ hs_status merge_sort_i64(int64_t *d_keys, size_t n, hs_netset s, void *d_ws, siz
 // Tile of the keys block sort of an n-key array for leaf size L, and its
 // shape options.
 int64_t keys_tile(int L, int64_t n);
+// One CTA sorts a whole array of up to small_sort_max(L) keys in one launch
+// (no workspace).
+int64_t small_sort_max(int L);
+hs_status small_sort(int32_t *keys, int64_t n, hs_netset s, cudaStream_t st);
 void merge_set_blocksort_shape(int v);
 void merge_set_fanin(int v);
 

@@ -411,6 +411,11 @@ static hs_status small_sort_launch(int32_t *keys, int64_t n, hs_netset s, cudaSt
     return fail(HS_ERR_INVALID_ARG, "leaf size outside 1, 3..8");
 }
 
+int64_t small_sort_max(int L) { return small_tile(L); }
+hs_status small_sort(int32_t *keys, int64_t n, hs_netset s, cudaStream_t st) {
+    return small_sort_launch(keys, n, s, st);
+}
+
 hs_status merge_sort(int32_t *d_keys, int32_t *d_vals, size_t n_, hs_netset s, void *d_ws,
                      size_t ws_bytes, cudaStream_t st) {
     if (d_vals) return pairs_sort(d_keys, d_vals, n_, s, d_ws, ws_bytes, st);

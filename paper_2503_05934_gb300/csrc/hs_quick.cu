@@ -497,6 +497,9 @@ hs_status quick_sort(int32_t *d_keys, size_t n_, hs_netset s, void *d_ws, size_t
     const int L = leaf_size(s);
     const int64_t tile = qs_tile(L);
     const int vec = aligned(d_keys, 16) ? 1 : 0;
+    // Arrays of one tile are the base case: no partition.  Up to the small
+    // sort's tile one CTA sorts them in one launch.
+    if (n <= small_sort_max(L)) return small_sort(d_keys, n, s, st);
     if (n <= keys_tile(L, n)) return blocksort_launch(L, d_keys, d_keys, n, s, vec, st);
 
     const QLayout q = qs_layout(n_);
