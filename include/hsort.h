@@ -97,7 +97,12 @@ HS_API size_t hs_sort_workspace_bytes(size_t n, int with_values, hs_algo a);
  *            vectorised paths); may be NULL only when n == 0.
  *   n        number of keys; 0 and 1 are no-ops.
  *   d_ws     device workspace of ws_bytes >= hs_sort_workspace_bytes(n, 0, a).
- * MERGE is fully asynchronous.  QUICK learns each partition level's
+ * MERGE is fully asynchronous, and a caller may capture it into its own CUDA
+ * graph.  A merge sort of more than one tile called again with the same
+ * keys and workspace addresses, n and s (on any stream, from the same host
+ * thread) is captured into a library graph on its second call and replayed
+ * from then on: the same kernels, with one graph launch instead of one
+ * launch per kernel (option "sort_graphs").  QUICK learns each partition level's
  * counters through mapped host memory and waits for the level two behind the
  * one it launches, so the call returns only when all but the last levels have
  * run, and it cannot be captured in a CUDA graph.  It also runs each level's
@@ -411,6 +416,10 @@ HS_API hs_status hs_bulk_wait_selftest(uint32_t polls, hs_stream_t stream);
  *     levels is odd); 2 binary levels only; 0 (default) four-way levels for
  *     arrays of at least 2^27 keys, binary below (the four-way partition's
  *     latency outweighs the saved pass on smaller arrays).
+ *   "sort_graphs": 1 (default) hs_sort_i32's merge path replays a captured
+ *     graph for repeated calls with the same arguments (see hs_sort_i32); 0
+ *     always launches kernel by kernel.  Changing any option, or the tuned
+ *     plans, retires the graphs captured before.
  * Tiled levels (bulk-copied tiles, sampled partition searches) serve 16-byte
  * aligned buffers whose length is a multiple of 4 keys (of 2 for int64);
  * other buffers take thread-staged generic forms.  Every option gives

@@ -54,6 +54,22 @@ LaunchToken launch_begin(int id, cudaStream_t stream);
 // Adds k kernels launched indirectly (graph replays) to the launch count.
 void count_launches(uint64_t k);
 hs_status launch_end(const LaunchToken &t);
+// While this thread captures a sort into a graph, launches are counted into
+// *counter instead of the global count (replays add them); null ends it.
+void capture_launches_into(uint64_t *counter);
+// Whether per-kernel event timing is on (graph replays are then not used).
+bool prof_enabled();
+
+// Generation of everything that decides a merge sort's launches (options,
+// tuned plans): bumped on every change, so cached graphs of older
+// generations are not replayed.
+uint64_t config_generation();
+void bump_config_generation();
+// Replays a captured graph of an earlier merge sort with the same
+// arguments, or captures one on the second call (hs_sort_i32's merge path).
+hs_status merge_sort_graphed(int32_t *d_keys, size_t n, hs_netset s, void *d_ws,
+                             size_t ws_bytes, cudaStream_t st);
+void sort_graphs_enable(int on);
 
 // Validation shared by the entry points.
 inline bool netset_ok(hs_netset s) {

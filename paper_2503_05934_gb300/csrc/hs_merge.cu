@@ -95,10 +95,12 @@ void sort_plan_cache_put(const std::string &device, int n_bucket, int leaf, cons
         if (e.device == device && e.n_bucket == n_bucket && e.leaf == leaf) {
             e.plan = p;
             e.ms = ms;
+            bump_config_generation();
             return;
         }
     g_plans.push_back(SortPlanEntry{device, n_bucket, leaf, p, ms});
     g_plans_count.store((int)g_plans.size());
+    bump_config_generation();
 }
 
 bool sort_plan_cache_get(const std::string &device, int n_bucket, int leaf, SortPlan *p,
@@ -117,6 +119,7 @@ void sort_plan_cache_clear() {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     g_plans.clear();
     g_plans_count.store(0);
+    bump_config_generation();
 }
 
 void sort_plan_cache_each(void (*fn)(void *, const std::string &, int, int, const SortPlan &, double),

@@ -63,6 +63,9 @@ static double g_prof_ms[K_COUNT];
 ApiRange::ApiRange(const char *name) { nvtxRangePushA(name); }
 ApiRange::~ApiRange() { nvtxRangePop(); }
 
+static thread_local uint64_t *t_capture_counter = nullptr;
+void capture_launches_into(uint64_t *counter) { t_capture_counter = counter; }
+
 LaunchToken launch_begin(int id, cudaStream_t stream) {
     nvtxRangePushA(kRangeNames[id]);  // popped by launch_end
     LaunchToken t{id, stream, nullptr, nullptr};
@@ -88,7 +91,8 @@ LaunchToken launch_begin(int id, cudaStream_t stream) {
 hs_status launch_end(const LaunchToken &t) {
     nvtxRangePop();
     cudaError_t e = cudaGetLastError();
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (t_capture_counter) *t_capture_counter += 1;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
     if (t.ev_a) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         cudaEventRecord(t.ev_b, t.stream);
@@ -99,6 +103,12 @@ hs_status launch_end(const LaunchToken &t) {
 }
 
 void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+bool prof_enabled() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
+
+static std::atomic<uint64_t> g_config_gen{1};
+uint64_t config_generation() { return g_config_gen.load(); }
+void bump_config_generation() { g_config_gen.fetch_add(1); }
 
 static void prof_drain_locked() {
     for (auto &s : g_prof_pending) {
@@ -296,7 +306,7 @@ hs_status hs_sort_i32(int32_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d
     if (st != HS_OK) return st;
     if (n <= 1) return HS_OK;
     if (a == HS_ALGO_QUICK) return quick_sort(d_keys, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
-    return merge_sort(d_keys, nullptr, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
+    return merge_sort_graphed(d_keys, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
 hs_status hs_sort_pairs_i32(int32_t *d_keys, int32_t *d_vals, size_t n, hs_algo a, hs_netset s,
@@ -389,6 +399,13 @@ hs_status hs_device_check(hs_stream_t stream) {
 hs_status hs_set_option(const char *name, int64_t value) {
     clear_error();
     if (!name) return fail(HS_ERR_INVALID_ARG, "hs_set_option: NULL name");
+    bump_config_generation();
+    if (std::strcmp(name, "sort_graphs") == 0) {
+        if (value != 0 && value != 1)
+            return fail(HS_ERR_INVALID_ARG, "hs_set_option: sort_graphs must be 0 or 1");
+        sort_graphs_enable((int)value);
+        return HS_OK;
+    }
     if (std::strcmp(name, "quick_max_levels") == 0) {
         quick_set_max_levels(value);
         return HS_OK;

@@ -484,3 +484,71 @@ def test_full_size_pairs_2p27(hs):
     ek, ev = oracle.merge_sort_pairs(k, v, "6To8")
     assert np.array_equal(ko, ek) and np.array_equal(vo, ev)
     check_stable_pairs_index_values(k, ko, vo)
+
+
+def _sort_calls(hs, src, buf, ws, calls):
+    """Sorts a fresh copy of src in the same buffer `calls` times; returns the
+    launches each call counted."""
+    import torch
+    counts = []
+    for _ in range(calls):
+        buf.copy_(src)
+        c0 = hs.hs_launch_count()
+        hs.hs_sort_i32(buf, "merge", "6To8", ws=ws)
+        counts.append(hs.hs_launch_count() - c0)
+        torch.cuda.synchronize()
+        assert np.array_equal(buf.cpu().numpy(), np.sort(src.cpu().numpy()))
+    return counts
+
+
+def test_repeated_sorts_replay_a_graph(hs):
+    """The second call with the same arrays captures the sort into a CUDA graph
+    and later calls replay it: identical results and the same kernels counted
+    as the direct launches (a replay does all the work again)."""
+    import torch
+    n = 1 << 20
+    src = to_dev(g.random_i32(n, 91))
+    buf = torch.empty_like(src)
+    ws = torch.empty(hs.hs_sort_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    hs.hs_set_option("sort_graphs", 0)
+    try:
+        direct = _sort_calls(hs, src, buf, ws, 2)
+    finally:
+        hs.hs_set_option("sort_graphs", 1)
+    assert direct == [15, 15]  # block sort + seven binary levels (partition and merge)
+    assert _sort_calls(hs, src, buf, ws, 5) == [15] * 5
+    # A changed option is a new configuration: older graphs are not replayed.
+    hs.hs_set_option("merge_fanin", 4)
+    try:
+        assert _sort_calls(hs, src, buf, ws, 4) == [9] * 4  # one binary, three four-way levels
+    finally:
+        hs.hs_set_option("merge_fanin", 0)
+    assert _sort_calls(hs, src, buf, ws, 3) == [15] * 3
+    # Another array of the same size is another signature, and still exact.
+    other = to_dev(g.keys(n, "nearly", 92))
+    buf2 = torch.empty_like(other)
+    assert _sort_calls(hs, other, buf2, ws, 3) == [15] * 3
+    hs.hs_device_check()
+
+
+def test_merge_sort_inside_a_caller_graph(hs):
+    """The merge path is asynchronous: a caller can capture it into its own
+    CUDA graph (the library then launches directly into the capture) and
+    replay it on new data."""
+    import torch
+    n = 300_000
+    src = to_dev(g.random_i32(n, 93))
+    buf = src.clone()
+    ws = torch.empty(hs.hs_sort_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    hs.hs_sort_i32(buf, "merge", "6To8", ws=ws)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        hs.hs_sort_i32(buf, "merge", "6To8", ws=ws)
+    for seed in (94, 95):
+        a = g.random_i32(n, seed)
+        buf.copy_(torch.from_numpy(a))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(buf.cpu().numpy(), np.sort(a))
+    hs.hs_device_check()

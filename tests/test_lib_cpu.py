@@ -137,6 +137,7 @@ OPTIONS = [
     ("blocksort_shape", -1, 4, [-2, 0, 1, 3, 5, 6]),
     ("merge_fanin", 0, 4, [1, 3, 8, -1]),
     ("quick_partition", 3, 2, [1, 4]),
+    ("sort_graphs", 1, 0, [2, -1]),
 ]
 
 
