@@ -431,7 +431,7 @@ def run_ours(args):
         for _ in range(max(1, min(args.warmup, 3))):
             h_buf.numpy()[:] = h_pristine
             hs.hs_sort_i32_host(h_buf, "merge", args.netset, ws=ws_h, stream=stream)
-        e2e_steps = max(1, min(args.steps, 10))
+        e2e_steps = max(1, min(args.steps, 20))
         step_s = []
         for _ in range(e2e_steps):
             h_buf.numpy()[:] = h_pristine
