@@ -103,10 +103,10 @@ HS_API size_t hs_sort_workspace_bytes(size_t n, int with_values, hs_algo a);
  * thread) is captured into a library graph on its second call and replayed
  * from then on: the same kernels, with one graph launch instead of one
  * launch per kernel (option "sort_graphs").  The graphs belong to the CUDA
- * context they were captured in: a process that calls cudaDeviceReset must
- * set "sort_graphs" to 0 before it (or not sort again afterwards), since a
- * replay after the reset would launch a graph of the old context.  QUICK
- * learns each partition level's
+ * context they were captured in and are kept for the life of the process:
+ * with "sort_graphs" on, do not sort across a cudaDeviceReset of a device the
+ * library has sorted on (a later call could replay or free a graph of the old
+ * context).  QUICK learns each partition level's
  * counters through mapped host memory and waits for the level two behind the
  * one it launches, so the call returns only when all but the last levels have
  * run, and it cannot be captured in a CUDA graph.  It also runs each level's
