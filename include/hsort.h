@@ -124,7 +124,8 @@ HS_API hs_status hs_sort_i32(int32_t *d_keys, size_t n, hs_algo a, hs_netset s, 
  * (key, input position); merges take the left run on ties.
  *   a must be HS_ALGO_MERGE: QUICK is not stable -> HS_ERR_UNSUPPORTED.
  *   d_ws: ws_bytes >= hs_sort_workspace_bytes(n, 1, HS_ALGO_MERGE).
- * Other conventions and errors as hs_sort_i32. */
+ * Other conventions and errors as hs_sort_i32 (graph replay of repeated calls
+ * included: the signature also holds d_vals). */
 HS_API hs_status hs_sort_pairs_i32(int32_t *d_keys, int32_t *d_vals, size_t n, hs_algo a,
                             hs_netset s, void *d_ws, size_t ws_bytes, hs_stream_t stream);
 
@@ -133,7 +134,8 @@ HS_API hs_status hs_sort_pairs_i32(int32_t *d_keys, int32_t *d_vals, size_t n, h
  * path only: HS_ALGO_QUICK returns HS_ERR_UNSUPPORTED.  d_keys must be 8-byte
  * aligned; the workspace (hs_sort_i64_workspace_bytes, 16-byte aligned,
  * owned by the caller) holds a keys copy, the merge partitions and every
- * 32nd key.  Errors as hs_sort_i32.  Asynchronous on stream. */
+ * 32nd key.  Errors as hs_sort_i32.  Asynchronous on stream; repeated calls
+ * replay a captured graph as hs_sort_i32's merge path does. */
 HS_API size_t hs_sort_i64_workspace_bytes(size_t n);
 HS_API hs_status hs_sort_i64(int64_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d_ws,
                              size_t ws_bytes, hs_stream_t stream);

@@ -67,8 +67,10 @@ uint64_t config_generation();
 void bump_config_generation();
 // Replays a captured graph of an earlier merge sort with the same
 // arguments, or captures one on the second call (hs_sort_i32's merge path).
-hs_status merge_sort_graphed(int32_t *d_keys, size_t n, hs_netset s, void *d_ws,
+hs_status merge_sort_graphed(int32_t *d_keys, int32_t *d_vals, size_t n, hs_netset s, void *d_ws,
                              size_t ws_bytes, cudaStream_t st);
+hs_status merge_sort_i64_graphed(int64_t *d_keys, size_t n, hs_netset s, void *d_ws,
+                                 size_t ws_bytes, cudaStream_t st);
 void sort_graphs_enable(int on);
 
 // Validation shared by the entry points.

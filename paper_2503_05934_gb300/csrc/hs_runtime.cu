@@ -306,7 +306,7 @@ hs_status hs_sort_i32(int32_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d
     if (st != HS_OK) return st;
     if (n <= 1) return HS_OK;
     if (a == HS_ALGO_QUICK) return quick_sort(d_keys, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
-    return merge_sort_graphed(d_keys, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
+    return merge_sort_graphed(d_keys, nullptr, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
 hs_status hs_sort_pairs_i32(int32_t *d_keys, int32_t *d_vals, size_t n, hs_algo a, hs_netset s,
@@ -320,7 +320,7 @@ hs_status hs_sort_pairs_i32(int32_t *d_keys, int32_t *d_vals, size_t n, hs_algo 
     if (a == HS_ALGO_QUICK)
         return fail(HS_ERR_UNSUPPORTED, "hs_sort_pairs_i32: quick sort is not stable; use HS_ALGO_MERGE");
     if (n <= 1) return HS_OK;
-    return merge_sort(d_keys, d_vals, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
+    return merge_sort_graphed(d_keys, d_vals, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
 size_t hs_sort_i64_workspace_bytes(size_t n) { return merge_workspace_bytes_i64(n); }
@@ -339,7 +339,7 @@ hs_status hs_sort_i64(int64_t *d_keys, size_t n, hs_algo a, hs_netset s, void *d
     if (a == HS_ALGO_QUICK)
         return fail(HS_ERR_UNSUPPORTED, "hs_sort_i64: int64 keys use the merge path");
     if (n <= 1) return HS_OK;
-    return merge_sort_i64(d_keys, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
+    return merge_sort_i64_graphed(d_keys, n, s, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
 size_t hs_sort_host_workspace_bytes(size_t n, hs_algo a) {

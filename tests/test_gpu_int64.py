@@ -90,3 +90,23 @@ def test_int64_full_size_2p27(hs):
     rng = np.random.default_rng(1)
     for v in a[rng.integers(0, n, 8)]:
         assert np.searchsorted(out, v, "left") == np.count_nonzero(a < v)
+
+
+def test_int64_repeated_sorts_replay_a_graph(hs):
+    """int64 keys through the graph replay: identical results on every call on
+    the same buffers, the same kernels counted each time."""
+    import torch
+    n = 500_000
+    a = g.keys_i64(n, "random", 97)
+    t = torch.from_numpy(a).cuda()
+    ws = torch.empty(hs.hs_sort_i64_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    counts = []
+    for _ in range(4):
+        t.copy_(torch.from_numpy(a))
+        c0 = hs.hs_launch_count()
+        hs.hs_sort_i64(t, "merge", "6To8", ws=ws)
+        counts.append(hs.hs_launch_count() - c0)
+        torch.cuda.synchronize()
+        assert np.array_equal(t.cpu().numpy(), np.sort(a))
+    assert len(set(counts)) == 1 and counts[0] > 1
+    hs.hs_device_check()

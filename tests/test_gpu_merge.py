@@ -552,3 +552,27 @@ def test_merge_sort_inside_a_caller_graph(hs):
         torch.cuda.synchronize()
         assert np.array_equal(buf.cpu().numpy(), np.sort(a))
     hs.hs_device_check()
+
+
+def test_repeated_pair_sorts_replay_a_graph(hs):
+    """Stable pairs through the graph replay: every call on the same buffers
+    (the third on replaying a captured graph) gives the oracle's stable order
+    and counts the same kernels."""
+    import torch
+    n = 300_000
+    k, v = g.pair_keys_16bit(n, 96)
+    ws = torch.empty(hs.hs_sort_workspace_bytes(n, True), dtype=torch.uint8, device="cuda")
+    tk, tv = to_dev(k), to_dev(v)
+    want_k, want_v = oracle.merge_sort_pairs(k, v, "6To8")
+    counts = []
+    for _ in range(4):
+        tk.copy_(torch.from_numpy(k))
+        tv.copy_(torch.from_numpy(v))
+        c0 = hs.hs_launch_count()
+        hs.hs_sort_pairs_i32(tk, tv, "merge", "6To8", ws=ws)
+        counts.append(hs.hs_launch_count() - c0)
+        torch.cuda.synchronize()
+        assert np.array_equal(tk.cpu().numpy(), want_k)
+        assert np.array_equal(tv.cpu().numpy(), want_v)
+    assert len(set(counts)) == 1 and counts[0] > 1
+    hs.hs_device_check()
