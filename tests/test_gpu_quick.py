@@ -41,8 +41,9 @@ def test_paper_sizes_quick(hs, n, dist, netset):
 def test_edge_sizes_quick(hs, netset):
     L = max([k for k in range(3, 9) if (oracle.NETSETS[netset] >> k) & 1] or [1])
     T = 1024 * L
+    ST = 1024 * (3 if L == 1 else 2 * L - 1)  # the single-CTA sort's tile: the base case up to it
     sizes = sorted(set(range(0, 12)) | {T - 1, T, T + 1, 2 * T + 1, 8191, 8192, 8193,
-                                        8192 * 3 + 1, (1 << 17) + 3, 500_001})
+                                        ST - 1, ST, ST + 1, 8192 * 3 + 1, (1 << 17) + 3, 500_001})
     for n in sizes:
         a = g.random_i32(n, 300 + n)
         assert np.array_equal(gpu_quick(hs, a, netset), oracle.quick_sort(a, netset)), n
