@@ -559,6 +559,23 @@ def run_extras(hs, torch, dev, stream, args, rank, pristine, passes_design):
                 entry["frac_of_measured_one_pass"] = qbytes1 / (ms / 1e3) / (peak * 1e9)
             out[f"{algo}_2p{args.log2n}_{dist}"] = entry
         del src
+    # The single-array autotuner on the headline workload: the plan it picks
+    # (block-sort CTA size, merge fan-in) beside the built-in rules' plan.
+    # The tuned plan is cleared afterwards so the extras below run on the rules.
+    work.copy_(pristine)
+    rule = hs.hs_sort_plan_for(n_keys, args.netset, work).as_dict()
+    wst = torch.empty(int(hs.lib().hs_sort_autotune_workspace_bytes(n_keys)), dtype=torch.uint8,
+                      device=dev)
+    t0 = time.perf_counter()
+    plan, best_ms = hs.hs_sort_autotune(work, args.netset, ws=wst, stream=stream)
+    tune_s = time.perf_counter() - t0
+    assert torch.equal(work, pristine), "the autotuner changed the keys"
+    out["autotune_2p%d" % args.log2n] = {"plan": plan.as_dict(), "best_ms": best_ms, "rule_plan": rule,
+                                         "tuning_s": tune_s,
+                                         "candidates": "blocksort_threads 256/288 x merge_fanin 2/4, "
+                                                       "one warm-up and two timed sorts each"}
+    hs.hs_tune_cache_clear()
+    del wst
     del work, wsm, wsq
     # Stable pairs: 2^27 keys from 2^16 distinct values, value = index.
     n = 1 << (args.log2n - 1)
