@@ -260,8 +260,10 @@ HS_API size_t hs_segsort_workspace_bytes(size_t n_keys, size_t num_segs);
  *              Malformed offsets are detected on the device: the segment is
  *              skipped and hs_device_check reports HS_ERR_INVALID_ARG.
  *   a          HS_ALGO_MERGE (QUICK -> HS_ERR_UNSUPPORTED).
- *   s, plan    plan == NULL: network set s with the default shape; otherwise
- *              the plan (its netset replaces s).
+ *   s, plan    plan == NULL: the plan hs_segsort_autotune cached for this
+ *              device and these size buckets when its network set is s, else
+ *              network set s with the default shape; otherwise the plan (its
+ *              netset replaces s).
  *   d_ws       ws_bytes >= hs_segsort_workspace_bytes(n_keys, num_segs).
  * No host synchronisation: the call can be captured (see hs_segsort_capture).
  * Designed for segments up to about 2^20 keys (larger ones work but are
@@ -298,6 +300,10 @@ HS_API void hs_graph_destroy(hs_graph *g);
  *   d_ws: ws_bytes >= hs_segsort_autotune_workspace_bytes(n_keys, num_segs)
  *   (the segsort workspace plus a copy of the keys). */
 HS_API size_t hs_segsort_autotune_workspace_bytes(size_t n_keys, size_t num_segs);
+/* The plan hs_segsort_i32 takes for plan == NULL with these sizes and network
+ * set s (see there); host only, launches nothing.  HS_ERR_INVALID_ARG for a
+ * NULL result or a bad netset. */
+HS_API hs_status hs_segsort_plan_for(size_t n_keys, size_t num_segs, hs_netset s, hs_plan *out);
 HS_API hs_status hs_segsort_autotune(int32_t *d_keys, size_t n_keys, const int64_t *d_offsets,
                                      size_t num_segs, void *d_ws, size_t ws_bytes,
                                      hs_stream_t stream, hs_plan *best, double *best_ms);

@@ -33,7 +33,7 @@ __all__ = [
     "Plan", "make_plan",
     "hs_segsort_workspace_bytes", "hs_segsort_i32", "hs_sort_i32_many", "Graph",
     "hs_segsort_capture", "hs_segsort_autotune", "hs_tune_cache_save", "hs_tune_cache_load",
-    "Server", "hs_merge_split", "SortPlan", "hs_sort_autotune", "hs_sort_plan_for", "hs_tune_cache_clear",
+    "Server", "hs_merge_split", "SortPlan", "hs_sort_autotune", "hs_sort_plan_for", "hs_tune_cache_clear", "hs_segsort_plan_for",
 ]
 
 
@@ -239,6 +239,13 @@ def hs_sort_autotune(keys: torch.Tensor, netset="6To8", ws: torch.Tensor | None 
                                      ws.data_ptr(), ws.numel() * ws.element_size(),
                                      _stream_ptr(stream), ctypes.byref(plan), ctypes.byref(ms)))
     return plan, float(ms.value)
+
+
+def hs_segsort_plan_for(n_keys: int, num_segs: int, netset="6To8") -> Plan:
+    """The plan hs_segsort_i32 takes with no plan given for these sizes and set."""
+    plan = Plan()
+    check(lib().hs_segsort_plan_for(n_keys, num_segs, netset_mask(netset), ctypes.byref(plan)))
+    return plan
 
 
 def hs_sort_plan_for(n: int, netset="6To8", keys: torch.Tensor | None = None) -> SortPlan:

@@ -43,6 +43,7 @@ SIGNATURES = {
     "hs_sort_autotune_workspace_bytes": (_sz, [_sz]),
     "hs_sort_autotune": (_int, [_vp, _sz, _u32, _vp, _sz, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "hs_sort_plan_for": (_int, [_vp, _sz, _u32, _vp]),
+    "hs_segsort_plan_for": (_int, [_sz, _sz, _u32, _vp]),
     "hs_tune_cache_save": (_int, [ctypes.c_char_p]),
     "hs_tune_cache_load": (_int, [ctypes.c_char_p]),
     "hs_tune_cache_clear": (None, []),

@@ -60,6 +60,11 @@ static bool cache_find(const std::string &dev, int nb, int sb, int mb, TuneEntry
     return false;
 }
 
+static size_t cache_size() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune.size();
+}
+
 static void cache_put(const TuneEntry &e) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (TuneEntry &t : g_tune)
@@ -406,13 +411,33 @@ size_t hs_segsort_workspace_bytes(size_t n_keys, size_t num_segs) {
     return segsort_workspace_bytes(n_keys, num_segs);
 }
 
-static hs_status plan_from(const hs_plan *plan, hs_netset s, hs_plan *out) {
+// The plan a NULL plan stands for: the one hs_segsort_autotune cached for
+// this device and these size buckets when its network set is s, else s with
+// the default shape.
+static hs_plan tuned_or_default(size_t n_keys, size_t num_segs, hs_netset s) {
+    if (n_keys > 0 && num_segs > 0 && cache_size() > 0) {
+        std::string dev;
+        if (current_device_name(&dev) == HS_OK) {
+            TuneEntry hit;
+            if (cache_find(dev, log2_bucket((double)n_keys), log2_bucket((double)num_segs),
+                           log2_bucket((double)n_keys / (double)num_segs), &hit) &&
+                hit.plan.netset == s)
+                return hit.plan;
+        } else {
+            clear_error();  // no device to match: the default shape
+        }
+    }
+    return default_seg_plan(s);
+}
+
+static hs_status plan_from(const hs_plan *plan, hs_netset s, size_t n_keys, size_t num_segs,
+                           hs_plan *out) {
     if (plan) {
         if (plan->reserved != 0) return fail(HS_ERR_INVALID_ARG, "plan reserved field must be 0");
         *out = *plan;
     } else {
         if (!netset_ok(s)) return fail(HS_ERR_INVALID_ARG, "netset is neither a set of sizes 3..8 nor a VarSort configuration");
-        *out = default_seg_plan(s);
+        *out = tuned_or_default(n_keys, num_segs, s);
     }
     return check_plan(*out);
 }
@@ -426,7 +451,7 @@ hs_status hs_segsort_i32(int32_t *d_keys, size_t n_keys, const int64_t *d_offset
         return fail(HS_ERR_UNSUPPORTED, "hs_segsort_i32: the batched form runs the merge path only");
     if (a != HS_ALGO_MERGE) return fail(HS_ERR_INVALID_ARG, "hs_segsort_i32: unknown algo");
     hs_plan p;
-    hs_status r = plan_from(plan, s, &p);
+    hs_status r = plan_from(plan, s, n_keys, num_segs, &p);
     if (r != HS_OK) return r;
     return segsort(d_keys, n_keys, d_offsets, num_segs, p, d_ws, ws_bytes, (cudaStream_t)stream);
 }
@@ -452,7 +477,7 @@ hs_status hs_segsort_capture(int32_t *d_keys, size_t n_keys, const int64_t *d_of
     clear_error();
     if (!out) return fail(HS_ERR_INVALID_ARG, "hs_segsort_capture: NULL result");
     hs_plan p;
-    hs_status r = plan_from(plan, HS_NETS_6TO8, &p);
+    hs_status r = plan_from(plan, HS_NETS_6TO8, n_keys, num_segs, &p);
     if (r != HS_OK) return r;
     void *h = nullptr;
     r = segsort_capture(d_keys, n_keys, d_offsets, num_segs, p, d_ws, ws_bytes, &h);
@@ -486,6 +511,12 @@ hs_status hs_sort_autotune(int32_t *d_keys, size_t n, hs_netset s, void *d_ws, s
     const ApiRange range("hs_sort_autotune");
     clear_error();
     return sort_autotune(d_keys, n, s, d_ws, ws_bytes, (cudaStream_t)stream, best, best_ms);
+}
+
+hs_status hs_segsort_plan_for(size_t n_keys, size_t num_segs, hs_netset s, hs_plan *out) {
+    clear_error();
+    if (!out) return fail(HS_ERR_INVALID_ARG, "hs_segsort_plan_for: NULL result");
+    return plan_from(nullptr, s, n_keys, num_segs, out);
 }
 
 hs_status hs_sort_plan_for(const int32_t *d_keys, size_t n, hs_netset s, hs_sort_plan *out) {

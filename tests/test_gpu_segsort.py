@@ -145,6 +145,17 @@ def test_autotune_restores_keys_and_caches(hs, tmp_path):
     assert '"block_threads"' in text and '"netset"' in text
     assert np.array_equal(gpu_segsort(hs, keys, off, plan=plan),
                           oracle.segsort(keys, off, "merge", "6To8"))
+    # With no plan given, a call with the tuned plan's network set takes it;
+    # another set keeps the default shape.
+    nseg = len(off) - 1
+    netsets = {v: k for k, v in hs.NETSETS.items()}
+    assert hs.hs_segsort_plan_for(keys.size, nseg, int(plan.netset)).as_dict() == plan.as_dict()
+    other = 0xA8 if int(plan.netset) != 0xA8 else 0x1C0
+    assert hs.hs_segsort_plan_for(keys.size, nseg, other).as_dict() == \
+        {"netset": other, "block_threads": 256, "ctas_per_sm": 0}
+    assert np.array_equal(gpu_segsort(hs, keys, off, netset=netsets.get(int(plan.netset), "6To8")),
+                          oracle.segsort(keys, off, "merge", "6To8"))
+    hs.hs_tune_cache_clear()
 
 
 def test_malformed_offsets_are_reported(hs):

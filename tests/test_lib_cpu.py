@@ -307,3 +307,16 @@ def test_tune_cache_json_holds_both_kinds(hs, tmp_path):
     src.write_text(json.dumps([{"kind": "other", "device": dev_b}]))
     assert hs.hs_tune_cache_load(str(src).encode()) == 1
     assert b"unknown kind" in hs.hs_last_error()
+
+
+def test_segsort_plan_for_defaults(hs):
+    """With no tuned plan for this device (none on a machine without a GPU),
+    a NULL batched plan is the network set with the default shape."""
+    from paper_2503_05934_gb300 import _lib
+    p = _lib.Plan()
+    assert hs.hs_segsort_plan_for(100_000, 100, 0x1C0, ctypes.byref(p)) == 0
+    assert p.as_dict() == {"netset": 0x1C0, "block_threads": 256, "ctas_per_sm": 0}
+    assert hs.hs_segsort_plan_for(100_000, 100, 0xA8, ctypes.byref(p)) == 0
+    assert p.netset == 0xA8
+    assert hs.hs_segsort_plan_for(100_000, 100, 0x1, ctypes.byref(p)) == 1
+    assert hs.hs_segsort_plan_for(100_000, 100, 0x1C0, None) == 1
