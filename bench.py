@@ -14,6 +14,7 @@ same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -357,9 +358,12 @@ def run_ours(args):
     if pg:
         pg.barrier()
     torch.cuda.synchronize(dev)
+    gc.collect()
+    gc.disable()
     t_wall0 = time.perf_counter()
     evs = [step_timed() for _ in range(args.steps)]
     torch.cuda.synchronize(dev)
+    gc.enable()
     if pg:
         pg.barrier()
     t_wall = time.perf_counter() - t_wall0
@@ -433,6 +437,11 @@ def run_ours(args):
             hs.hs_sort_i32_host(h_buf, "merge", args.netset, ws=ws_h, stream=stream)
         e2e_steps = max(1, min(args.steps, 20))
         step_s = []
+        # The harness's own garbage collection is kept out of the timed calls
+        # (as timeit does): a full collection in this long-lived process can
+        # take tens of milliseconds.
+        gc.collect()
+        gc.disable()
         for _ in range(e2e_steps):
             h_buf.numpy()[:] = h_pristine
             if pg:
@@ -440,6 +449,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             hs.hs_sort_i32_host(h_buf, "merge", args.netset, ws=ws_h, stream=stream)
             step_s.append(time.perf_counter() - t0)
+        gc.enable()
         tot = max_over_ranks(sum(step_s), pg, dev)
         assert bool(np.all(h_buf.numpy()[1:] >= h_buf.numpy()[:-1])), "e2e output not sorted"
         # The host link on this machine: plain copies of the same bytes, each
