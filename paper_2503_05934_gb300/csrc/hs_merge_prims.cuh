@@ -229,6 +229,32 @@ static __global__ void k_merge_partition(const int32_t *in, int64_t n, int64_t w
 // and both tests are monotone in m.  Same result as k_merge_partition.
 constexpr int kSampleStride = 32;
 
+// Merge-path split by one warp (32-ary search): the smallest i in [lo, hi]
+// with A[i] > B[diag - 1 - i] (hi when there is none), the number of A
+// elements among the first diag outputs of the stable merge.  Each round the
+// lanes test 32 evenly spaced candidates (two independent loads each) and the
+// range shrinks 32-fold, so a 65536-key range takes about four dependent load
+// rounds instead of sixteen.  The final round starts with fewer than 32
+// candidates left, so the last lane always tests a position >= hi and the
+// ballot is never empty.  Every lane returns the result.
+HS_DEV int64_t warp_merge_path(const int32_t *A, const int32_t *B, int64_t diag, int64_t lo,
+                               int64_t hi, int lane) {
+    while (hi - lo >= 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t q = lo + (int64_t)(lane + 1) * step;  // candidate; q >= hi counts as true
+        const bool t = q >= hi || A[q] > B[diag - 1 - q];
+        const unsigned m = __ballot_sync(0xffffffffu, t);
+        const int f = __ffs(m) - 1;  // some lane holds q >= hi, so m != 0
+        const int64_t nlo = f == 0 ? lo : lo + (int64_t)f * step + 1;
+        hi = hs_min(hi, lo + (int64_t)(f + 1) * step);
+        lo = nlo;
+    }
+    const int64_t q = lo + lane;
+    const bool t = q >= hi || A[q] > B[diag - 1 - q];
+    const unsigned m = __ballot_sync(0xffffffffu, t);
+    return lo + (__ffs(m) - 1);
+}
+
 static __global__ void k_merge_partition_sampled(const int32_t *in, const int32_t *samp,
                                                  int64_t n, int64_t w, int to, int tpg,
                                                  int64_t nblocks, int64_t *part) {

@@ -284,15 +284,17 @@ def test_workspace_reuse_and_launch_count(hs, fanin):
             assert np.array_equal(t.cpu().numpy(), np.sort(a))
     finally:
         hs.hs_set_option("merge_fanin", 0)
-    # 1 block sort + 2 launches (partition, merge) per global level over the
-    # block-sort tile the library reports for this n; four-way levels take
-    # two doublings each, after one binary level when their number is odd
+    # 1 block sort, then the global levels over the block-sort tile the
+    # library reports for this n: four-way levels take two doublings each
+    # (partition + merge launches), after one binary level when their number
+    # is odd; binary levels of this size (265 tiles, within L2) search their
+    # own splits: one launch each
     tile = int(hs.lib().hs_keys_tile(hs.netset_mask("6To8"), n))
     levels = 0
     while tile << levels < n:
         levels += 1
-    launches = levels // 2 + levels % 2 if fanin == 4 else levels
-    assert hs.hs_launch_count() - before == 3 * (1 + 2 * launches)
+    binary, four = (levels % 2, levels // 2) if fanin == 4 else (levels, 0)
+    assert hs.hs_launch_count() - before == 3 * (1 + binary + 2 * four)
 
 
 def _four_way_inputs(n, seed):
@@ -515,19 +517,19 @@ def test_repeated_sorts_replay_a_graph(hs):
         direct = _sort_calls(hs, src, buf, ws, 2)
     finally:
         hs.hs_set_option("sort_graphs", 1)
-    assert direct == [15, 15]  # block sort + seven binary levels (partition and merge)
-    assert _sort_calls(hs, src, buf, ws, 5) == [15] * 5
+    assert direct == [8, 8]  # block sort + seven binary levels that search their own splits
+    assert _sort_calls(hs, src, buf, ws, 5) == [8] * 5
     # A changed option is a new configuration: older graphs are not replayed.
-    hs.hs_set_option("merge_fanin", 4)
+    hs.hs_set_option("blocksort_shape", 2)
     try:
-        assert _sort_calls(hs, src, buf, ws, 4) == [9] * 4  # one binary, three four-way levels
+        assert _sort_calls(hs, src, buf, ws, 4) == [9] * 4  # 7936-key tiles: eight levels
     finally:
-        hs.hs_set_option("merge_fanin", 0)
-    assert _sort_calls(hs, src, buf, ws, 3) == [15] * 3
+        hs.hs_set_option("blocksort_shape", -1)
+    assert _sort_calls(hs, src, buf, ws, 3) == [8] * 3
     # Another array of the same size is another signature, and still exact.
     other = to_dev(g.keys(n, "nearly", 92))
     buf2 = torch.empty_like(other)
-    assert _sort_calls(hs, other, buf2, ws, 3) == [15] * 3
+    assert _sort_calls(hs, other, buf2, ws, 3) == [8] * 3
     hs.hs_device_check()
 
 
