@@ -63,22 +63,7 @@ __global__ void __launch_bounds__(NT)
     int64_t a0, a1;
     if constexpr (SELF_SPLIT) {
         static_assert(NT >= 64, "two warps search the tile's two splits");
-        __shared__ int64_t s_split[2];
-        const int wp = (int)(threadIdx.x >> 5);
-        if (wp < 2) {
-            // Boundary wp of this tile: output rank o0 (wp 0) or o1 (wp 1).
-            const int64_t diag = wp == 0 ? o0 : o1;
-            const int64_t lo = diag > m.blen ? diag - m.blen : 0;
-            const int64_t hi = diag < m.alen ? diag : m.alen;
-            const int64_t r = (wp == 1 && o1 == glen)
-                                  ? m.alen
-                                  : warp_merge_path(in + m.gs, in + m.gs + w, diag, lo, hi,
-                                                    (int)(threadIdx.x & 31));
-            if ((threadIdx.x & 31) == 0) s_split[wp] = r;
-        }
-        __syncthreads();
-        a0 = s_split[0];
-        a1 = s_split[1];
+        tile_self_split(in, m.gs, w, m.alen, m.blen, o0, o1, &a0, &a1);
     } else {
         a0 = part[b];
         a1 = (o1 == glen) ? m.alen : part[b + 1];
@@ -157,13 +142,7 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
-// Levels of at most this many output tiles (about 17.8M keys: both buffers
-// of such a level fit the 129 MB L2) search their splits inside the merge
-// tiles (SELF_SPLIT) instead of a partition pass.  Measured per sort, with /
-// without: 25K keys 40.6 / 47 us, 100K 50 / 71 us, 1M 68.7 / 117.6 us, 4M 146
-// / 219 us, 16M 0.497 / 0.513 ms; past L2 the searches go to DRAM and lose:
-// 64M keys (16,900 tiles) 1.963 / 1.697 ms.
-constexpr int64_t kSelfSplitMaxTiles = 4500;
+
 
 // Partition pass of one tiled level: part[b] = A keys before output tile b.
 // With samp (samples of kin at stride kSampleStride) it searches the samples

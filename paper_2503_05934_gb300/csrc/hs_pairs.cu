@@ -28,7 +28,9 @@ struct TileMergePairs {
     static constexpr int SMEM_BYTES = 2 * REG * 4;  // keys, values
 };
 
-template <int NT, int EO>
+// SELF_SPLIT: the CTA searches its own two splits (tile_self_split), for
+// levels small enough to need no partition pass (part is unused).
+template <int NT, int EO, bool SELF_SPLIT = false>
 __global__ void __launch_bounds__(NT)
     k_merge_tile_pairs_bulk(const int32_t *kin, int32_t *kout, const int32_t *vin, int32_t *vout,
                             int64_t n, int64_t w, const int64_t *part, int tpg, int32_t *samp,
@@ -46,8 +48,14 @@ __global__ void __launch_bounds__(NT)
     const int64_t glen = m.alen + m.blen;
     const int64_t o0 = (int64_t)t * TO;
     const int64_t o1 = (o0 + TO) < glen ? (o0 + TO) : glen;
-    const int64_t a0 = part[blockIdx.x];
-    const int64_t a1 = (o1 == glen) ? m.alen : part[blockIdx.x + 1];
+    int64_t a0, a1;
+    if constexpr (SELF_SPLIT) {
+        static_assert(NT >= 64, "two warps search the tile's two splits");
+        tile_self_split(kin, m.gs, w, m.alen, m.blen, o0, o1, &a0, &a1);
+    } else {
+        a0 = part[blockIdx.x];
+        a1 = (o1 == glen) ? m.alen : part[blockIdx.x + 1];
+    }
     const int na = (int)(a1 - a0);
     const int tot = (int)(o1 - o0);
     const int nb = tot - na;
@@ -398,6 +406,17 @@ static hs_status launch_pairs_tile(const int32_t *kin, int32_t *kout, const int3
     using C = TileMergePairs<PM_NT, PM_EO>;
     static_assert(C::TO % kSampleStride == 0, "output tiles start on sample positions");
     const LevelTiles lt = level_tiles(n, w, C::TO);
+    if (lt.nblocks <= kSelfSplitMaxTiles) {
+        unsigned *status = nullptr;
+        hs_status r = device_status(&status);
+        if (r != HS_OK) return r;
+        auto kern = k_merge_tile_pairs_bulk<PM_NT, PM_EO, true>;
+        if ((r = ensure_smem((const void *)kern, C::SMEM_BYTES)) != HS_OK) return r;
+        LaunchToken t = launch_begin(K_MERGE_PAIRS, st);
+        kern<<<(unsigned)lt.nblocks, PM_NT, C::SMEM_BYTES, st>>>(kin, kout, vin, vout, n, w, nullptr,
+                                                                 (int)lt.tpg, samp, status);
+        return launch_end(t);
+    }
     LaunchToken t = launch_begin(K_MERGE_PARTITION, st);
     k_merge_partition_sampled<<<(unsigned)((lt.nblocks + 255) / 256), 256, 0, st>>>(
         kin, samp, n, w, C::TO, (int)lt.tpg, lt.nblocks, part);
